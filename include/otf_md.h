@@ -1,0 +1,235 @@
+/*
+ * otf_md.h - C ABI of the GB300 on-the-fly property library.
+ *
+ * The library runs a Lennard-Jones molecular-dynamics system on one GPU and
+ * computes, while it runs, the quantities of arXiv 2503.07526 ("DL_POLY 5:
+ * Calculation of system properties on the fly for very large systems via
+ * massive parallelism"): the system stress tensor and heat flux every step
+ * (Sec. 2.3), multiple-tau correlators of the off-diagonal stress, the heat
+ * flux and every atom's velocity (Sec. 2.2, Appendix D Algorithms 1-2), and
+ * Green-Kubo integrals of them (Sec. 2.3 Eqs. (visc), (therm)).
+ *
+ * Conventions shared by every call:
+ *  - Every function returns an int status: MD_OK (0) or a negative MD_E*
+ *    code; md_last_error() then holds a message for the calling thread.  No
+ *    C++ exception crosses this boundary.
+ *  - Positions, velocities and forces are component-major arrays [3][n]
+ *    (all x, then all y, then all z) in the caller's atom order.  Stress
+ *    tensors and per-particle virials use the order xx, yy, zz, xy, xz, yz.
+ *  - The library copies every input and keeps no caller pointer.  Handles
+ *    are owned by the library and released with md_free / corr_free.
+ *  - All GPU work is enqueued on the CUDA stream given at creation
+ *    (a cudaStream_t passed as void*, NULL for the legacy default stream).
+ *    Calls that hand results to the host synchronise that stream.
+ *  - Units are the caller's; the tests use LJ reduced units
+ *    (eps = sigma = m = kB = 1).
+ */
+#ifndef OTF_MD_H
+#define OTF_MD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Exported from libotfmd.so (the library is built with hidden visibility). */
+#if defined(__GNUC__)
+#define OTF_API __attribute__((visibility("default")))
+#else
+#define OTF_API
+#endif
+
+/* Status codes. */
+#define MD_OK 0
+#define MD_EINVAL (-1)   /* invalid argument or parameter */
+#define MD_ENOMEM (-2)   /* device or host allocation failed */
+#define MD_ECUDA (-3)    /* a CUDA runtime call failed */
+#define MD_ESTATE (-4)   /* the system left its valid state: non-finite
+                            coordinates, a neighbour list or cell over its
+                            capacity, fewer than 3 cells per side */
+#define MD_ETIMEOUT (-5) /* a bounded device wait gave up */
+#define MD_ECAP (-6)     /* output buffer too small; *n holds the size needed */
+
+/* Arithmetic of the MD path. */
+#define MD_PREC_FP64 0   /* every step in FP64 */
+#define MD_PREC_MIXED 1  /* FP32 forces, per-particle fluxes and correlator
+                            products; FP64 positions, velocities, global
+                            reductions and correlator lag sums */
+
+/* Where caller arrays live. */
+#define MD_MEM_HOST 0
+#define MD_MEM_DEVICE 1
+
+/* Correlators owned by an MD system (md_corr). */
+#define MD_CORR_STRESS 0   /* 3 series: sigma_xy, sigma_xz, sigma_yz */
+#define MD_CORR_HEATFLUX 1 /* 3 series: q_x, q_y, q_z */
+#define MD_CORR_VACF 2     /* 3n series: v_x of every atom, then v_y, then v_z;
+                              read out per component, averaged over atoms */
+
+/* Pair evaluation. */
+#define MD_PAIR_VERLET 0 /* Verlet neighbour lists built from link cells,
+                            rebuilt when an atom has moved skin/2 */
+#define MD_PAIR_CELLS 1  /* direct link-cell evaluation every step */
+
+/* Multiple-tau parameters of one correlator (Sec. 2.2: b blocks of p points
+ * with block averages of m samples; u = update interval in MD steps).
+ * p must be a multiple of m, 2 <= p <= 64, 1 <= b <= 32, m >= 1.  u = 0
+ * disables the correlator. */
+typedef struct {
+  int32_t b, p, m, u;
+} corr_spec;
+
+typedef struct {
+  int64_t n;          /* atoms, >= 2 */
+  double box;         /* edge of the periodic cubic box */
+  double eps, sigma;  /* Lennard-Jones parameters */
+  double rc;          /* cutoff radius; box >= 3 (rc + skin) */
+  int32_t shift;      /* 1: energy-shifted potential (U(rc) subtracted) */
+  int32_t ntypes;     /* 1..8 atom types (mass only) */
+  double mass[8];     /* mass of each type */
+  double dt;          /* time step */
+  int32_t precision;  /* MD_PREC_FP64 or MD_PREC_MIXED */
+  int32_t pair_mode;  /* MD_PAIR_VERLET or MD_PAIR_CELLS */
+  double skin;        /* Verlet skin (MD_PAIR_VERLET); 0 rebuilds every step */
+  int32_t max_neighbors; /* neighbour-list capacity per atom; 0 = automatic */
+  int32_t use_graph;  /* 1: md_step replays a captured CUDA graph of a step */
+  corr_spec stress, heatflux, vacf; /* the three correlators of Sec. 2.3/2.7 */
+} md_params;
+
+typedef struct {
+  const double *r;     /* [3][n] positions (wrapped into the box by md_init) */
+  const double *v;     /* [3][n] velocities */
+  const int32_t *type; /* [n] type of each atom, or NULL for all type 0 */
+  int32_t mem;         /* MD_MEM_HOST or MD_MEM_DEVICE for the three arrays */
+} md_system;
+
+/* Observables of the last completed step (Sec. 2.3). */
+typedef struct {
+  int64_t step;        /* steps completed since md_init */
+  double U, K, T;      /* potential and kinetic energy, T = 2K/(3n-3) */
+  double sigma[6];     /* pressure tensor: (sum m v v + sum_i W_i) / V */
+  double q[3];         /* heat flux: sum_i (E_i v_i + W_i v_i) / V */
+  double T_mean;       /* mean of T over the steps since md_init */
+} md_obs;
+
+typedef struct md_handle_s md_handle;
+typedef struct corr_handle_s corr_handle;
+
+/* Creates a system: copies r, v, type, builds the cell-sorted layout,
+ * evaluates forces, per-particle energies and virials at t = 0 and the
+ * observables (no correlator sample is taken at t = 0).  Link cells of edge
+ * >= rc + skin (Sec. 1 "linked cells").  Errors: MD_EINVAL for bad
+ * parameters (including fewer than 3 cells per side), MD_ENOMEM, MD_ECUDA,
+ * MD_ESTATE for non-finite input. */
+OTF_API int md_init(const md_params *p, const md_system *s, void *cuda_stream, md_handle **out);
+
+/* Advances nsteps velocity-Verlet NVE steps (Sec. 1).  Each step: half
+ * kick and drift; neighbour-list rebuild when needed; pair forces with
+ * per-particle energy and virial; half kick; reduction to U, K, sigma, q;
+ * correlator samples of the stress and heat flux every stress.u /
+ * heatflux.u steps and of every atom's velocity every vacf.u steps
+ * (Algorithm 1).  Everything stays on the device.  Synchronises the stream
+ * at the end and returns MD_ESTATE if a device check failed (the state is
+ * then undefined). */
+OTF_API int md_step(md_handle *h, int64_t nsteps);
+
+/* Observables of the last step (synchronises). */
+OTF_API int md_observables(md_handle *h, md_obs *out);
+
+/* Per-particle state in the caller's atom order: positions (wrapped into
+ * [0, box)), velocities, forces, potential energies [n] and virials [6][n]
+ * (W_i = 1/2 sum_j r_ij (x) f_ij).  Any pointer may be NULL.  mem says where
+ * the outputs live.  Synchronises. */
+OTF_API int md_get_particles(md_handle *h, double *r, double *v, double *F, double *epot,
+                     double *W, int32_t mem);
+
+/* Multiplies every velocity by lambda (velocity-rescaling equilibration;
+ * not part of the correlated run) and refreshes the observables. */
+OTF_API int md_scale_velocities(md_handle *h, double lambda);
+
+/* Clears the correlators and the running temperature mean of a system, so
+ * that a production run can start after equilibration. */
+OTF_API int md_reset_correlators(md_handle *h);
+
+/* Borrowed view of a correlator of the system (MD_CORR_*); valid until
+ * md_free; do not pass it to corr_free or corr_push. */
+OTF_API int md_corr(md_handle *h, int32_t which, corr_handle **out);
+
+/* Kernel classes timed by md_set_timing / md_kernel_times. */
+#define MD_K_INTEGRATE 0 /* half kick + drift + skin check */
+#define MD_K_REBUILD 1   /* cell counting sort + neighbour-list build */
+#define MD_K_PAIR 2      /* pair forces, per-particle energy and virial */
+#define MD_K_REDUCE 3    /* half kick + stress / heat-flux reduction + their
+                            correlator samples */
+#define MD_K_VACF 4      /* per-atom velocity correlator sample */
+#define MD_NKCLASS 5
+
+/* on = 1: the following md_step calls launch every kernel directly (no graph)
+ * between CUDA events on the system's stream and add each kernel class's
+ * device time to counters; on = 0 stops that.  Enabling clears the
+ * counters. */
+OTF_API int md_set_timing(md_handle *h, int32_t on);
+
+/* Accumulated device milliseconds [MD_NKCLASS] and launches [MD_NKCLASS]
+ * per kernel class since timing was enabled (host arrays). */
+OTF_API int md_kernel_times(md_handle *h, double *ms, int64_t *launches);
+
+OTF_API void md_free(md_handle *h);
+
+/* A free-standing correlator over nseries series pushed in lockstep
+ * (Sec. 2.2 "any pair of observables can be correlated").  Series are split
+ * into contiguous groups of group_size; a group's readout is the mean of its
+ * series' correlations.  cross = 0: autocorrelation of x; cross = 1: x
+ * with y.  precision: MD_PREC_FP64 (FP64 ring and products) or
+ * MD_PREC_MIXED (FP32 ring and products, FP64 lag sums).  dt_unit: time
+ * between two pushes (readout times are lag * m^(k-1) * dt_unit). */
+typedef struct {
+  int32_t b, p, m;
+  int32_t cross;
+  int64_t nseries;
+  int64_t group_size;
+  int32_t precision;
+  double dt_unit;
+} corr_params;
+
+OTF_API int corr_create(const corr_params *cp, void *cuda_stream, corr_handle **out);
+
+/* One sample per series (Algorithm 1 applied to every series): x [nseries]
+ * and, for cross correlators, y [nseries]; FP64, in host or device memory
+ * (mem).  Host input is copied before the call returns. */
+OTF_API int corr_push(corr_handle *c, const double *x, const double *y, int64_t nseries, int32_t mem);
+
+/* Readout of group g (Algorithm 2), or of the mean over all groups when
+ * g = -1: writes up to cap (time, value) points to host arrays and the
+ * number of points to *n; MD_ECAP (with *n set) when cap is too small.
+ * Synchronises. */
+OTF_API int corr_read(corr_handle *c, int64_t g, double *times, double *values, int64_t cap, int64_t *n);
+
+/* Raw lag sums [ngroups][b][p] (sums over each group's series), product
+ * counts per series [b][p] and the number of blocks used (host arrays). */
+OTF_API int corr_raw(corr_handle *c, double *values, int64_t *count, int32_t *blocks_used);
+
+/* Number of samples pushed so far. */
+OTF_API int corr_pushes(corr_handle *c, int64_t *n);
+
+OTF_API int corr_reset(corr_handle *c);
+OTF_API void corr_free(corr_handle *c);
+
+/* Green-Kubo integral (Sec. 2.3 Eqs. (visc), (therm)): prefactor times the
+ * integral of the piecewise-linear interpolant of (t[i], c[i]) from t[0] to
+ * min(t_cut, t[n-1]) (trapezoid rule).  running (nullable, [n]) receives
+ * prefactor times the integral from t[0] to t[i].  Host arrays; t must be
+ * strictly increasing.  Viscosity: prefactor V / (kB T); conductivity with
+ * c = <q(t).q(0)>: V / (3 kB T^2). */
+OTF_API int gk_integrate(const double *t, const double *c, int64_t n, double t_cut, double prefactor,
+                 double *integral, double *running);
+
+/* Message of the last failed call on this thread ("" if none). */
+OTF_API const char *md_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OTF_MD_H */

@@ -1,0 +1,27 @@
+"""GB300-native on-the-fly property library (arXiv 2503.07526).
+
+Lennard-Jones MD on one GPU with the system stress tensor, heat flux and
+multiple-tau correlators (stress, heat flux, per-atom velocity) computed
+while the simulation runs, plus Green-Kubo integrals.  The compute lives in
+``libotfmd.so`` (C ABI in ``include/otf_md.h``); this package only marshals
+arguments.
+"""
+from ._lib import (  # noqa: F401
+    EXPORTS,
+    MD_CORR_HEATFLUX,
+    MD_CORR_STRESS,
+    MD_CORR_VACF,
+    MD_K_NAMES,
+    MD_MEM_DEVICE,
+    MD_MEM_HOST,
+    MD_PAIR_CELLS,
+    MD_PAIR_VERLET,
+    MD_PREC_FP64,
+    MD_PREC_MIXED,
+    Corr,
+    MdError,
+    System,
+    gk_integrate,
+    lib,
+    make_params,
+)

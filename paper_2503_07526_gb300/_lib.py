@@ -1,0 +1,324 @@
+"""ctypes binding of ``include/otf_md.h`` (argument marshalling only).
+
+Every computation runs in ``libotfmd.so``.  If the library is missing the
+import fails loudly: there is no CPU fallback.  Arrays may be numpy arrays
+(host memory) or CUDA torch tensors (device memory); streams are torch
+streams or raw ``cudaStream_t`` integers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build_lib
+
+MD_OK, MD_EINVAL, MD_ENOMEM, MD_ECUDA, MD_ESTATE, MD_ETIMEOUT, MD_ECAP = 0, -1, -2, -3, -4, -5, -6
+MD_PREC_FP64, MD_PREC_MIXED = 0, 1
+MD_MEM_HOST, MD_MEM_DEVICE = 0, 1
+MD_CORR_STRESS, MD_CORR_HEATFLUX, MD_CORR_VACF = 0, 1, 2
+MD_PAIR_VERLET, MD_PAIR_CELLS = 0, 1
+MD_K_NAMES = ("integrate", "rebuild", "pair", "reduce", "vacf")
+MD_NKCLASS = 5
+
+_ERRNAMES = {MD_EINVAL: "MD_EINVAL", MD_ENOMEM: "MD_ENOMEM", MD_ECUDA: "MD_ECUDA", MD_ESTATE: "MD_ESTATE",
+             MD_ETIMEOUT: "MD_ETIMEOUT", MD_ECAP: "MD_ECAP"}
+
+
+class MdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class corr_spec(C.Structure):
+    _fields_ = [("b", C.c_int32), ("p", C.c_int32), ("m", C.c_int32), ("u", C.c_int32)]
+
+
+class md_params(C.Structure):
+    _fields_ = [("n", C.c_int64), ("box", C.c_double), ("eps", C.c_double), ("sigma", C.c_double),
+                ("rc", C.c_double), ("shift", C.c_int32), ("ntypes", C.c_int32), ("mass", C.c_double * 8),
+                ("dt", C.c_double), ("precision", C.c_int32), ("pair_mode", C.c_int32), ("skin", C.c_double),
+                ("max_neighbors", C.c_int32), ("use_graph", C.c_int32), ("stress", corr_spec),
+                ("heatflux", corr_spec), ("vacf", corr_spec)]
+
+
+class md_system(C.Structure):
+    _fields_ = [("r", C.c_void_p), ("v", C.c_void_p), ("type", C.c_void_p), ("mem", C.c_int32)]
+
+
+class md_obs(C.Structure):
+    _fields_ = [("step", C.c_int64), ("U", C.c_double), ("K", C.c_double), ("T", C.c_double),
+                ("sigma", C.c_double * 6), ("q", C.c_double * 3), ("T_mean", C.c_double)]
+
+
+class corr_params(C.Structure):
+    _fields_ = [("b", C.c_int32), ("p", C.c_int32), ("m", C.c_int32), ("cross", C.c_int32),
+                ("nseries", C.c_int64), ("group_size", C.c_int64), ("precision", C.c_int32),
+                ("dt_unit", C.c_double)]
+
+
+_lib = None
+
+
+def lib(build: bool = False):
+    """The loaded ``libotfmd.so`` (built first when ``build`` is set)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = build_lib.build() if build else build_lib.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with __graft_entry__.build() or "
+                          "python -m paper_2503_07526_gb300.build_lib")
+    L = C.CDLL(path)
+    vp, i64, i32, dp = C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_double)
+    sig = {
+        "md_init": [C.POINTER(md_params), C.POINTER(md_system), vp, C.POINTER(vp)],
+        "md_step": [vp, i64],
+        "md_observables": [vp, C.POINTER(md_obs)],
+        "md_get_particles": [vp, vp, vp, vp, vp, vp, i32],
+        "md_scale_velocities": [vp, C.c_double],
+        "md_reset_correlators": [vp],
+        "md_corr": [vp, i32, C.POINTER(vp)],
+        "md_set_timing": [vp, i32],
+        "md_kernel_times": [vp, dp, C.POINTER(C.c_int64)],
+        "corr_create": [C.POINTER(corr_params), vp, C.POINTER(vp)],
+        "corr_push": [vp, vp, vp, i64, i32],
+        "corr_read": [vp, i64, dp, dp, i64, C.POINTER(C.c_int64)],
+        "corr_raw": [vp, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)],
+        "corr_pushes": [vp, C.POINTER(C.c_int64)],
+        "corr_reset": [vp],
+        "gk_integrate": [dp, dp, i64, C.c_double, C.c_double, dp, dp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    L.md_free.argtypes = [vp]
+    L.md_free.restype = None
+    L.corr_free.argtypes = [vp]
+    L.corr_free.restype = None
+    L.md_last_error.argtypes = []
+    L.md_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+EXPORTS = ("md_init", "md_step", "md_observables", "md_get_particles", "md_scale_velocities",
+           "md_reset_correlators", "md_corr", "md_set_timing", "md_kernel_times", "md_free", "corr_create",
+           "corr_push", "corr_read", "corr_raw", "corr_pushes", "corr_reset", "corr_free", "gk_integrate",
+           "md_last_error")
+
+
+def _check(rc):
+    if rc != MD_OK:
+        raise MdError(rc, lib().md_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(a, dtype, mem_hint=None):
+    """(pointer, mem flag, keep-alive) of a numpy array or CUDA torch tensor."""
+    try:
+        import torch
+
+        if isinstance(a, torch.Tensor):
+            if a.dtype != dtype["torch"]:
+                raise TypeError(f"expected {dtype['torch']}, got {a.dtype}")
+            if not a.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return a.data_ptr(), (MD_MEM_DEVICE if a.is_cuda else MD_MEM_HOST), a
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(a, dtype=dtype["np"])
+    return arr.ctypes.data, MD_MEM_HOST, arr
+
+
+F64 = {"np": np.float64, "torch": None}
+I32 = {"np": np.int32, "torch": None}
+
+
+def _init_dtypes():
+    try:
+        import torch
+
+        F64["torch"] = torch.float64
+        I32["torch"] = torch.int32
+    except ImportError:
+        pass
+
+
+_init_dtypes()
+
+
+def make_params(n, box, *, eps=1.0, sigma=1.0, rc=2.5, shift=True, masses=(1.0,), dt=0.005,
+                precision=MD_PREC_FP64, pair_mode=MD_PAIR_VERLET, skin=0.3, max_neighbors=0, use_graph=True,
+                stress=(12, 16, 2, 1), heatflux=(12, 16, 2, 1), vacf=(8, 16, 2, 1)):
+    p = md_params()
+    p.n, p.box, p.eps, p.sigma, p.rc, p.shift = int(n), float(box), eps, sigma, rc, int(bool(shift))
+    p.ntypes = len(masses)
+    for t, m in enumerate(masses):
+        p.mass[t] = float(m)
+    p.dt, p.precision, p.pair_mode, p.skin = dt, int(precision), int(pair_mode), float(skin)
+    p.max_neighbors, p.use_graph = int(max_neighbors), int(bool(use_graph))
+    for name, spec in (("stress", stress), ("heatflux", heatflux), ("vacf", vacf)):
+        cs = getattr(p, name)
+        cs.b, cs.p, cs.m, cs.u = spec if spec is not None else (1, 2, 1, 0)
+    return p
+
+
+class Corr:
+    """A correlator handle (free-standing or borrowed from a System)."""
+
+    def __init__(self, handle, owned, nseries, ngroups, cross, b, p, keep=None):
+        self._h, self._owned, self.nseries, self.ngroups, self.cross = handle, owned, nseries, ngroups, cross
+        self.b, self.p = b, p
+        self._keep = keep
+
+    @classmethod
+    def create(cls, b, p, m, nseries, group_size=1, cross=False, precision=MD_PREC_FP64, dt_unit=1.0,
+               stream=None):
+        cp = corr_params(b, p, m, int(bool(cross)), nseries, group_size, precision, dt_unit)
+        h = C.c_void_p()
+        _check(lib().corr_create(C.byref(cp), _stream_ptr(stream), C.byref(h)))
+        return cls(h, True, nseries, nseries // group_size, bool(cross), b, p)
+
+    def push(self, x, y=None):
+        px, mem, kx = _ptr(x, F64)
+        py, ky = None, None
+        if self.cross:
+            py, memy, ky = _ptr(y, F64)
+            if memy != mem:
+                raise ValueError("x and y must live in the same memory")
+        _check(lib().corr_push(self._h, px, py, self.nseries, mem))
+
+    def read(self, group=-1):
+        cap = self.b * self.p
+        t = np.zeros(cap)
+        v = np.zeros(cap)
+        n = C.c_int64(0)
+        dp = C.POINTER(C.c_double)
+        _check(lib().corr_read(self._h, group, t.ctypes.data_as(dp), v.ctypes.data_as(dp), cap, C.byref(n)))
+        return t[: n.value].copy(), v[: n.value].copy()
+
+    def raw(self):
+        vals = np.zeros((self.ngroups, self.b, self.p))
+        cnt = np.zeros((self.b, self.p), dtype=np.int64)
+        used = C.c_int32(0)
+        _check(lib().corr_raw(self._h, vals.ctypes.data_as(C.POINTER(C.c_double)),
+                              cnt.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(used)))
+        return vals, cnt, used.value
+
+    def pushes(self):
+        n = C.c_int64(0)
+        _check(lib().corr_pushes(self._h, C.byref(n)))
+        return n.value
+
+    def reset(self):
+        _check(lib().corr_reset(self._h))
+
+    def close(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h and self._owned and _lib is not None:
+            _lib.corr_free(h)
+
+    __del__ = close
+
+
+class System:
+    """An MD system on the GPU behind md_init / md_step / md_free."""
+
+    def __init__(self, params: md_params, r, v, types=None, stream=None):
+        self.params = params
+        self.n = params.n
+        pr, mem, kr = _ptr(r, F64)
+        pv, memv, kv = _ptr(v, F64)
+        pt, kt = None, None
+        if types is not None:
+            pt, memt, kt = _ptr(types, I32)
+            if memt != mem:
+                raise ValueError("r, v and types must live in the same memory")
+        if memv != mem:
+            raise ValueError("r and v must live in the same memory")
+        sysd = md_system(pr, pv, pt, mem)
+        h = C.c_void_p()
+        self.stream = _stream_ptr(stream)
+        _check(lib().md_init(C.byref(params), C.byref(sysd), self.stream, C.byref(h)))
+        self._h = h
+
+    def step(self, nsteps):
+        _check(lib().md_step(self._h, int(nsteps)))
+
+    def observables(self):
+        o = md_obs()
+        _check(lib().md_observables(self._h, C.byref(o)))
+        return dict(step=o.step, U=o.U, K=o.K, T=o.T, sigma=np.array(o.sigma[:]), q=np.array(o.q[:]),
+                    T_mean=o.T_mean)
+
+    def particles(self):
+        n = self.n
+        r, v, F = np.zeros((3, n)), np.zeros((3, n)), np.zeros((3, n))
+        e, W = np.zeros(n), np.zeros((6, n))
+        _check(lib().md_get_particles(self._h, r.ctypes.data, v.ctypes.data, F.ctypes.data, e.ctypes.data,
+                                      W.ctypes.data, MD_MEM_HOST))
+        return dict(r=r, v=v, F=F, epot=e, W=W)
+
+    def particles_device(self, r=None, v=None, F=None, epot=None, W=None):
+        ptr = lambda t: None if t is None else t.data_ptr()
+        _check(lib().md_get_particles(self._h, ptr(r), ptr(v), ptr(F), ptr(epot), ptr(W), MD_MEM_DEVICE))
+
+    def scale_velocities(self, lam):
+        _check(lib().md_scale_velocities(self._h, float(lam)))
+
+    def reset_correlators(self):
+        _check(lib().md_reset_correlators(self._h))
+
+    def corr(self, which):
+        h = C.c_void_p()
+        _check(lib().md_corr(self._h, int(which), C.byref(h)))
+        spec = (self.params.stress, self.params.heatflux, self.params.vacf)[which]
+        ns, ng = (3 * self.n, 3) if which == MD_CORR_VACF else (3, 3)
+        return Corr(h, False, ns, ng, False, spec.b, spec.p, keep=self)
+
+    def set_timing(self, on=True):
+        _check(lib().md_set_timing(self._h, int(bool(on))))
+
+    def kernel_times(self):
+        ms = np.zeros(MD_NKCLASS)
+        nl = np.zeros(MD_NKCLASS, dtype=np.int64)
+        _check(lib().md_kernel_times(self._h, ms.ctypes.data_as(C.POINTER(C.c_double)),
+                                     nl.ctypes.data_as(C.POINTER(C.c_int64))))
+        return {k: (float(ms[i]), int(nl[i])) for i, k in enumerate(MD_K_NAMES)}
+
+    def close(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h and _lib is not None:
+            _lib.md_free(h)
+
+    __del__ = close
+
+
+def gk_integrate(t, c, t_cut=float("inf"), prefactor=1.0):
+    """(integral, running integral) by the library's trapezoid rule."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    run = np.zeros(t.size)
+    out = C.c_double(0.0)
+    dp = C.POINTER(C.c_double)
+    _check(lib().gk_integrate(t.ctypes.data_as(dp), c.ctypes.data_as(dp), t.size, float(t_cut), float(prefactor),
+                              C.byref(out), run.ctypes.data_as(dp)))
+    return out.value, run

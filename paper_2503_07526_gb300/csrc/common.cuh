@@ -1,0 +1,93 @@
+// Internal helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "otf_md.h"
+
+namespace otf {
+
+// Per-thread error message behind md_last_error().
+void set_error(const char *fmt, ...);
+void clear_error();
+
+// Device-side error bits, OR-ed into a status word by kernels and turned
+// into MD_ESTATE by the host.
+enum : unsigned {
+  ERR_NONFINITE = 1u,      // a coordinate or velocity became NaN / Inf
+  ERR_NBR_OVERFLOW = 2u,   // an atom has more neighbours than the list holds
+  ERR_BAD_TYPE = 4u,       // an atom type outside [0, ntypes)
+};
+
+#define OTF_CUDA(call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) {                                                                 \
+      otf::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,      \
+                     __LINE__);                                                              \
+      return e_ == cudaErrorMemoryAllocation ? MD_ENOMEM : MD_ECUDA;                         \
+    }                                                                                        \
+  } while (0)
+
+#define OTF_LAUNCH_CHECK()                                                                   \
+  do {                                                                                       \
+    cudaError_t e_ = cudaGetLastError();                                                     \
+    if (e_ != cudaSuccess) {                                                                 \
+      otf::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_), __FILE__,  \
+                     __LINE__);                                                              \
+      return MD_ECUDA;                                                                       \
+    }                                                                                        \
+  } while (0)
+
+constexpr int kWarp = 32;
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Four-wide position record (x, y, z, unused) in the arithmetic type of the
+// pair path: float4 in the mixed form, two 16-byte halves in FP64.
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  using type = float4;
+  __device__ __forceinline__ static float4 load(const float4 *p) { return __ldg(p); }
+  __device__ __forceinline__ static void store(float4 *p, float x, float y, float z) {
+    *p = make_float4(x, y, z, 0.f);
+  }
+};
+struct alignas(16) dvec4 {
+  double x, y, z, w;
+};
+template <>
+struct Vec4<double> {
+  using type = dvec4;
+  __device__ __forceinline__ static dvec4 load(const dvec4 *p) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    double2 a = __ldg(q), b = __ldg(q + 1);
+    return dvec4{a.x, a.y, b.x, b.y};
+  }
+  __device__ __forceinline__ static void store(dvec4 *p, double x, double y, double z) {
+    double2 *q = reinterpret_cast<double2 *>(p);
+    q[0] = make_double2(x, y);
+    q[1] = make_double2(z, 0.0);
+  }
+};
+
+__device__ __forceinline__ float fast_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace otf

@@ -1,0 +1,445 @@
+// Multiple-tau correlator kernels and the corr_* C ABI
+// (arXiv 2503.07526, Sec. 2.2; Appendix D Algorithms 1 and 2).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "corr.cuh"
+
+namespace otf {
+
+namespace {
+
+constexpr int kPushThreads = 256;
+constexpr int kPushWarps = kPushThreads / kWarp;
+
+// Per-series correlators: one thread runs Algorithm 1 for one series.
+template <typename T, typename Tin>
+__global__ void k_push_series(CorrDev c, const Tin *__restrict__ x, const Tin *__restrict__ y,
+                              PushIdx pi) {
+  int64_t t;
+  if (!resolve_push(pi, &t)) return;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < c.ns;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const T xv = (T)x[s];
+    const T yv = c.cross ? (T)y[s] : xv;
+    push_one_series<T>(c, s, xv, yv, t);
+  }
+}
+
+// Grouped correlators (e.g. the per-atom velocity autocorrelation): block
+// (cx, g) owns a fixed slice of group g's series; per block, each block
+// touched by the push streams its ring planes once, forms the lag products
+// in registers (A = accumulation type: float in the mixed form, double in
+// FP64), reduces them over the CTA with warp shuffles and adds the FP64 sum
+// into its own row of partial lag sums (no atomics: deterministic).
+template <typename T, typename Tin, int PMAX>
+__global__ void __launch_bounds__(kPushThreads)
+    k_push_grouped(CorrDev c, const Tin *__restrict__ x, const Tin *__restrict__ y, PushIdx pi) {
+  int64_t t;
+  if (!resolve_push(pi, &t)) return;
+  __shared__ double red[kPushWarps][PMAX];
+  const int g = blockIdx.y, cx = blockIdx.x;
+  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x / kWarp;
+  const int64_t base = (int64_t)g * c.gs;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t plane = c.ns;
+  T *rx = static_cast<T *>(c.ringx);
+  T *ry = c.cross ? static_cast<T *>(c.ringy) : rx;
+  int64_t Mk = 1;
+  for (int k = 0; k < c.b; ++k) {
+    if (k > 0) {
+      Mk *= c.m;
+      if (t % Mk) break;
+    }
+    const int64_t nk = t / Mk;
+    const int slot = (int)((nk - 1) % c.p);
+    const int lo = (k == 0) ? 0 : c.p / c.m;
+    const int nl = (int)min((int64_t)c.p - 1, nk - 1) - lo + 1;
+    T *rxk = rx + (int64_t)k * c.p * plane;
+    T *ryk = ry + (int64_t)k * c.p * plane;
+    T acc[PMAX];
+#pragma unroll
+    for (int l = 0; l < PMAX; ++l) acc[l] = T(0);
+    int jl[PMAX];
+#pragma unroll
+    for (int l = 0; l < PMAX; ++l) {
+      int j = slot - lo - l;
+      if (j < 0) j += c.p;
+      jl[l] = j;
+    }
+    for (int64_t i = cx * (int64_t)blockDim.x + threadIdx.x; i < c.gs; i += stride) {
+      const int64_t s = base + i;
+      T xk, yk;
+      if (k == 0) {
+        xk = (T)x[s];
+        yk = c.cross ? (T)y[s] : xk;
+      } else {
+        const int64_t nprev = nk * c.m;
+        const T *rp = rx + (int64_t)(k - 1) * c.p * plane;
+        const T *rq = ry + (int64_t)(k - 1) * c.p * plane;
+        T sx = T(0), sy = T(0);
+        for (int j = c.m - 1; j >= 0; --j) {
+          const int sl = (int)((nprev - 1 - j) % c.p);
+          sx += rp[sl * plane + s];
+          if (c.cross) sy += rq[sl * plane + s];
+        }
+        xk = sx / T(c.m);
+        yk = c.cross ? sy / T(c.m) : xk;
+      }
+      rxk[slot * plane + s] = xk;
+      if (c.cross) ryk[slot * plane + s] = yk;
+#pragma unroll
+      for (int l = 0; l < PMAX; ++l) {
+        if (l < nl) {
+          const T older = (lo + l == 0) ? xk : rxk[jl[l] * plane + s];
+          acc[l] += older * yk;
+        }
+      }
+    }
+    if (nl <= 0) continue;  // uniform over the grid
+#pragma unroll
+    for (int l = 0; l < PMAX; ++l) {
+      if (l < nl) {
+        const T v = warp_sum(acc[l]);
+        if (lane == 0) red[warp][l] = (double)v;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < nl) {
+      double s = 0.0;
+      for (int w = 0; w < kPushWarps; ++w) s += red[w][threadIdx.x];
+      c.vals[(((int64_t)g * c.nchunk + cx) * c.b + k) * c.p + lo + threadIdx.x] += s;
+    }
+    __syncthreads();
+  }
+}
+
+// Sums the per-block partial lag sums of each group in a fixed order.
+__global__ void k_fold(CorrDev c, double *__restrict__ out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)c.b * c.p;
+  if (e >= c.ng * per) return;
+  const int64_t g = e / per, kl = e % per;
+  double s = 0.0;
+  for (int cx = 0; cx < c.nchunk; ++cx) s += c.vals[(g * c.nchunk + cx) * per + kl];
+  out[e] = s;
+}
+
+template <typename T, typename Tin>
+int launch_grouped(const CorrDev &c, const Tin *x, const Tin *y, PushIdx pi, cudaStream_t s) {
+  dim3 grid(c.nchunk, (unsigned)c.ng);
+  if (c.p <= 16)
+    k_push_grouped<T, Tin, 16><<<grid, kPushThreads, 0, s>>>(c, x, y, pi);
+  else if (c.p <= 32)
+    k_push_grouped<T, Tin, 32><<<grid, kPushThreads, 0, s>>>(c, x, y, pi);
+  else
+    k_push_grouped<T, Tin, 64><<<grid, kPushThreads, 0, s>>>(c, x, y, pi);
+  OTF_LAUNCH_CHECK();
+  return MD_OK;
+}
+
+template <typename T, typename Tin>
+int launch_series(const CorrDev &c, const Tin *x, const Tin *y, PushIdx pi, cudaStream_t s) {
+  int blocks = std::max(1, std::min(ceil_div(c.ns, 128), 152 * 8));
+  k_push_series<T, Tin><<<blocks, 128, 0, s>>>(c, x, y, pi);
+  OTF_LAUNCH_CHECK();
+  return MD_OK;
+}
+
+}  // namespace
+
+int validate_corr_params(const corr_params &p) {
+  if (p.b < 1 || p.b > 32 || p.p < 2 || p.p > 64 || p.m < 1 || p.m > p.p || p.p % p.m != 0) {
+    set_error("correlator needs 1 <= b <= 32, 2 <= p <= 64, 1 <= m <= p, m | p (got b=%d p=%d m=%d)",
+              p.b, p.p, p.m);
+    return MD_EINVAL;
+  }
+  if (p.nseries < 1 || p.group_size < 1 || p.nseries % p.group_size != 0) {
+    set_error("nseries must be a positive multiple of group_size");
+    return MD_EINVAL;
+  }
+  if (p.precision != MD_PREC_FP64 && p.precision != MD_PREC_MIXED) {
+    set_error("unknown precision %d", p.precision);
+    return MD_EINVAL;
+  }
+  if (!(p.dt_unit > 0.0)) {
+    set_error("dt_unit must be positive");
+    return MD_EINVAL;
+  }
+  return MD_OK;
+}
+
+int Correlator::create(const corr_params &p, cudaStream_t s) {
+  int rc = validate_corr_params(p);
+  if (rc) return rc;
+  prm = p;
+  prec = p.precision;
+  stream = s;
+  grouped = p.group_size > 1;
+  dev.b = p.b;
+  dev.p = p.p;
+  dev.m = p.m;
+  dev.cross = p.cross ? 1 : 0;
+  dev.ns = p.nseries;
+  dev.gs = p.group_size;
+  dev.ng = p.nseries / p.group_size;
+  if (grouped) {
+    const int64_t target = 152 * 8;  // resident CTAs of 256 threads on 152 SMs
+    int64_t per_group = std::max<int64_t>(1, target / dev.ng);
+    dev.nchunk = (int)std::max<int64_t>(1, std::min<int64_t>(per_group, (dev.gs + kPushThreads - 1) / kPushThreads));
+  } else {
+    dev.nchunk = 1;
+  }
+  const size_t esz = prec == MD_PREC_FP64 ? sizeof(double) : sizeof(float);
+  const size_t ring = (size_t)p.b * p.p * p.nseries * esz;
+  OTF_CUDA(cudaMalloc(&dev.ringx, ring));
+  if (dev.cross) OTF_CUDA(cudaMalloc(&dev.ringy, ring));
+  const size_t nvals = grouped ? (size_t)dev.ng * dev.nchunk * p.b * p.p : (size_t)p.nseries * p.b * p.p;
+  OTF_CUDA(cudaMalloc(&dev.vals, nvals * sizeof(double)));
+  OTF_CUDA(cudaMalloc(&d_fold, (size_t)dev.ng * p.b * p.p * sizeof(double)));
+  return reset();
+}
+
+int Correlator::reset() {
+  const size_t esz = prec == MD_PREC_FP64 ? sizeof(double) : sizeof(float);
+  const size_t ring = (size_t)prm.b * prm.p * prm.nseries * esz;
+  const size_t nvals = grouped ? (size_t)dev.ng * dev.nchunk * prm.b * prm.p : (size_t)prm.nseries * prm.b * prm.p;
+  OTF_CUDA(cudaMemsetAsync(dev.ringx, 0, ring, stream));
+  if (dev.cross) OTF_CUDA(cudaMemsetAsync(dev.ringy, 0, ring, stream));
+  OTF_CUDA(cudaMemsetAsync(dev.vals, 0, nvals * sizeof(double), stream));
+  pushes = 0;
+  return MD_OK;
+}
+
+void Correlator::destroy() {
+  cudaFree(dev.ringx);
+  if (dev.ringy) cudaFree(dev.ringy);
+  cudaFree(dev.vals);
+  cudaFree(d_fold);
+  cudaFree(d_in);
+  dev.ringx = dev.ringy = nullptr;
+  dev.vals = d_fold = d_in = nullptr;
+}
+
+int Correlator::launch_push(const void *x, const void *y, bool input_fp32, PushIdx pi, cudaStream_t s) {
+  const bool fp64 = prec == MD_PREC_FP64;
+  if (grouped) {
+    if (fp64) {
+      if (input_fp32) return launch_grouped<double, float>(dev, (const float *)x, (const float *)y, pi, s);
+      return launch_grouped<double, double>(dev, (const double *)x, (const double *)y, pi, s);
+    }
+    if (input_fp32) return launch_grouped<float, float>(dev, (const float *)x, (const float *)y, pi, s);
+    return launch_grouped<float, double>(dev, (const double *)x, (const double *)y, pi, s);
+  }
+  if (fp64) {
+    if (input_fp32) return launch_series<double, float>(dev, (const float *)x, (const float *)y, pi, s);
+    return launch_series<double, double>(dev, (const double *)x, (const double *)y, pi, s);
+  }
+  if (input_fp32) return launch_series<float, float>(dev, (const float *)x, (const float *)y, pi, s);
+  return launch_series<float, double>(dev, (const double *)x, (const double *)y, pi, s);
+}
+
+int Correlator::fetch(double *vals_host) {
+  const size_t n = (size_t)dev.ng * prm.b * prm.p;
+  const double *src = dev.vals;
+  if (grouped) {
+    k_fold<<<ceil_div((int64_t)n, 256), 256, 0, stream>>>(dev, d_fold);
+    OTF_LAUNCH_CHECK();
+    src = d_fold;
+  }
+  OTF_CUDA(cudaMemcpyAsync(vals_host, src, n * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  OTF_CUDA(cudaStreamSynchronize(stream));
+  return MD_OK;
+}
+
+}  // namespace otf
+
+using otf::Correlator;
+using otf::set_error;
+
+namespace {
+
+// Products per series at each (block, lag) after t pushes, and blocks used.
+void counts_from_pushes(const corr_params &p, int64_t t, std::vector<int64_t> &count, int *used) {
+  count.assign((size_t)p.b * p.p, 0);
+  *used = 0;
+  int64_t Mk = 1;
+  for (int k = 0; k < p.b; ++k) {
+    if (k > 0) Mk *= p.m;
+    const int64_t nk = t / Mk;
+    if (nk < 1) break;
+    *used = k + 1;
+    const int lo = (k == 0) ? 0 : p.p / p.m;
+    for (int lag = lo; lag < p.p; ++lag) count[(size_t)k * p.p + lag] = std::max<int64_t>(0, nk - lag);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int corr_create(const corr_params *cp, void *cuda_stream, corr_handle **out) {
+  otf::clear_error();
+  if (!cp || !out) {
+    set_error("corr_create: null argument");
+    return MD_EINVAL;
+  }
+  *out = nullptr;
+  corr_handle *h = new (std::nothrow) corr_handle;
+  if (!h) return MD_ENOMEM;
+  int rc = h->c.create(*cp, (cudaStream_t)cuda_stream);
+  if (rc) {
+    h->c.destroy();
+    delete h;
+    return rc;
+  }
+  rc = [&]() -> int {
+    OTF_CUDA(cudaMalloc(&h->c.d_in, sizeof(double) * 2 * cp->nseries));
+    return MD_OK;
+  }();
+  if (rc) {
+    h->c.destroy();
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return MD_OK;
+}
+
+int corr_push(corr_handle *h, const double *x, const double *y, int64_t nseries, int32_t mem) {
+  otf::clear_error();
+  if (!h || !x) {
+    set_error("corr_push: null argument");
+    return MD_EINVAL;
+  }
+  Correlator &c = h->c;
+  if (c.borrowed) {
+    set_error("corr_push: this correlator is fed by md_step");
+    return MD_EINVAL;
+  }
+  if (nseries != c.prm.nseries) {
+    set_error("corr_push: %lld series given, correlator has %lld", (long long)nseries,
+              (long long)c.prm.nseries);
+    return MD_EINVAL;
+  }
+  if (c.prm.cross && !y) {
+    set_error("corr_push: cross correlator needs y");
+    return MD_EINVAL;
+  }
+  const double *dx = x, *dy = y;
+  if (mem == MD_MEM_HOST) {
+    OTF_CUDA(cudaMemcpyAsync(c.d_in, x, sizeof(double) * nseries, cudaMemcpyHostToDevice, c.stream));
+    dx = c.d_in;
+    if (c.prm.cross) {
+      OTF_CUDA(cudaMemcpyAsync(c.d_in + nseries, y, sizeof(double) * nseries, cudaMemcpyHostToDevice, c.stream));
+      dy = c.d_in + nseries;
+    }
+    // host buffers may be reused as soon as the call returns
+    OTF_CUDA(cudaStreamSynchronize(c.stream));
+  } else if (mem != MD_MEM_DEVICE) {
+    set_error("corr_push: mem must be MD_MEM_HOST or MD_MEM_DEVICE");
+    return MD_EINVAL;
+  }
+  c.pushes += 1;
+  otf::PushIdx pi{nullptr, nullptr, 1, c.pushes};
+  int rc = c.launch_push(dx, c.prm.cross ? dy : dx, false, pi, c.stream);
+  if (rc) c.pushes -= 1;
+  return rc;
+}
+
+int corr_raw(corr_handle *h, double *values, int64_t *count, int32_t *blocks_used) {
+  otf::clear_error();
+  if (!h) {
+    set_error("corr_raw: null handle");
+    return MD_EINVAL;
+  }
+  Correlator &c = h->c;
+  std::vector<double> v((size_t)c.dev.ng * c.prm.b * c.prm.p);
+  int rc = c.fetch(v.data());
+  if (rc) return rc;
+  std::vector<int64_t> cnt;
+  int used = 0;
+  counts_from_pushes(c.prm, c.push_count(), cnt, &used);
+  if (values) std::memcpy(values, v.data(), sizeof(double) * v.size());
+  if (count) std::memcpy(count, cnt.data(), sizeof(int64_t) * cnt.size());
+  if (blocks_used) *blocks_used = used;
+  return MD_OK;
+}
+
+int corr_read(corr_handle *h, int64_t g, double *times, double *values, int64_t cap, int64_t *n) {
+  otf::clear_error();
+  if (!h || !n) {
+    set_error("corr_read: null argument");
+    return MD_EINVAL;
+  }
+  Correlator &c = h->c;
+  const corr_params &p = c.prm;
+  const int64_t ng = c.dev.ng;
+  if (g < -1 || g >= ng) {
+    set_error("corr_read: group %lld out of range", (long long)g);
+    return MD_EINVAL;
+  }
+  std::vector<double> v((size_t)ng * p.b * p.p);
+  int rc = c.fetch(v.data());
+  if (rc) return rc;
+  std::vector<int64_t> cnt;
+  int used = 0;
+  counts_from_pushes(p, c.push_count(), cnt, &used);
+  // Algorithm 2: block 1 lags 0..p-1, then blocks 2..used lags p/m..p-1.
+  int64_t npts = 0;
+  double scale = 1.0;
+  for (int k = 0; k < used; ++k) {
+    if (k > 0) scale *= p.m;
+    const int lo = (k == 0) ? 0 : p.p / p.m;
+    for (int lag = lo; lag < p.p; ++lag) {
+      const int64_t ct = cnt[(size_t)k * p.p + lag];
+      if (ct <= 0) continue;
+      if (npts < cap && times && values) {
+        double sum = 0.0;
+        if (g >= 0) {
+          sum = v[((size_t)g * p.b + k) * p.p + lag];
+        } else {
+          for (int64_t gg = 0; gg < ng; ++gg) sum += v[((size_t)gg * p.b + k) * p.p + lag];
+          sum /= (double)ng;
+        }
+        times[npts] = lag * scale * p.dt_unit;
+        values[npts] = sum / ((double)ct * (double)p.group_size);
+      }
+      ++npts;
+    }
+  }
+  *n = npts;
+  if (npts > cap) {
+    set_error("corr_read: %lld points need a larger buffer", (long long)npts);
+    return MD_ECAP;
+  }
+  return MD_OK;
+}
+
+int corr_pushes(corr_handle *h, int64_t *n) {
+  if (!h || !n) return MD_EINVAL;
+  *n = h->c.push_count();
+  return MD_OK;
+}
+
+int corr_reset(corr_handle *h) {
+  otf::clear_error();
+  if (!h) return MD_EINVAL;
+  if (h->c.borrowed) {
+    set_error("corr_reset: use md_reset_correlators for a system's correlators");
+    return MD_EINVAL;
+  }
+  return h->c.reset();
+}
+
+void corr_free(corr_handle *h) {
+  if (!h || h->c.borrowed) return;
+  cudaStreamSynchronize(h->c.stream);
+  h->c.destroy();
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,1108 @@
+// Lennard-Jones MD step with on-the-fly stress, heat flux and correlators
+// (arXiv 2503.07526: Sec. 1 linked cells and velocity Verlet; Sec. 2.3
+// Eq. (stress) and the heat-flux definition; Sec. 2.2 correlators).
+//
+// GB300 design.  Atoms live in a cell-sorted structure of arrays that is
+// rebuilt by a counting sort when any atom has moved half the skin.  Each
+// atom also carries its coordinates relative to the origin of the cell it
+// was sorted into, in the arithmetic type of the pair path, so the FP32
+// form never subtracts two large absolute coordinates.  A step is a fixed
+// sequence of kernels (no host decision inside it), so it is captured once
+// as a CUDA graph and replayed; the rebuild kernels read a device flag and
+// return at once when no rebuild is due.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "corr.cuh"
+
+namespace otf {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPairThreads = 128;
+constexpr int kCellWarps = 4;  // warps (cells) per CTA in the link-cell kernels
+constexpr int kNRed = 11;      // K, U, V*sigma[6], V*q[3]
+constexpr int kMaxRedBlocks = 152 * 4;
+
+struct ObsDev {
+  int64_t step;       // steps completed
+  int64_t corr_base;  // step at the last correlator reset
+  int64_t Tn;
+  double U, K, T;
+  double sigma[6];
+  double q[3];
+  double Tsum;
+};
+
+struct Sys {
+  int64_t n, ncell;
+  int nc, ntypes, maxnb, always_rebuild, vacf_u;
+  double L, edge, dt, lim2;
+  double invm[8], mass[8];
+  // cell-sorted state
+  double *r, *v;        // [3][n]
+  void *F, *epot, *W;   // [3][n], [n], [6][n] in the pair type
+  void *rel, *relb;     // Vec4 of the pair type: current / at last rebuild
+  void *vbuf;           // [3][n] velocities in atom-id order (correlator input)
+  int *id, *type, *cpk; // atom id, type, packed cell coordinates
+  // rebuild scratch
+  double *rB, *vB;
+  int *idB, *typeB, *cellB, *slot, *perm, *cellcount, *cellstart;
+  uint32_t *nbr;        // [maxnb][n] neighbour j | (image code << 27)
+  int *nnb;
+  // reductions and flags
+  double *partials;
+  unsigned *counter;
+  ObsDev *obs;
+  int *rebuild;
+  unsigned *err;
+};
+
+template <typename TF>
+struct LJ {
+  TF eps4, eps24, sig2, rc2, ushift, rlist2;
+};
+
+__device__ __forceinline__ int pack_cell(int x, int y, int z) { return x | (y << 10) | (z << 20); }
+__device__ __forceinline__ void unpack_cell(int c, int &x, int &y, int &z) {
+  x = c & 1023;
+  y = (c >> 10) & 1023;
+  z = c >> 20;
+}
+
+// ------------------------------------------------------------ integrate
+
+// First half kick and drift (velocity Verlet), new cell-relative
+// coordinates, and the skin test that decides the next rebuild.
+template <typename TF>
+__global__ void __launch_bounds__(kThreads) k_kick_drift(Sys d, double hdt) {
+  using V4 = typename Vec4<TF>::type;
+  const TF *F = static_cast<const TF *>(d.F);
+  V4 *rel = static_cast<V4 *>(d.rel);
+  const V4 *relb = static_cast<const V4 *>(d.relb);
+  bool over = false, bad = false;
+  const int64_t n = d.n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double h = hdt * d.invm[min(max(d.type[i], 0), 7)];
+    double x[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double va = fma(h, (double)F[a * n + i], d.v[a * n + i]);
+      d.v[a * n + i] = va;
+      x[a] = fma(d.dt, va, d.r[a * n + i]);
+      d.r[a * n + i] = x[a];
+    }
+    int cx, cy, cz;
+    unpack_cell(d.cpk[i], cx, cy, cz);
+    const TF px = (TF)fma(-(double)cx, d.edge, x[0]);
+    const TF py = (TF)fma(-(double)cy, d.edge, x[1]);
+    const TF pz = (TF)fma(-(double)cz, d.edge, x[2]);
+    Vec4<TF>::store(rel + i, px, py, pz);
+    const V4 b = Vec4<TF>::load(relb + i);
+    const TF dx = px - b.x, dy = py - b.y, dz = pz - b.z;
+    over |= (double)(dx * dx + dy * dy + dz * dz) > d.lim2;
+    bad |= !(isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]));
+  }
+  if (__any_sync(0xffffffffu, over || d.always_rebuild) && (threadIdx.x & 31) == 0) *d.rebuild = 1;
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(d.err, ERR_NONFINITE);
+}
+
+// ---------------------------------------------------------------- sort
+
+__global__ void k_rb_zero(Sys d) {
+  if (!*d.rebuild) return;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < d.ncell;
+       c += (int64_t)gridDim.x * blockDim.x)
+    d.cellcount[c] = 0;
+}
+
+// Wraps positions into the box, bins every atom into its cell and takes a
+// provisional slot in it; copies the state aside for the gather.
+__global__ void __launch_bounds__(kThreads) k_rb_assign(Sys d) {
+  if (!*d.rebuild) return;
+  const int64_t n = d.n;
+  const int nc = d.nc;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int ci[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double x = d.r[a * n + i];
+      x -= d.L * floor(x / d.L);
+      if (x >= d.L) x -= d.L;
+      if (x < 0.0) x = 0.0;
+      int c = (int)(x / d.edge);
+      ci[a] = c < nc ? c : nc - 1;
+      d.rB[a * n + i] = x;
+      d.vB[a * n + i] = d.v[a * n + i];
+    }
+    const int t = d.type[i];
+    if (t < 0 || t >= d.ntypes) atomicOr(d.err, ERR_BAD_TYPE);
+    d.idB[i] = d.id[i];
+    d.typeB[i] = t;
+    const int c = (ci[2] * nc + ci[1]) * nc + ci[0];
+    d.cellB[i] = c;
+    d.slot[i] = atomicAdd(&d.cellcount[c], 1);
+  }
+}
+
+// Exclusive scan of the cell counts (one CTA of 1024 threads).
+__global__ void __launch_bounds__(1024) k_rb_scan(Sys d) {
+  if (!*d.rebuild) return;
+  __shared__ int wsum[32];
+  const int64_t nc3 = d.ncell;
+  const int tid = threadIdx.x;
+  const int64_t per = (nc3 + blockDim.x - 1) / blockDim.x;
+  const int64_t c0 = tid * per, c1 = min(nc3, c0 + per);
+  int local = 0;
+  for (int64_t c = c0; c < c1; ++c) local += d.cellcount[c];
+  // block exclusive scan of local
+  const int lane = tid & 31, warp = tid >> 5;
+  int incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int w = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  int run = incl - local + (warp > 0 ? wsum[warp - 1] : 0);
+  for (int64_t c = c0; c < c1; ++c) {
+    d.cellstart[c] = run;
+    run += d.cellcount[c];
+  }
+  if (tid == 0) d.cellstart[nc3] = (int)d.n;
+}
+
+__global__ void __launch_bounds__(kThreads) k_rb_place(Sys d) {
+  if (!*d.rebuild) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    d.perm[d.cellstart[d.cellB[i]] + d.slot[i]] = (int)i;
+}
+
+// One warp per cell: orders the cell's atoms by id (deterministic layout
+// whatever order the atomics gave) and gathers them into place with their
+// cell-relative coordinates.
+template <typename TF>
+__global__ void __launch_bounds__(kCellWarps * 32) k_rb_rank(Sys d) {
+  if (!*d.rebuild) return;
+  using V4 = typename Vec4<TF>::type;
+  const int lane = threadIdx.x & 31;
+  const int64_t n = d.n;
+  const int64_t wglobal = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = wglobal; c < d.ncell; c += nwarps) {
+    const int s0 = d.cellstart[c], cnt = d.cellstart[c + 1] - s0;
+    const int cx = (int)(c % d.nc), cy = (int)((c / d.nc) % d.nc), cz = (int)(c / ((int64_t)d.nc * d.nc));
+    for (int e0 = 0; e0 < cnt; e0 += 32) {
+      const int e = e0 + lane;
+      const int a = e < cnt ? d.perm[s0 + e] : 0;
+      const int key = e < cnt ? d.idB[a] : 0x7fffffff;
+      int rank = 0;
+      for (int f0 = 0; f0 < cnt; f0 += 32) {
+        const int other = (f0 + lane < cnt) ? d.idB[d.perm[s0 + f0 + lane]] : 0x7fffffff;
+        for (int f = 0; f < 32; ++f) rank += (__shfl_sync(0xffffffffu, other, f) < key);
+      }
+      if (e < cnt) {
+        const int dst = s0 + rank;
+        double x[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          x[q] = d.rB[q * n + a];
+          d.r[q * n + dst] = x[q];
+          d.v[q * n + dst] = d.vB[q * n + a];
+        }
+        d.id[dst] = key;
+        d.type[dst] = d.typeB[a];
+        d.cpk[dst] = pack_cell(cx, cy, cz);
+        const TF px = (TF)fma(-(double)cx, d.edge, x[0]);
+        const TF py = (TF)fma(-(double)cy, d.edge, x[1]);
+        const TF pz = (TF)fma(-(double)cz, d.edge, x[2]);
+        Vec4<TF>::store(static_cast<V4 *>(d.rel) + dst, px, py, pz);
+        Vec4<TF>::store(static_cast<V4 *>(d.relb) + dst, px, py, pz);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- pairs
+
+// Shifted LJ pair terms for r2 < rc2 (Sec. 2.3): adds f_ij = fs d to f,
+// U(r) to e and d (x) f_ij to w (the 1/2 of the per-particle split is
+// applied once at the end).
+template <typename TF>
+__device__ __forceinline__ void lj_accumulate(const LJ<TF> &lj, TF dx, TF dy, TF dz, TF r2, TF f[3],
+                                              TF &e, TF w[6]) {
+  const TF ir2 = fast_rcp(r2);
+  const TF s2 = lj.sig2 * ir2;
+  const TF s6 = s2 * s2 * s2;
+  const TF u = lj.eps4 * s6 * (s6 - TF(1)) - lj.ushift;
+  const TF fs = lj.eps24 * s6 * (s6 + s6 - TF(1)) * ir2;
+  const TF fx = fs * dx, fy = fs * dy, fz = fs * dz;
+  f[0] += fx;
+  f[1] += fy;
+  f[2] += fz;
+  e += u;
+  w[0] += dx * fx;
+  w[1] += dy * fy;
+  w[2] += dz * fz;
+  w[3] += dx * fy;
+  w[4] += dx * fz;
+  w[5] += dy * fz;
+}
+
+template <typename TF>
+__device__ __forceinline__ void store_pair_out(const Sys &d, int64_t i, const TF f[3], TF e, const TF w[6]) {
+  TF *F = static_cast<TF *>(d.F);
+  TF *E = static_cast<TF *>(d.epot);
+  TF *W = static_cast<TF *>(d.W);
+  const int64_t n = d.n;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) F[a * n + i] = f[a];
+  E[i] = TF(0.5) * e;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) W[a * n + i] = TF(0.5) * w[a];
+}
+
+__device__ __forceinline__ void image_offset(int code, int &ox, int &oy, int &oz) {
+  ox = code % 3 - 1;
+  oy = (code / 3) % 3 - 1;
+  oz = code / 9 - 1;
+}
+
+// Link-cell kernel, one warp per cell (lanes = the cell's atoms, 32 at a
+// time).  The 27 neighbour cells are staged through shared memory 32 atoms
+// at a time; every lane then sweeps the staged atoms (broadcast reads).
+// BUILD: append every j within rlist to i's Verlet list, tagged with the
+// periodic image it was found in.  !BUILD: evaluate the forces directly.
+template <typename TF, bool BUILD>
+__global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
+  using V4 = typename Vec4<TF>::type;
+  if (BUILD && !*d.rebuild) return;
+  __shared__ V4 spos[kCellWarps][32];
+  __shared__ int sidx[kCellWarps][32];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int64_t n = d.n;
+  const int nc = d.nc;
+  const V4 *rel = static_cast<const V4 *>(d.rel);
+  const int64_t c = blockIdx.x * (int64_t)kCellWarps + wl;
+  if (c >= d.ncell) return;
+  const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
+  const int i0 = d.cellstart[c], i1 = d.cellstart[c + 1];
+  const TF edge = (TF)d.edge;
+  for (int ib = i0; ib < i1; ib += 32) {
+    const int i = ib + lane;
+    const bool act = i < i1;
+    V4 pi;
+    if (act) pi = Vec4<TF>::load(rel + i);
+    TF f[3] = {0, 0, 0}, e = 0, w[6] = {0, 0, 0, 0, 0, 0};
+    int cnt = 0;
+    for (int code = 0; code < 27; ++code) {
+      int ox, oy, oz;
+      image_offset(code, ox, oy, oz);
+      const int jx = (cx + ox + nc) % nc, jy = (cy + oy + nc) % nc, jz = (cz + oz + nc) % nc;
+      const int64_t cj = ((int64_t)jz * nc + jy) * nc + jx;
+      const int j0 = d.cellstart[cj], j1 = d.cellstart[cj + 1];
+      const TF offx = ox * edge, offy = oy * edge, offz = oz * edge;
+      for (int jb = j0; jb < j1; jb += 32) {
+        __syncwarp();
+        if (jb + lane < j1) {
+          spos[wl][lane] = Vec4<TF>::load(rel + jb + lane);
+          sidx[wl][lane] = jb + lane;
+        }
+        __syncwarp();
+        const int nj = min(32, j1 - jb);
+        if (act) {
+          for (int t = 0; t < nj; ++t) {
+            const V4 pj = spos[wl][t];
+            const int j = sidx[wl][t];
+            const TF dx = (pi.x - pj.x) - offx;
+            const TF dy = (pi.y - pj.y) - offy;
+            const TF dz = (pi.z - pj.z) - offz;
+            const TF r2 = dx * dx + dy * dy + dz * dz;
+            if (BUILD) {
+              if (r2 < lj.rlist2 && j != i) {
+                if (cnt < d.maxnb) d.nbr[(int64_t)cnt * n + i] = (uint32_t)j | ((uint32_t)code << 27);
+                ++cnt;
+              }
+            } else {
+              if (r2 < lj.rc2 && j != i) lj_accumulate<TF>(lj, dx, dy, dz, r2, f, e, w);
+            }
+          }
+        }
+      }
+    }
+    if (act) {
+      if (BUILD) {
+        d.nnb[i] = min(cnt, d.maxnb);
+        if (cnt > d.maxnb) atomicOr(d.err, ERR_NBR_OVERFLOW);
+      } else {
+        store_pair_out<TF>(d, i, f, e, w);
+      }
+    }
+  }
+}
+
+// Verlet-list pair kernel: one thread per atom (cell-sorted, so a warp's
+// neighbours overlap and their coordinates come from L1), full neighbour
+// shell, no atomics; FP32 FMA work on the CUDA cores in the mixed form.
+template <typename TF>
+__global__ void __launch_bounds__(kPairThreads) k_pair_list(Sys d, LJ<TF> lj) {
+  using V4 = typename Vec4<TF>::type;
+  __shared__ TF off[27][3];
+  if (threadIdx.x < 27) {
+    int ox, oy, oz;
+    image_offset(threadIdx.x, ox, oy, oz);
+    off[threadIdx.x][0] = ox * (TF)d.edge;
+    off[threadIdx.x][1] = oy * (TF)d.edge;
+    off[threadIdx.x][2] = oz * (TF)d.edge;
+  }
+  __syncthreads();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  const int64_t n = d.n;
+  const V4 *rel = static_cast<const V4 *>(d.rel);
+  const V4 pi = Vec4<TF>::load(rel + i);
+  TF f[3] = {0, 0, 0}, e = 0, w[6] = {0, 0, 0, 0, 0, 0};
+  const int nn = d.nnb[i];
+  const uint32_t *nb = d.nbr + i;
+  for (int k = 0; k < nn; ++k) {
+    const uint32_t ent = __ldg(nb + (int64_t)k * n);
+    const int j = (int)(ent & 0x07ffffffu);
+    const int code = (int)(ent >> 27);
+    const V4 pj = Vec4<TF>::load(rel + j);
+    const TF dx = (pi.x - pj.x) - off[code][0];
+    const TF dy = (pi.y - pj.y) - off[code][1];
+    const TF dz = (pi.z - pj.z) - off[code][2];
+    const TF r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 < lj.rc2) lj_accumulate<TF>(lj, dx, dy, dz, r2, f, e, w);
+  }
+  store_pair_out<TF>(d, i, f, e, w);
+}
+
+// ---------------------------------------------------- reduce and sample
+
+// Second half kick, then the per-step system observables (Sec. 2.3):
+// K, U, V sigma_ab = sum m v_a v_b + sum W_i,ab, V q = sum (E_i v_i + W_i v_i).
+// Per-thread partial sums in A (float in the mixed form, double in FP64),
+// the CTA and grid tree in FP64 (fixed order: deterministic).  The last CTA
+// to finish writes the observables, advances the step counter and takes
+// the stress and heat-flux correlator samples (Algorithm 1).  When a
+// velocity sample is due, velocities are also scattered to atom-id order.
+template <typename TF, typename A, bool KICK>
+__global__ void __launch_bounds__(kThreads)
+    k_kick_reduce(Sys d, double hdt, CorrDev cs, int64_t us, CorrDev ch, int64_t uh) {
+  __shared__ double red[kThreads / 32][kNRed];
+  __shared__ double tot[kNRed];
+  __shared__ int last;
+  const TF *F = static_cast<const TF *>(d.F);
+  const TF *Ep = static_cast<const TF *>(d.epot);
+  const TF *Wp = static_cast<const TF *>(d.W);
+  TF *vb = static_cast<TF *>(d.vbuf);
+  const int64_t n = d.n;
+  const ObsDev *o = d.obs;
+  const int64_t step_now = o->step + (KICK ? 1 : 0);
+  const bool vacf_due = KICK && d.vacf_u > 0 && ((step_now - o->corr_base) % d.vacf_u == 0);
+  A acc[kNRed];
+#pragma unroll
+  for (int q = 0; q < kNRed; ++q) acc[q] = A(0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int t = min(max(d.type[i], 0), 7);  // out-of-range types are flagged by the sort
+    double v[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      v[a] = d.v[a * n + i];
+      if (KICK) {
+        v[a] = fma(hdt * d.invm[t], (double)F[a * n + i], v[a]);
+        d.v[a * n + i] = v[a];
+      }
+    }
+    if (vacf_due) {
+      const int id = d.id[i];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) vb[a * n + id] = (TF)v[a];
+    }
+    const A m = (A)d.mass[t];
+    const A vx = (A)v[0], vy = (A)v[1], vz = (A)v[2];
+    const A ep = (A)Ep[i];
+    A w[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) w[q] = (A)Wp[q * n + i];
+    const A ke = A(0.5) * m * (vx * vx + vy * vy + vz * vz);
+    const A E = ke + ep;
+    acc[0] += ke;
+    acc[1] += ep;
+    acc[2] += m * vx * vx + w[0];
+    acc[3] += m * vy * vy + w[1];
+    acc[4] += m * vz * vz + w[2];
+    acc[5] += m * vx * vy + w[3];
+    acc[6] += m * vx * vz + w[4];
+    acc[7] += m * vy * vz + w[5];
+    acc[8] += E * vx + w[0] * vx + w[3] * vy + w[4] * vz;
+    acc[9] += E * vy + w[3] * vx + w[1] * vy + w[5] * vz;
+    acc[10] += E * vz + w[4] * vx + w[5] * vy + w[2] * vz;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kNRed; ++q) {
+    const double s = warp_sum((double)acc[q]);
+    if (lane == 0) red[warp][q] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < kNRed) {
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += red[w][threadIdx.x];
+    d.partials[blockIdx.x * kNRed + threadIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(d.counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int q = warp; q < kNRed; q += kThreads / 32) {
+    double s = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(d.partials + b * kNRed + q);
+    s = warp_sum(s);
+    if (lane == 0) tot[q] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ObsDev *ow = d.obs;
+    const double V = d.L * d.L * d.L;
+    ow->K = tot[0];
+    ow->U = tot[1];
+    ow->T = n > 1 ? 2.0 * tot[0] / (3.0 * (double)n - 3.0) : 0.0;
+    for (int a = 0; a < 6; ++a) ow->sigma[a] = tot[2 + a] / V;
+    for (int a = 0; a < 3; ++a) ow->q[a] = tot[8 + a] / V;
+    if (KICK) {
+      ow->step = step_now;
+      ow->Tsum += ow->T;
+      ow->Tn += 1;
+    }
+    *d.counter = 0u;
+    *d.rebuild = 0;
+  }
+  if (!KICK) return;
+  __syncthreads();
+  const int64_t tc = step_now - o->corr_base;
+  const int tid = threadIdx.x;
+  const double V = d.L * d.L * d.L;
+  if (tid < 3 && us > 0 && cs.b > 0 && tc % us == 0) {
+    const double x = tot[5 + tid] / V;  // sigma_xy, sigma_xz, sigma_yz
+    push_one_series<double>(cs, tid, x, x, tc / us);
+  } else if (tid >= 3 && tid < 6 && uh > 0 && ch.b > 0 && tc % uh == 0) {
+    const double x = tot[8 + tid - 3] / V;  // q_x, q_y, q_z
+    push_one_series<double>(ch, tid - 3, x, x, tc / uh);
+  }
+}
+
+__global__ void k_scale_v(Sys d, double lam) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * d.n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    d.v[i] *= lam;
+}
+
+__global__ void k_iota(int *id, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    id[i] = (int)i;
+}
+
+// Per-particle outputs back in atom-id order (FP64), positions wrapped.
+template <typename TF>
+__global__ void k_unsort(Sys d, double *r, double *v, double *F, double *epot, double *W) {
+  const int64_t n = d.n;
+  const TF *Fs = static_cast<const TF *>(d.F);
+  const TF *Es = static_cast<const TF *>(d.epot);
+  const TF *Ws = static_cast<const TF *>(d.W);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t id = d.id[i];
+    for (int a = 0; a < 3; ++a) {
+      if (r) {
+        double x = d.r[a * n + i];
+        x -= d.L * floor(x / d.L);
+        if (x >= d.L) x -= d.L;
+        r[a * n + id] = x;
+      }
+      if (v) v[a * n + id] = d.v[a * n + i];
+      if (F) F[a * n + id] = (double)Fs[a * n + i];
+    }
+    if (epot) epot[id] = (double)Es[i];
+    if (W)
+      for (int a = 0; a < 6; ++a) W[a * n + id] = (double)Ws[a * n + i];
+  }
+}
+
+}  // namespace
+}  // namespace otf
+
+using namespace otf;
+
+struct md_handle_s {
+  md_params prm{};
+  Sys d{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  bool fp64 = true;
+  int red_blocks = 1;
+  int64_t steps_done = 0;
+  int64_t corr_base = 0;
+  corr_handle banks[3];  // system-owned correlators (borrowed by md_corr)
+  bool bank_on[3] = {false, false, false};
+  double *d_out = nullptr;  // unsort staging [16][n]
+  ObsDev *h_obs = nullptr;  // pinned
+  unsigned *h_err = nullptr;
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+  std::vector<int> ev_class;
+  double kms[MD_NKCLASS] = {0};
+  int64_t klaunch[MD_NKCLASS] = {0};
+};
+
+namespace {
+
+int grid_for(int64_t n, int threads, int max_blocks = 152 * 8) {
+  return std::max(1, std::min(ceil_div(n, threads), max_blocks));
+}
+
+template <typename TF>
+LJ<TF> lj_of(const md_params &p) {
+  LJ<TF> lj;
+  const double sr = p.sigma / p.rc;
+  const double sr6 = sr * sr * sr * sr * sr * sr;
+  lj.eps4 = (TF)(4.0 * p.eps);
+  lj.eps24 = (TF)(24.0 * p.eps);
+  lj.sig2 = (TF)(p.sigma * p.sigma);
+  lj.rc2 = (TF)(p.rc * p.rc);
+  lj.ushift = (TF)(p.shift ? 4.0 * p.eps * (sr6 * sr6 - sr6) : 0.0);
+  const double rl = p.rc + (p.pair_mode == MD_PAIR_VERLET ? p.skin : 0.0);
+  lj.rlist2 = (TF)(rl * rl);
+  return lj;
+}
+
+// Event bracket around one kernel class when timing is on.
+struct KTimer {
+  md_handle *h;
+  cudaStream_t s;
+  int cls;
+  KTimer(md_handle *h_, cudaStream_t s_, int cls_) : h(h_), s(s_), cls(cls_) { mark(); }
+  ~KTimer() { mark(); }
+  void mark() {
+    if (!h || !h->timing) return;
+    if (h->ev_used == h->ev.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      h->ev.push_back(e);
+      h->ev_class.push_back(cls);
+    }
+    h->ev_class[h->ev_used] = cls;
+    cudaEventRecord(h->ev[h->ev_used++], s);
+  }
+};
+
+template <typename TF>
+int launch_rebuild(md_handle *h, cudaStream_t s) {
+  const Sys &d = h->d;
+  KTimer tm(h, s, MD_K_REBUILD);
+  k_rb_zero<<<grid_for(d.ncell, kThreads), kThreads, 0, s>>>(d);
+  k_rb_assign<<<grid_for(d.n, kThreads), kThreads, 0, s>>>(d);
+  k_rb_scan<<<1, 1024, 0, s>>>(d);
+  k_rb_place<<<grid_for(d.n, kThreads), kThreads, 0, s>>>(d);
+  k_rb_rank<TF><<<grid_for(d.ncell * 32, kCellWarps * 32), kCellWarps * 32, 0, s>>>(d);
+  if (h->prm.pair_mode == MD_PAIR_VERLET)
+    k_cells<TF, true><<<ceil_div(d.ncell, kCellWarps), kCellWarps * 32, 0, s>>>(d, lj_of<TF>(h->prm));
+  OTF_LAUNCH_CHECK();
+  return MD_OK;
+}
+
+template <typename TF>
+int launch_pair(md_handle *h, cudaStream_t s) {
+  const Sys &d = h->d;
+  KTimer tm(h, s, MD_K_PAIR);
+  if (h->prm.pair_mode == MD_PAIR_VERLET)
+    k_pair_list<TF><<<ceil_div(d.n, kPairThreads), kPairThreads, 0, s>>>(d, lj_of<TF>(h->prm));
+  else
+    k_cells<TF, false><<<ceil_div(d.ncell, kCellWarps), kCellWarps * 32, 0, s>>>(d, lj_of<TF>(h->prm));
+  OTF_LAUNCH_CHECK();
+  return MD_OK;
+}
+
+template <typename TF, typename A, bool KICK>
+int launch_reduce(md_handle *h, cudaStream_t s) {
+  KTimer tm(h, s, MD_K_REDUCE);
+  const Sys &d = h->d;
+  CorrDev cs = h->bank_on[0] ? h->banks[0].c.dev : CorrDev{};
+  CorrDev ch = h->bank_on[1] ? h->banks[1].c.dev : CorrDev{};
+  k_kick_reduce<TF, A, KICK><<<h->red_blocks, kThreads, 0, s>>>(
+      d, 0.5 * h->prm.dt, cs, h->bank_on[0] ? h->prm.stress.u : 0, ch, h->bank_on[1] ? h->prm.heatflux.u : 0);
+  OTF_LAUNCH_CHECK();
+  return MD_OK;
+}
+
+template <typename TF, typename A>
+int launch_step(md_handle *h, cudaStream_t s) {
+  const Sys &d = h->d;
+  {
+    KTimer tm(h, s, MD_K_INTEGRATE);
+    k_kick_drift<TF><<<grid_for(d.n, kThreads), kThreads, 0, s>>>(d, 0.5 * h->prm.dt);
+    OTF_LAUNCH_CHECK();
+  }
+  int rc = launch_rebuild<TF>(h, s);
+  if (rc) return rc;
+  if ((rc = launch_pair<TF>(h, s))) return rc;
+  if ((rc = launch_reduce<TF, A, true>(h, s))) return rc;
+  if (h->bank_on[2]) {
+    KTimer tm(h, s, MD_K_VACF);
+    const PushIdx pi{&h->d.obs->step, &h->d.obs->corr_base, h->prm.vacf.u, 0};
+    if ((rc = h->banks[2].c.launch_push(h->d.vbuf, h->d.vbuf, !h->fp64, pi, s))) return rc;
+  }
+  return MD_OK;
+}
+
+int step_once(md_handle *h, cudaStream_t s) {
+  return h->fp64 ? launch_step<double, double>(h, s) : launch_step<float, float>(h, s);
+}
+
+int refresh_obs(md_handle *h) {
+  return h->fp64 ? launch_reduce<double, double, false>(h, h->stream)
+                 : launch_reduce<float, float, false>(h, h->stream);
+}
+
+int check_device(md_handle *h) {
+  OTF_CUDA(cudaMemcpyAsync(h->h_err, h->d.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  OTF_CUDA(cudaStreamSynchronize(h->stream));
+  const unsigned e = *h->h_err;
+  if (e) {
+    set_error("device check failed (flags 0x%x):%s%s%s", e, (e & ERR_NONFINITE) ? " non-finite coordinates;" : "",
+              (e & ERR_NBR_OVERFLOW) ? " neighbour list over capacity (raise max_neighbors);" : "",
+              (e & ERR_BAD_TYPE) ? " atom type out of range;" : "");
+    return MD_ESTATE;
+  }
+  return MD_OK;
+}
+
+int build_graph(md_handle *h) {
+  cudaGraph_t g = nullptr;
+  OTF_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = step_once(h, h->cap_stream);
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) {
+    set_error("graph capture failed: %s", cudaGetErrorString(e));
+    return MD_ECUDA;
+  }
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->graph = nullptr;
+    set_error("graph instantiate failed: %s", cudaGetErrorString(e));
+    return MD_ECUDA;
+  }
+  return MD_OK;
+}
+
+int validate(const md_params *p, const md_system *s) {
+  if (!p || !s) {
+    set_error("md_init: null argument");
+    return MD_EINVAL;
+  }
+  if (p->n < 2 || p->n >= (1 << 27)) {
+    set_error("md_init: n must be in [2, 2^27)");
+    return MD_EINVAL;
+  }
+  if (!(p->box > 0) || !(p->rc > 0) || !(p->sigma > 0) || !(p->dt > 0) || p->skin < 0 ||
+      !std::isfinite(p->eps)) {
+    set_error("md_init: box, rc, sigma, dt must be positive and skin >= 0");
+    return MD_EINVAL;
+  }
+  if (p->ntypes < 1 || p->ntypes > 8) {
+    set_error("md_init: ntypes must be in [1, 8]");
+    return MD_EINVAL;
+  }
+  for (int t = 0; t < p->ntypes; ++t)
+    if (!(p->mass[t] > 0)) {
+      set_error("md_init: mass[%d] must be positive", t);
+      return MD_EINVAL;
+    }
+  if (p->precision != MD_PREC_FP64 && p->precision != MD_PREC_MIXED) {
+    set_error("md_init: unknown precision");
+    return MD_EINVAL;
+  }
+  if (p->pair_mode != MD_PAIR_VERLET && p->pair_mode != MD_PAIR_CELLS) {
+    set_error("md_init: unknown pair_mode");
+    return MD_EINVAL;
+  }
+  const double rl = p->rc + (p->pair_mode == MD_PAIR_VERLET ? p->skin : 0.0);
+  const int nc = (int)std::floor(p->box / rl);
+  if (nc < 3) {
+    set_error("md_init: box %.6g holds fewer than 3 cells of edge rc + skin = %.6g", p->box, rl);
+    return MD_EINVAL;
+  }
+  if (nc > 1023) {
+    set_error("md_init: more than 1023 cells per side");
+    return MD_EINVAL;
+  }
+  const corr_spec *cs[3] = {&p->stress, &p->heatflux, &p->vacf};
+  for (int k = 0; k < 3; ++k) {
+    if (cs[k]->u < 0) {
+      set_error("md_init: correlator update interval must be >= 0");
+      return MD_EINVAL;
+    }
+    if (cs[k]->u == 0) continue;
+    corr_params cp{cs[k]->b, cs[k]->p, cs[k]->m, 0, 3, 1, MD_PREC_FP64, 1.0};
+    if (validate_corr_params(cp)) return MD_EINVAL;
+  }
+  if (!s->r || !s->v || (s->mem != MD_MEM_HOST && s->mem != MD_MEM_DEVICE)) {
+    set_error("md_init: system needs r, v and a valid mem flag");
+    return MD_EINVAL;
+  }
+  if (s->mem == MD_MEM_HOST) {
+    for (int64_t i = 0; i < 3 * p->n; ++i)
+      if (!std::isfinite(s->r[i]) || !std::isfinite(s->v[i])) {
+        set_error("md_init: non-finite position or velocity at %lld", (long long)i);
+        return MD_ESTATE;
+      }
+    if (s->type)
+      for (int64_t i = 0; i < p->n; ++i)
+        if (s->type[i] < 0 || s->type[i] >= p->ntypes) {
+          set_error("md_init: atom %lld has type %d outside [0, %d)", (long long)i, s->type[i], p->ntypes);
+          return MD_EINVAL;
+        }
+  }
+  return MD_OK;
+}
+
+void release(md_handle *h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  Sys &d = h->d;
+  void *ptrs[] = {d.r, d.v, d.F, d.epot, d.W, d.rel, d.relb, d.vbuf, d.id, d.type, d.cpk, d.rB, d.vB,
+                  d.idB, d.typeB, d.cellB, d.slot, d.perm, d.cellcount, d.cellstart, d.nbr, d.nnb,
+                  d.partials, d.counter, d.obs, d.rebuild, d.err, h->d_out};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  for (int k = 0; k < 3; ++k)
+    if (h->bank_on[k]) h->banks[k].c.destroy();
+  if (h->h_obs) cudaFreeHost(h->h_obs);
+  if (h->h_err) cudaFreeHost(h->h_err);
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  delete h;
+}
+
+int init_impl(md_handle *h, const md_params *p, const md_system *s) {
+  h->prm = *p;
+  h->fp64 = p->precision == MD_PREC_FP64;
+  Sys &d = h->d;
+  const int64_t n = p->n;
+  const double rl = p->rc + (p->pair_mode == MD_PAIR_VERLET ? p->skin : 0.0);
+  d.n = n;
+  d.nc = (int)std::floor(p->box / rl);
+  d.ncell = (int64_t)d.nc * d.nc * d.nc;
+  d.L = p->box;
+  d.edge = p->box / d.nc;
+  d.dt = p->dt;
+  const double half_skin = 0.5 * (p->pair_mode == MD_PAIR_VERLET ? p->skin : 0.0);
+  d.lim2 = half_skin * half_skin;
+  d.always_rebuild = (p->pair_mode == MD_PAIR_CELLS || p->skin <= 0.0) ? 1 : 0;
+  d.ntypes = p->ntypes;
+  for (int t = 0; t < 8; ++t) {
+    d.mass[t] = t < p->ntypes ? p->mass[t] : 1.0;
+    d.invm[t] = 1.0 / d.mass[t];
+  }
+  const double rho = (double)n / (p->box * p->box * p->box);
+  int maxnb = p->max_neighbors;
+  if (maxnb <= 0) {
+    const double mean = rho * 4.18879020478639 * rl * rl * rl;
+    maxnb = ((int)(1.35 * mean + 24.0) + 31) / 32 * 32;
+  }
+  d.maxnb = maxnb;
+  d.vacf_u = p->vacf.u;
+  const size_t tf = h->fp64 ? sizeof(double) : sizeof(float);
+  const size_t v4 = h->fp64 ? sizeof(dvec4) : sizeof(float4);
+  h->red_blocks = grid_for(n, kThreads, kMaxRedBlocks);
+  OTF_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  OTF_CUDA(cudaMalloc(&d.r, 3 * n * sizeof(double)));
+  OTF_CUDA(cudaMalloc(&d.v, 3 * n * sizeof(double)));
+  OTF_CUDA(cudaMalloc(&d.F, 3 * n * tf));
+  OTF_CUDA(cudaMalloc(&d.epot, n * tf));
+  OTF_CUDA(cudaMalloc(&d.W, 6 * n * tf));
+  OTF_CUDA(cudaMalloc(&d.rel, n * v4));
+  OTF_CUDA(cudaMalloc(&d.relb, n * v4));
+  OTF_CUDA(cudaMalloc(&d.vbuf, 3 * n * tf));
+  OTF_CUDA(cudaMalloc(&d.id, n * sizeof(int)));
+  OTF_CUDA(cudaMalloc(&d.type, n * sizeof(int)));
+  OTF_CUDA(cudaMalloc(&d.cpk, n * sizeof(int)));
+  OTF_CUDA(cudaMalloc(&d.rB, 3 * n * sizeof(double)));
+  OTF_CUDA(cudaMalloc(&d.vB, 3 * n * sizeof(double)));
+  OTF_CUDA(cudaMalloc(&d.idB, n * sizeof(int)));
+  OTF_CUDA(cudaMalloc(&d.typeB, n * sizeof(int)));
+  OTF_CUDA(cudaMalloc(&d.cellB, n * sizeof(int)));
+  OTF_CUDA(cudaMalloc(&d.slot, n * sizeof(int)));
+  OTF_CUDA(cudaMalloc(&d.perm, n * sizeof(int)));
+  OTF_CUDA(cudaMalloc(&d.cellcount, d.ncell * sizeof(int)));
+  OTF_CUDA(cudaMalloc(&d.cellstart, (d.ncell + 1) * sizeof(int)));
+  if (p->pair_mode == MD_PAIR_VERLET) OTF_CUDA(cudaMalloc(&d.nbr, (size_t)maxnb * n * sizeof(uint32_t)));
+  OTF_CUDA(cudaMalloc(&d.nnb, n * sizeof(int)));
+  OTF_CUDA(cudaMalloc(&d.partials, (size_t)h->red_blocks * kNRed * sizeof(double)));
+  OTF_CUDA(cudaMalloc(&d.counter, sizeof(unsigned)));
+  OTF_CUDA(cudaMalloc(&d.obs, sizeof(ObsDev)));
+  OTF_CUDA(cudaMalloc(&d.rebuild, sizeof(int)));
+  OTF_CUDA(cudaMalloc(&d.err, sizeof(unsigned)));
+  OTF_CUDA(cudaMallocHost(&h->h_obs, sizeof(ObsDev)));
+  OTF_CUDA(cudaMallocHost(&h->h_err, sizeof(unsigned)));
+  cudaStream_t st = h->stream;
+  OTF_CUDA(cudaMemsetAsync(d.counter, 0, sizeof(unsigned), st));
+  OTF_CUDA(cudaMemsetAsync(d.obs, 0, sizeof(ObsDev), st));
+  OTF_CUDA(cudaMemsetAsync(d.err, 0, sizeof(unsigned), st));
+  OTF_CUDA(cudaMemsetAsync(d.F, 0, 3 * n * tf, st));
+  OTF_CUDA(cudaMemsetAsync(d.vbuf, 0, 3 * n * tf, st));
+  const int one = 1;
+  OTF_CUDA(cudaMemcpyAsync(d.rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+  const cudaMemcpyKind kind = s->mem == MD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  OTF_CUDA(cudaMemcpyAsync(d.r, s->r, 3 * n * sizeof(double), kind, st));
+  OTF_CUDA(cudaMemcpyAsync(d.v, s->v, 3 * n * sizeof(double), kind, st));
+  if (s->type)
+    OTF_CUDA(cudaMemcpyAsync(d.type, s->type, n * sizeof(int), kind, st));
+  else
+    OTF_CUDA(cudaMemsetAsync(d.type, 0, n * sizeof(int), st));
+  k_iota<<<grid_for(n, kThreads), kThreads, 0, st>>>(d.id, n);
+  OTF_LAUNCH_CHECK();
+  // host-side copies of the inputs must be done before returning
+  OTF_CUDA(cudaStreamSynchronize(st));
+  // correlators
+  const corr_spec *specs[3] = {&p->stress, &p->heatflux, &p->vacf};
+  for (int k = 0; k < 3; ++k) {
+    if (specs[k]->u <= 0) continue;
+    corr_params cp{specs[k]->b, specs[k]->p, specs[k]->m, 0, k == 2 ? 3 * n : 3, k == 2 ? n : 1,
+                   k == 2 ? p->precision : MD_PREC_FP64, specs[k]->u * p->dt};
+    Correlator &c = h->banks[k].c;
+    h->bank_on[k] = true;
+    int rc = c.create(cp, st);
+    if (rc) return rc;
+    c.borrowed = true;
+    c.host_steps = &h->steps_done;
+    c.host_base = &h->corr_base;
+    c.u = specs[k]->u;
+  }
+  // initial layout, forces and observables
+  int rc = h->fp64 ? launch_rebuild<double>(h, st) : launch_rebuild<float>(h, st);
+  if (rc) return rc;
+  rc = h->fp64 ? launch_pair<double>(h, st) : launch_pair<float>(h, st);
+  if (rc) return rc;
+  if ((rc = refresh_obs(h))) return rc;
+  return check_device(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+int md_init(const md_params *p, const md_system *s, void *cuda_stream, md_handle **out) {
+  clear_error();
+  if (!out) {
+    set_error("md_init: null output handle");
+    return MD_EINVAL;
+  }
+  *out = nullptr;
+  int rc = validate(p, s);
+  if (rc) return rc;
+  md_handle *h = new (std::nothrow) md_handle;
+  if (!h) return MD_ENOMEM;
+  h->stream = (cudaStream_t)cuda_stream;
+  rc = init_impl(h, p, s);
+  if (rc) {
+    release(h);
+    return rc;
+  }
+  *out = h;
+  return MD_OK;
+}
+
+int md_step(md_handle *h, int64_t nsteps) {
+  clear_error();
+  if (!h || nsteps < 0) {
+    set_error("md_step: null handle or negative nsteps");
+    return MD_EINVAL;
+  }
+  if (nsteps == 0) return MD_OK;
+  int rc = MD_OK;
+  if (h->timing || !h->prm.use_graph) {
+    for (int64_t s = 0; s < nsteps && !rc; ++s) rc = step_once(h, h->stream);
+  } else {
+    if (!h->graph && (rc = build_graph(h))) return rc;
+    for (int64_t s = 0; s < nsteps; ++s) {
+      cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
+      if (e != cudaSuccess) {
+        set_error("cudaGraphLaunch failed: %s", cudaGetErrorString(e));
+        return MD_ECUDA;
+      }
+    }
+  }
+  if (rc) return rc;
+  h->steps_done += nsteps;
+  rc = check_device(h);
+  if (h->timing && !rc) {
+    // pair up the events of each class: (start, stop)
+    for (size_t e = 0; e + 1 < h->ev_used; e += 2) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, h->ev[e], h->ev[e + 1]) == cudaSuccess) {
+        h->kms[h->ev_class[e]] += ms;
+        h->klaunch[h->ev_class[e]] += 1;
+      }
+    }
+  }
+  h->ev_used = 0;
+  return rc;
+}
+
+int md_observables(md_handle *h, md_obs *out) {
+  clear_error();
+  if (!h || !out) {
+    set_error("md_observables: null argument");
+    return MD_EINVAL;
+  }
+  OTF_CUDA(cudaMemcpyAsync(h->h_obs, h->d.obs, sizeof(ObsDev), cudaMemcpyDeviceToHost, h->stream));
+  OTF_CUDA(cudaStreamSynchronize(h->stream));
+  const ObsDev &o = *h->h_obs;
+  out->step = o.step;
+  out->U = o.U;
+  out->K = o.K;
+  out->T = o.T;
+  for (int a = 0; a < 6; ++a) out->sigma[a] = o.sigma[a];
+  for (int a = 0; a < 3; ++a) out->q[a] = o.q[a];
+  out->T_mean = o.Tn > 0 ? o.Tsum / (double)o.Tn : o.T;
+  return MD_OK;
+}
+
+int md_get_particles(md_handle *h, double *r, double *v, double *F, double *epot, double *W, int32_t mem) {
+  clear_error();
+  if (!h || (mem != MD_MEM_HOST && mem != MD_MEM_DEVICE)) {
+    set_error("md_get_particles: bad argument");
+    return MD_EINVAL;
+  }
+  const int64_t n = h->d.n;
+  cudaStream_t st = h->stream;
+  if (mem == MD_MEM_DEVICE) {
+    if (h->fp64)
+      k_unsort<double><<<grid_for(n, kThreads), kThreads, 0, st>>>(h->d, r, v, F, epot, W);
+    else
+      k_unsort<float><<<grid_for(n, kThreads), kThreads, 0, st>>>(h->d, r, v, F, epot, W);
+    OTF_LAUNCH_CHECK();
+    OTF_CUDA(cudaStreamSynchronize(st));
+    return MD_OK;
+  }
+  if (!h->d_out) OTF_CUDA(cudaMalloc(&h->d_out, 16 * n * sizeof(double)));
+  double *o = h->d_out;
+  double *dr = o, *dv = o + 3 * n, *dF = o + 6 * n, *de = o + 9 * n, *dW = o + 10 * n;
+  if (h->fp64)
+    k_unsort<double><<<grid_for(n, kThreads), kThreads, 0, st>>>(h->d, dr, dv, dF, de, dW);
+  else
+    k_unsort<float><<<grid_for(n, kThreads), kThreads, 0, st>>>(h->d, dr, dv, dF, de, dW);
+  OTF_LAUNCH_CHECK();
+  const size_t b3 = 3 * n * sizeof(double);
+  if (r) OTF_CUDA(cudaMemcpyAsync(r, dr, b3, cudaMemcpyDeviceToHost, st));
+  if (v) OTF_CUDA(cudaMemcpyAsync(v, dv, b3, cudaMemcpyDeviceToHost, st));
+  if (F) OTF_CUDA(cudaMemcpyAsync(F, dF, b3, cudaMemcpyDeviceToHost, st));
+  if (epot) OTF_CUDA(cudaMemcpyAsync(epot, de, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (W) OTF_CUDA(cudaMemcpyAsync(W, dW, 2 * b3, cudaMemcpyDeviceToHost, st));
+  OTF_CUDA(cudaStreamSynchronize(st));
+  return MD_OK;
+}
+
+int md_scale_velocities(md_handle *h, double lambda) {
+  clear_error();
+  if (!h || !std::isfinite(lambda)) {
+    set_error("md_scale_velocities: bad argument");
+    return MD_EINVAL;
+  }
+  k_scale_v<<<grid_for(3 * h->d.n, kThreads), kThreads, 0, h->stream>>>(h->d, lambda);
+  OTF_LAUNCH_CHECK();
+  int rc = refresh_obs(h);
+  if (rc) return rc;
+  OTF_CUDA(cudaStreamSynchronize(h->stream));
+  return MD_OK;
+}
+
+int md_reset_correlators(md_handle *h) {
+  clear_error();
+  if (!h) return MD_EINVAL;
+  for (int k = 0; k < 3; ++k)
+    if (h->bank_on[k]) {
+      int rc = h->banks[k].c.reset();
+      if (rc) return rc;
+    }
+  // correlator base := current step; temperature mean restarts
+  OTF_CUDA(cudaMemcpyAsync(h->h_obs, h->d.obs, sizeof(ObsDev), cudaMemcpyDeviceToHost, h->stream));
+  OTF_CUDA(cudaStreamSynchronize(h->stream));
+  h->h_obs->corr_base = h->h_obs->step;
+  h->h_obs->Tsum = 0.0;
+  h->h_obs->Tn = 0;
+  OTF_CUDA(cudaMemcpyAsync(h->d.obs, h->h_obs, sizeof(ObsDev), cudaMemcpyHostToDevice, h->stream));
+  OTF_CUDA(cudaStreamSynchronize(h->stream));
+  h->corr_base = h->steps_done;
+  return MD_OK;
+}
+
+int md_corr(md_handle *h, int32_t which, corr_handle **out) {
+  clear_error();
+  if (!h || !out || which < 0 || which > 2) {
+    set_error("md_corr: bad argument");
+    return MD_EINVAL;
+  }
+  if (!h->bank_on[which]) {
+    set_error("md_corr: correlator %d is disabled (u = 0)", which);
+    return MD_EINVAL;
+  }
+  *out = &h->banks[which];
+  return MD_OK;
+}
+
+int md_set_timing(md_handle *h, int32_t on) {
+  if (!h) return MD_EINVAL;
+  h->timing = on != 0;
+  for (int k = 0; k < MD_NKCLASS; ++k) {
+    h->kms[k] = 0.0;
+    h->klaunch[k] = 0;
+  }
+  h->ev_used = 0;
+  return MD_OK;
+}
+
+int md_kernel_times(md_handle *h, double *ms, int64_t *launches) {
+  if (!h) return MD_EINVAL;
+  for (int k = 0; k < MD_NKCLASS; ++k) {
+    if (ms) ms[k] = h->kms[k];
+    if (launches) launches[k] = h->klaunch[k];
+  }
+  return MD_OK;
+}
+
+void md_free(md_handle *h) { release(h); }
+
+}  // extern "C"

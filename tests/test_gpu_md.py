@@ -1,0 +1,244 @@
+"""GPU MD path parity against the FP64 oracle (Sec. 1 link cells and velocity
+Verlet; Sec. 2.3 stress tensor and heat flux; Sec. 2.2 correlators).
+
+Tolerances.  FP64: max|GPU - oracle| / max|oracle| <= 1e-11 per array (only
+summation order differs; over 10 steps chaotic growth of rounding is far
+below that).  Mixed form: every force component within
+2e-5 * max(|F_ia|, F_rms) of the FP64 oracle at the same positions; the
+per-particle energy and virial within 2e-5 of their largest magnitude.
+"""
+import numpy as np
+import pytest
+
+from paper_2503_07526_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2503_07526_gb300 as pkg
+
+    pkg.lib(build=True)
+    return pkg
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def min_image(d, L):
+    return d - L * np.round(d / L)
+
+
+def jittered(cells, seed, rho=0.8442, T=0.722, amp=0.2):
+    s = synth.lj_system(cells, rho=rho, T=T, seed=seed)
+    s["r"] = s["r"] + amp * (synth.uniform01(seed + 99, s["r"].size).reshape(s["r"].shape) - 0.5)
+    return s
+
+
+def params(pkg, s, **kw):
+    kw.setdefault("stress", (6, 16, 2, 1))
+    kw.setdefault("heatflux", (6, 16, 2, 1))
+    kw.setdefault("vacf", (4, 16, 2, 1))
+    return pkg.make_params(s["n"], s["L"], **kw)
+
+
+def check_mixed_forces(F, Fo):
+    frms = np.sqrt((Fo ** 2).mean())
+    bound = 2e-5 * np.maximum(np.abs(Fo), frms)
+    assert np.all(np.abs(F - Fo) <= bound), np.max(np.abs(F - Fo) / np.maximum(np.abs(Fo), frms))
+
+
+@pytest.mark.parametrize("cells", [6, 8, 10, 11])
+@pytest.mark.parametrize("mode", ["verlet", "cells"])
+def test_initial_forces_fp64(pkg, oracle_mod, cells, mode):
+    s = jittered(cells, seed=cells)
+    pm = pkg.MD_PAIR_VERLET if mode == "verlet" else pkg.MD_PAIR_CELLS
+    g = pkg.System(params(pkg, s, precision=pkg.MD_PREC_FP64, pair_mode=pm), s["r"], s["v"])
+    got = g.particles()
+    F, e, W = oracle_mod.lj_forces(s["r"], s["L"], method="cells")
+    assert rel(got["F"], F) <= 1e-11
+    assert rel(got["epot"], e) <= 1e-11
+    assert rel(got["W"], W) <= 1e-11
+    assert np.abs(min_image(got["r"] - s["r"], s["L"])).max() <= 1e-12
+    assert np.array_equal(got["v"], s["v"])
+    obs = g.observables()
+    want = oracle_mod.observables(s["L"] ** 3, np.ones(s["n"]), s["v"], e, W)
+    assert obs["U"] == pytest.approx(want[0], rel=1e-12)
+    assert obs["K"] == pytest.approx(want[1], rel=1e-12)
+    assert rel(obs["sigma"], want[3:9]) <= 1e-11
+    assert rel(obs["q"], want[9:12]) <= 1e-11
+
+
+@pytest.mark.parametrize("cells", [6, 10])
+@pytest.mark.parametrize("mode", ["verlet", "cells"])
+def test_initial_forces_mixed(pkg, oracle_mod, cells, mode):
+    s = jittered(cells, seed=cells + 1)
+    pm = pkg.MD_PAIR_VERLET if mode == "verlet" else pkg.MD_PAIR_CELLS
+    g = pkg.System(params(pkg, s, precision=pkg.MD_PREC_MIXED, pair_mode=pm), s["r"], s["v"])
+    got = g.particles()
+    F, e, W = oracle_mod.lj_forces(s["r"], s["L"], method="cells")
+    check_mixed_forces(got["F"], F)
+    assert np.abs(got["epot"] - e).max() <= 2e-5 * np.abs(e).max()
+    assert np.abs(got["W"] - W).max() <= 2e-5 * np.abs(W).max()
+
+
+@pytest.mark.parametrize("mode,skin,graph", [("verlet", 0.3, True), ("verlet", 0.05, True),
+                                             ("verlet", 0.05, False), ("cells", 0.0, True)])
+def test_ten_steps_fp64(pkg, oracle_mod, mode, skin, graph):
+    """Per-step parity over 10 steps; skin 0.05 forces neighbour-list rebuilds
+    inside the window."""
+    s = jittered(8, seed=5, T=1.2)
+    pm = pkg.MD_PAIR_VERLET if mode == "verlet" else pkg.MD_PAIR_CELLS
+    g = pkg.System(params(pkg, s, precision=pkg.MD_PREC_FP64, pair_mode=pm, skin=skin, use_graph=graph),
+                   s["r"], s["v"])
+    md = oracle_mod.MD(s["r"], s["v"], s["L"])
+    for step in range(10):
+        g.step(1)
+        o = md.step(1, record=True)[0]
+        obs = g.observables()
+        assert obs["step"] == step + 1
+        assert obs["U"] == pytest.approx(o[0], rel=1e-11)
+        assert obs["K"] == pytest.approx(o[1], rel=1e-11)
+        assert rel(obs["sigma"], o[3:9]) <= 1e-11
+        assert rel(obs["q"], o[9:12]) <= 1e-11
+    got, want = g.particles(), md.get()
+    assert np.abs(min_image(got["r"] - want["r"], s["L"])).max() <= 1e-11 * s["L"]
+    assert rel(got["v"], want["v"]) <= 1e-11
+    assert rel(got["F"], want["F"]) <= 1e-11
+    assert rel(got["W"], want["W"]) <= 1e-11
+
+
+def test_mixed_forces_along_trajectory(pkg, oracle_mod):
+    """Mixed form: at every step the FP32 forces meet the per-component
+    bound against FP64 forces at the GPU's own positions; the stress and heat
+    flux error against the FP64 reduction of the same particles is stated."""
+    s = jittered(10, seed=2)
+    g = pkg.System(params(pkg, s, precision=pkg.MD_PREC_MIXED, skin=0.1), s["r"], s["v"])
+    for _ in range(10):
+        g.step(1)
+        got = g.particles()
+        F, e, W = oracle_mod.lj_forces(got["r"], s["L"], method="cells")
+        check_mixed_forces(got["F"], F)
+        obs = g.observables()
+        want = oracle_mod.observables(s["L"] ** 3, np.ones(s["n"]), got["v"], got["epot"], got["W"])
+        scale = np.abs(want[3:6]).max()
+        assert np.abs(obs["sigma"] - want[3:9]).max() <= 1e-6 * scale
+        assert np.abs(obs["q"] - want[9:12]).max() <= 1e-6 * np.abs(want[9:12]).max() + 1e-7 * scale
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_md_correlators_match_oracle(pkg, oracle_mod, prec):
+    """The stress, heat-flux and velocity correlators fed by md_step equal
+    oracle correlators fed by the oracle's own run (FP64, 64 steps), or by
+    the GPU's recorded series (mixed form, where trajectories differ)."""
+    s = jittered(8, seed=11, T=1.0)
+    n = s["n"]
+    g = pkg.System(params(pkg, s, precision=prec, stress=(5, 16, 2, 1), heatflux=(5, 8, 2, 2),
+                          vacf=(4, 16, 2, 1)), s["r"], s["v"])
+    cs = oracle_mod.Corr(5, 16, 2, 3)
+    ch = oracle_mod.Corr(5, 8, 2, 3)
+    cv = oracle_mod.Corr(4, 16, 2, 3 * n, gs=n)
+    if prec == 0:
+        md = oracle_mod.MD(s["r"], s["v"], s["L"])
+    for step in range(1, 65):
+        g.step(1)
+        if prec == 0:
+            o = md.step(1, record=True)[0]
+            st = md.get()
+            sig, q, v = o[6:9], o[9:12], st["v"]
+        else:
+            obs = g.observables()
+            sig, q, v = obs["sigma"][3:6], obs["q"], g.particles()["v"]
+        cs.push(sig)
+        if step % 2 == 0:
+            ch.push(q)
+        cv.push(v)
+    tol = 1e-11 if prec == 0 else 2e-5
+    for which, orc, dtu in [(pkg.MD_CORR_STRESS, cs, 1), (pkg.MD_CORR_HEATFLUX, ch, 2), (pkg.MD_CORR_VACF, cv, 1)]:
+        c = g.corr(which)
+        for grp in range(3):
+            tg, vg = c.read(grp)
+            to, vo = orc.read(grp)
+            assert np.allclose(tg, to * dtu * 0.005, rtol=1e-14)
+            assert np.abs(vg - vo).max() <= (1e-11 if (prec == 0 or which != pkg.MD_CORR_VACF) else tol) * abs(vo[0])
+    assert g.corr(pkg.MD_CORR_HEATFLUX).pushes() == 32
+
+
+def test_reset_and_scale_velocities(pkg, oracle_mod):
+    s = jittered(8, seed=4)
+    g = pkg.System(params(pkg, s), s["r"], s["v"])
+    g.step(7)
+    T0 = g.observables()["T"]
+    g.scale_velocities(0.5)
+    assert g.observables()["T"] == pytest.approx(0.25 * T0, rel=1e-12)
+    g.reset_correlators()
+    assert g.corr(pkg.MD_CORR_VACF).pushes() == 0
+    g.step(5)
+    assert g.corr(pkg.MD_CORR_STRESS).pushes() == 5
+    assert g.observables()["step"] == 12
+
+
+def test_energy_conservation_fp64_and_mixed(pkg):
+    s = jittered(10, seed=8, amp=0.05)
+    for prec in (0, 1):
+        g = pkg.System(params(pkg, s, precision=prec), s["r"], s["v"])
+        E = []
+        for _ in range(40):
+            g.step(10)
+            o = g.observables()
+            E.append(o["U"] + o["K"])
+        E = np.array(E)
+        assert np.abs(E - E[0]).max() / s["n"] < 2e-3, prec
+
+
+def test_invalid_inputs_are_errors(pkg):
+    s = synth.lj_system(5)  # L = 8.40: only 2 cells of rc + skin
+    with pytest.raises(pkg.MdError) as ei:
+        pkg.System(params(pkg, s), s["r"], s["v"])
+    assert ei.value.code == -1
+    s = synth.lj_system(6)
+    r = s["r"].copy()
+    r[1, 5] = np.nan
+    with pytest.raises(pkg.MdError) as ei:
+        pkg.System(params(pkg, s), r, s["v"])
+    assert ei.value.code == -4
+    with pytest.raises(pkg.MdError) as ei:
+        pkg.System(params(pkg, s, max_neighbors=8), s["r"], s["v"])
+    assert ei.value.code == -4
+    with pytest.raises(pkg.MdError):
+        pkg.System(params(pkg, s), s["r"], s["v"], types=np.full(s["n"], 3, dtype=np.int32))
+
+
+def test_device_inputs_and_outputs(pkg, oracle_mod):
+    import torch
+
+    s = jittered(6, seed=3)
+    rd = torch.tensor(s["r"], device="cuda")
+    vd = torch.tensor(s["v"], device="cuda")
+    g = pkg.System(params(pkg, s), rd, vd)
+    F = torch.empty((3, s["n"]), dtype=torch.float64, device="cuda")
+    g.particles_device(F=F)
+    Fo, _, _ = oracle_mod.lj_forces(s["r"], s["L"], method="cells")
+    assert rel(F.cpu().numpy(), Fo) <= 1e-11
+
+
+def test_full_size_mixed_forces_and_reduction(pkg, oracle_mod):
+    """The 2,048,000-atom mixed-precision system of the benchmark: every
+    force component against the FP64 oracle at the GPU's positions after two
+    steps, and the stress / heat-flux reduction against the FP64 reduction
+    of the same particle data."""
+    s = synth.lj_system(80, seed=1)
+    g = pkg.System(params(pkg, s, precision=pkg.MD_PREC_MIXED), s["r"], s["v"])
+    g.step(2)
+    got = g.particles()
+    F, e, W = oracle_mod.lj_forces(got["r"], s["L"], method="cells")
+    check_mixed_forces(got["F"], F)
+    obs = g.observables()
+    want = oracle_mod.observables(s["L"] ** 3, np.ones(s["n"]), got["v"], got["epot"], got["W"])
+    scale = np.abs(want[3:6]).max()
+    assert np.abs(obs["sigma"] - want[3:9]).max() <= 1e-6 * scale
