@@ -1,0 +1,421 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the on-the-fly property MD step on GB300.
+
+One step = velocity-Verlet kick/drift, neighbour-list rebuild when due, LJ
+pair forces with per-particle energy and virial, second kick with the
+stress / heat-flux reduction, and correlator samples of the stress, heat
+flux and every atom's velocity (u = 1).  Workload: the 2,048,000-atom LJ
+liquid (80^3 fcc cells x 4, rho* = 0.8442, T* = 0.722, rc = 2.5, dt = 0.005)
+in the mixed form (FP32 forces / fluxes / correlator products, FP64
+positions, velocities, reductions and lag sums), melted before timing.
+Prints one JSON line (rank 0).
+
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atom-steps/s with on-the-fly correlators vs plain FP64 GPU; time-to-viscosity at ≤2% err"
+UNIT = "atom-steps/s"
+CELLS = 80  # 4 * 80^3 = 2,048,000 atoms
+RHO, T_STAR, RC, DT, SKIN = 0.8442, 0.722, 2.5, 0.005, 0.3
+SPEC = dict(stress=(12, 16, 2, 1), heatflux=(12, 16, 2, 1), vacf=(8, 16, 2, 1))
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5, derived from unit counts
+PAIR_FLOP_PER_ATOM = 0.5 * RHO * (4.0 / 3.0) * math.pi * RC ** 3 * 50.0  # unique pairs x 50 flop
+
+
+def workload_name(n):
+    return (f"LJ liquid {n:,} atoms (fcc {CELLS}^3 x 4 melted), rho*={RHO}, T*={T_STAR}, rc={RC} shifted, "
+            f"dt={DT}, velocity Verlet NVE; on-the-fly correlators: stress xy/xz/yz and heat flux "
+            f"(b=12,p=16,m=2,u=1), per-atom VACF over all atoms (b=8,p=16,m=2,u=1)")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.i0, self.i1 = 0, None
+
+    def start(self):
+        self.i0 = len(self.lines)
+
+    def stop(self):
+        time.sleep(0.15)  # let the sample taken at the end of the region arrive
+        self.i1 = len(self.lines)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines[self.i0:self.i1]:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def vacf_bytes_per_push(t, b, p, m, nseries, esz):
+    """Algorithmic HBM bytes of push t of a grouped correlator: per series,
+    block 0 reads the new sample and p-1 older ring entries and writes one;
+    each higher block the push reaches reads m entries of the block below,
+    p - p/m older entries (fewer while filling) and writes one."""
+    tot = 0
+    Mk = 1
+    for k in range(b):
+        if k > 0:
+            Mk *= m
+            if t % Mk:
+                break
+        nk = t // Mk
+        lo = 0 if k == 0 else p // m
+        nl = max(0, min(p - 1, nk - 1) - lo + 1)
+        older = nl - (1 if lo == 0 and nl > 0 else 0)
+        reads = (1 if k == 0 else m) + older
+        tot += (reads + 1) * esz
+    return tot * nseries
+
+
+def melt(sysg, target_T, steps, every=10):
+    for _ in range(steps // every):
+        sysg.step(every)
+        T = sysg.observables()["T"]
+        sysg.scale_velocities(math.sqrt(target_T / T))
+
+
+def prepare_state(pkg, synth, seed):
+    """Melted liquid at T* (untimed): rescale to T* = 2.0 for 600 steps, then
+    to T* = 0.722 for 600 steps, on the mixed-precision path."""
+    s = synth.lj_system(CELLS, rho=RHO, T=T_STAR, seed=seed)
+    p = pkg.make_params(s["n"], s["L"], rc=RC, dt=DT, skin=SKIN, precision=pkg.MD_PREC_MIXED,
+                        stress=None, heatflux=None, vacf=None)
+    g = pkg.System(p, s["r"], s["v"])
+    melt(g, 2.0, 600)
+    melt(g, T_STAR, 600)
+    st = g.particles()
+    g.close()
+    return s, st
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import paper_2503_07526_gb300 as pkg
+    from paper_2503_07526_gb300 import synth
+
+    pkg.lib()
+    s, st = prepare_state(pkg, synth, seed=1 + rank)
+    n, L = s["n"], s["L"]
+    p = pkg.make_params(n, L, rc=RC, dt=DT, skin=SKIN, precision=pkg.MD_PREC_MIXED, **SPEC)
+    g = pkg.System(p, st["r"], st["v"])
+    g.step(args.warmup)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # --- timed region: K steps, every kernel bracketed by CUDA events
+    g.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        clk.start()
+        e0.record(stream)
+        g.step(args.steps)
+        e1.record(stream)
+        barrier()
+        clk.stop()
+    ms_total = e0.elapsed_time(e1)
+    ktimes = g.kernel_times()
+    g.set_timing(False)
+    if dist:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * n * args.steps / (ms_total / 1e3)
+
+    # graph-replay time of the same step (product default), for reference
+    barrier()
+    e0.record(stream)
+    g.step(args.steps)
+    e1.record(stream)
+    barrier()
+    graph_ms_step = e0.elapsed_time(e1) / args.steps
+    g.close()
+
+    # --- plain FP64 GPU path on the same state (the comparison form)
+    k64 = max(3, args.steps // 10)
+    p64 = pkg.make_params(n, L, rc=RC, dt=DT, skin=SKIN, precision=pkg.MD_PREC_FP64, **SPEC)
+    g64 = pkg.System(p64, st["r"], st["v"])
+    g64.step(2)
+    barrier()
+    e0.record(stream)
+    g64.step(k64)
+    e1.record(stream)
+    barrier()
+    ms64 = e0.elapsed_time(e1) / k64
+    g64.close()
+
+    # --- end to end through the C ABI from host buffers
+    barrier()
+    t0 = time.perf_counter()
+    ge = pkg.System(p, st["r"], st["v"])  # host -> device copy of the state
+    ge.step(args.steps)
+    obs = ge.observables()
+    for which in (pkg.MD_CORR_STRESS, pkg.MD_CORR_HEATFLUX, pkg.MD_CORR_VACF):
+        ge.corr(which).read(-1)  # device -> host readout of every correlator
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    ge.close()
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = (2 * 3 * n * 8) / args.steps
+    d2h = (8 * 16 + 3 * 2 * 8 * (12 * 16 + 12 * 16 + 8 * 16)) / args.steps
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_kind = measured_peaks()
+    # roofline of the dominant kernel class
+    shares = {k: v[0] for k, v in ktimes.items()}
+    kern_ms = sum(shares.values())
+    dom = max(shares, key=shares.get)
+    if dom == "vacf":
+        b, pp, m, _ = SPEC["vacf"]
+        # the timed pushes are steps warmup+1 .. warmup+K after the reset at init
+        pushes = range(args.warmup + 1, args.warmup + args.steps + 1)
+        bytes_tot = sum(vacf_bytes_per_push(t, b, pp, m, 3 * n, 4) for t in pushes)
+        achieved = bytes_tot / (ktimes["vacf"][0] / 1e3) / 1e9
+        roof = {"kernel": "k_push_grouped (per-atom VACF push)", "bound": "hbm", "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "peak_source": f"{peak_kind} hbm_gbs"}
+    else:
+        flops = PAIR_FLOP_PER_ATOM * n * ktimes["pair"][1]
+        achieved = flops / (ktimes["pair"][0] / 1e3) / 1e12
+        roof = {"kernel": "k_pair_list (LJ forces + per-particle energy and virial)", "bound": "alu",
+                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS,
+                "peak_source": "FP32 FMA lanes: 152 SMs x 128 x 2 flop x 2070 MHz"}
+    roof["traffic"] = committed_traffic(roof["kernel"].split()[0])
+    # secondary kernel roofline (pair ALU / VACF HBM) for completeness
+    b, pp, m, _ = SPEC["vacf"]
+    pushes = range(args.warmup + 1, args.warmup + args.steps + 1)
+    vacf_gbs = sum(vacf_bytes_per_push(t, b, pp, m, 3 * n, 4) for t in pushes) / (ktimes["vacf"][0] / 1e3) / 1e9
+    pair_tf = PAIR_FLOP_PER_ATOM * n * ktimes["pair"][1] / (ktimes["pair"][0] / 1e3) / 1e12
+
+    launches_per_step = 10  # kick_drift, 5 sort kernels, list build, pair, kick_reduce, VACF push
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 forces/fluxes/products + f64 state/reductions/lag sums",
+        "data": "synthetic (seeded fcc start melted at T*=2.0 then 0.722, Maxwell-Boltzmann velocities)",
+        "config": {"workload": workload_name(n), "n_atoms": n, "precision": "mixed", "pair": f"Verlet list, skin {SKIN}",
+                   "replicas": "one independent system per GPU" if world > 1 else "one system",
+                   "l2": "inputs larger than L2 (state + neighbour lists + VACF ring about 5 GB)",
+                   "timing": "CUDA events around every kernel on the system stream; eager launches"},
+        "clocks": clk.summary(),
+        "e2e": {"value": world * n * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "what": "md_init from host arrays + md_step(K) + md_observables + corr_read of all correlators"},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": roof,
+        "kernel_ms": {k: {"total_ms": v[0], "launch_brackets": v[1], "share": v[0] / kern_ms if kern_ms else None}
+                      for k, v in ktimes.items()},
+        "secondary_roofline": {"pair_alu_tflops": pair_tf, "pair_frac_fp32_peak": pair_tf / FP32_PEAK_TFLOPS,
+                               "vacf_hbm_gbs": vacf_gbs, "vacf_frac_hbm": vacf_gbs / peaks["hbm_gbs"]},
+        "graph_ms_per_step": graph_ms_step,
+        "fp64_gpu": {"ms_per_step": ms64, "value": world * n / (ms64 / 1e3), "steps": k64,
+                     "speedup_mixed_over_fp64": ms64 / ms_step},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(st, s, budget_s=args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def committed_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else null)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+    except OSError:
+        return None
+    ent = tr.get(kernel)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2503_07526_gb300", "csrc", ent["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return ent["bytes_per_launch"] if h == ent.get("source_sha") else None
+
+
+def cpu_baseline(st, s, budget_s=20.0):
+    """The FP64 oracle, as it stands, on the host cores: full 2,048,000-atom
+    system with the same correlators, timed over as many whole steps as fit
+    in the budget after one warm-up step."""
+    import oracle
+
+    n, L = s["n"], s["L"]
+    oracle.build()
+    cores = oracle.num_threads()
+    md = oracle.MD(st["r"], st["v"], L, rc=RC, dt=DT, cells=True)
+    cs = oracle.Corr(12, 16, 2, 6)  # sigma_xy, sigma_xz, sigma_yz, q_x, q_y, q_z
+    cv = oracle.Corr(8, 16, 2, 3 * n, gs=n)
+    md.step(1, cs=cs, cv=cv)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        md.step(1, cs=cs, cv=cv)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or steps >= 50:
+            break
+    return {"value": n * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} whole steps of the {n:,}-atom workload (link-cell forces, integration, "
+                      f"observables, stress/heat-flux and per-atom VACF correlators) after 1 warm-up step, "
+                      f"{el:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle on the host cores, on this arm's workload (rank 0 only)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2503_07526_gb300 import synth
+
+    import oracle
+
+    s = synth.lj_system(CELLS, rho=RHO, T=T_STAR, seed=1)
+    n, L = s["n"], s["L"]
+    oracle.build()
+    cores = oracle.num_threads()
+    md = oracle.MD(s["r"], s["v"], L, rc=RC, dt=DT, cells=True)
+    cs = oracle.Corr(12, 16, 2, 6)
+    cv = oracle.Corr(8, 16, 2, 3 * n, gs=n)
+    md.step(args.warmup, cs=cs, cv=cv)
+    t0 = time.perf_counter()
+    md.step(args.steps, cs=cs, cv=cv)
+    el = time.perf_counter() - t0
+    value = n * args.steps / el
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded fcc, Maxwell-Boltzmann)",
+           "impl": "reference",
+           "config": {"workload": workload_name(n) + " (fcc start, not melted)", "n_atoms": n, "precision": "fp64"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{args.steps} timed steps of the full workload after {args.warmup} warm-up"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -81,12 +81,15 @@ struct Vec4<double> {
   }
 };
 
-__device__ __forceinline__ float fast_rcp(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
+// 1/x: hardware approximation refined by one Newton-Raphson step
+// (y <- y + y (1 - x y)), which brings it to within about half an ulp.
+__device__ __forceinline__ float pair_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  const float e = fmaf(-x, y, 1.0f);
+  return fmaf(y, e, y);
 }
-__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ double pair_rcp(double x) { return 1.0 / x; }
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 

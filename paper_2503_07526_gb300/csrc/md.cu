@@ -5,8 +5,9 @@
 // GB300 design.  Atoms live in a cell-sorted structure of arrays that is
 // rebuilt by a counting sort when any atom has moved half the skin.  Each
 // atom also carries its coordinates relative to the origin of the cell it
-// was sorted into, in the arithmetic type of the pair path, so the FP32
-// form never subtracts two large absolute coordinates.  A step is a fixed
+// was sorted into, measured from the cell centre (|rel| <= edge/2, which
+// halves their FP32 rounding), in the arithmetic type of the pair path, so
+// the FP32 form never subtracts two large absolute coordinates.  A step is a fixed
 // sequence of kernels (no host decision inside it), so it is captured once
 // as a CUDA graph and replayed; the rebuild kernels read a device flag and
 // return at once when no rebuild is due.
@@ -98,9 +99,9 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift(Sys d, double hdt) {
     }
     int cx, cy, cz;
     unpack_cell(d.cpk[i], cx, cy, cz);
-    const TF px = (TF)fma(-(double)cx, d.edge, x[0]);
-    const TF py = (TF)fma(-(double)cy, d.edge, x[1]);
-    const TF pz = (TF)fma(-(double)cz, d.edge, x[2]);
+    const TF px = (TF)fma(-(cx + 0.5), d.edge, x[0]);
+    const TF py = (TF)fma(-(cy + 0.5), d.edge, x[1]);
+    const TF pz = (TF)fma(-(cz + 0.5), d.edge, x[2]);
     Vec4<TF>::store(rel + i, px, py, pz);
     const V4 b = Vec4<TF>::load(relb + i);
     const TF dx = px - b.x, dy = py - b.y, dz = pz - b.z;
@@ -230,9 +231,9 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_rb_rank(Sys d) {
         d.id[dst] = key;
         d.type[dst] = d.typeB[a];
         d.cpk[dst] = pack_cell(cx, cy, cz);
-        const TF px = (TF)fma(-(double)cx, d.edge, x[0]);
-        const TF py = (TF)fma(-(double)cy, d.edge, x[1]);
-        const TF pz = (TF)fma(-(double)cz, d.edge, x[2]);
+        const TF px = (TF)fma(-(cx + 0.5), d.edge, x[0]);
+        const TF py = (TF)fma(-(cy + 0.5), d.edge, x[1]);
+        const TF pz = (TF)fma(-(cz + 0.5), d.edge, x[2]);
         Vec4<TF>::store(static_cast<V4 *>(d.rel) + dst, px, py, pz);
         Vec4<TF>::store(static_cast<V4 *>(d.relb) + dst, px, py, pz);
       }
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_rb_rank(Sys d) {
 template <typename TF>
 __device__ __forceinline__ void lj_accumulate(const LJ<TF> &lj, TF dx, TF dy, TF dz, TF r2, TF f[3],
                                               TF &e, TF w[6]) {
-  const TF ir2 = fast_rcp(r2);
+  const TF ir2 = pair_rcp(r2);
   const TF s2 = lj.sig2 * ir2;
   const TF s6 = s2 * s2 * s2;
   const TF u = lj.eps4 * s6 * (s6 - TF(1)) - lj.ushift;
@@ -331,9 +332,9 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
           for (int t = 0; t < nj; ++t) {
             const V4 pj = spos[wl][t];
             const int j = sidx[wl][t];
-            const TF dx = (pi.x - pj.x) - offx;
-            const TF dy = (pi.y - pj.y) - offy;
-            const TF dz = (pi.z - pj.z) - offz;
+            const TF dx = pi.x - (pj.x + offx);
+            const TF dy = pi.y - (pj.y + offy);
+            const TF dz = pi.z - (pj.z + offz);
             const TF r2 = dx * dx + dy * dy + dz * dz;
             if (BUILD) {
               if (r2 < lj.rlist2 && j != i) {
@@ -386,9 +387,11 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_list(Sys d, LJ<TF> lj) {
     const int j = (int)(ent & 0x07ffffffu);
     const int code = (int)(ent >> 27);
     const V4 pj = Vec4<TF>::load(rel + j);
-    const TF dx = (pi.x - pj.x) - off[code][0];
-    const TF dy = (pi.y - pj.y) - off[code][1];
-    const TF dz = (pi.z - pj.z) - off[code][2];
+    // j moved into i's cell frame first: for a close pair across a cell face
+    // pj + off lands next to pi, so the final subtraction is exact.
+    const TF dx = pi.x - (pj.x + off[code][0]);
+    const TF dy = pi.y - (pj.y + off[code][1]);
+    const TF dz = pi.z - (pj.z + off[code][2]);
     const TF r2 = dx * dx + dy * dy + dz * dz;
     if (r2 < lj.rc2) lj_accumulate<TF>(lj, dx, dy, dz, r2, f, e, w);
   }
