@@ -41,7 +41,7 @@ PAIR_FLOP_PER_ATOM = 0.5 * RHO * (4.0 / 3.0) * math.pi * RC ** 3 * 50.0  # uniqu
 
 
 def workload_name(n):
-    return (f"LJ liquid {n:,} atoms (fcc {CELLS}^3 x 4 melted), rho*={RHO}, T*={T_STAR}, rc={RC} shifted, "
+    return (f"LJ liquid {n:,} atoms (fcc {round((n / 4) ** (1 / 3))}^3 x 4 melted), rho*={RHO}, T*={T_STAR}, rc={RC} shifted, "
             f"dt={DT}, velocity Verlet NVE; on-the-fly correlators: stress xy/xz/yz and heat flux "
             f"(b=12,p=16,m=2,u=1), per-atom VACF over all atoms (b=8,p=16,m=2,u=1)")
 
@@ -153,15 +153,15 @@ def melt(sysg, target_T, steps, every=10):
         sysg.scale_velocities(math.sqrt(target_T / T))
 
 
-def prepare_state(pkg, synth, seed):
-    """Melted liquid at T* (untimed): rescale to T* = 2.0 for 600 steps, then
-    to T* = 0.722 for 600 steps, on the mixed-precision path."""
-    s = synth.lj_system(CELLS, rho=RHO, T=T_STAR, seed=seed)
+def prepare_state(pkg, synth, seed, cells=CELLS, melt_steps=600):
+    """Melted liquid at T* (untimed): rescale to T* = 2.0 for melt_steps
+    steps, then to T* = 0.722 for melt_steps steps, on the mixed path."""
+    s = synth.lj_system(cells, rho=RHO, T=T_STAR, seed=seed)
     p = pkg.make_params(s["n"], s["L"], rc=RC, dt=DT, skin=SKIN, precision=pkg.MD_PREC_MIXED,
                         stress=None, heatflux=None, vacf=None)
     g = pkg.System(p, s["r"], s["v"])
-    melt(g, 2.0, 600)
-    melt(g, T_STAR, 600)
+    melt(g, 2.0, melt_steps)
+    melt(g, T_STAR, melt_steps)
     st = g.particles()
     g.close()
     return s, st
@@ -181,7 +181,7 @@ def run_ours(args):
     from paper_2503_07526_gb300 import synth
 
     pkg.lib()
-    s, st = prepare_state(pkg, synth, seed=1 + rank)
+    s, st = prepare_state(pkg, synth, seed=1 + rank, cells=args.cells, melt_steps=100 if args.quick else 600)
     n, L = s["n"], s["L"]
     p = pkg.make_params(n, L, rc=RC, dt=DT, skin=SKIN, precision=pkg.MD_PREC_MIXED, **SPEC)
     g = pkg.System(p, st["r"], st["v"])
@@ -222,6 +222,11 @@ def run_ours(args):
     barrier()
     graph_ms_step = e0.elapsed_time(e1) / args.steps
     g.close()
+    if args.quick:  # profiling runs: timed region only
+        if rank == 0:
+            print(json.dumps({"quick": True, "n_atoms": n, "ms_per_step": ms_step, "graph_ms_per_step": graph_ms_step,
+                              "kernel_ms": ktimes}), flush=True)
+        return
 
     # --- plain FP64 GPU path on the same state (the comparison form)
     k64 = max(3, args.steps // 10)
@@ -408,6 +413,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cells", type=int, default=CELLS, help="fcc cells per side (4 cells^3 atoms)")
+    ap.add_argument("--quick", action="store_true", help="short melt, timed region only (for profilers)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -52,6 +52,8 @@ def lib():
                                        C.c_double, C.c_int, dp, dp, dp]
             L.orc_lj_cells.argtypes = [i64, dp, C.c_double, C.c_double, C.c_double, C.c_double,
                                        C.c_int, dp, dp, dp]
+            L.orc_lj_near_cutoff.argtypes = [i64, dp, C.c_double, C.c_double, C.c_double,
+                                             C.POINTER(C.c_int32)]
             L.orc_observables.argtypes = [i64, C.c_double, dp, dp, dp, dp, dp]
             L.orc_observables.restype = None
             L.orc_corr_new.argtypes = [C.c_int, C.c_int, C.c_int, i64, i64, C.c_int]
@@ -112,6 +114,16 @@ def lj_forces(r, L, *, rc=2.5, eps=1.0, sig=1.0, shift=True, method="cells", per
     if rc_ != 0:
         raise ValueError(f"oracle force call failed ({rc_})")
     return F, e, W
+
+
+def near_cutoff_pairs(r, L, rc=2.5, band=1e-5):
+    """Per atom, neighbours whose distance is within band of rc (test helper
+    for reduced-precision forces: the truncated force jumps there)."""
+    r = _f64(r)
+    out = np.zeros(r.shape[1], dtype=np.int32)
+    if lib().orc_lj_near_cutoff(r.shape[1], _d(r), L, rc, band, out.ctypes.data_as(C.POINTER(C.c_int32))) != 0:
+        raise ValueError("near-cutoff count failed")
+    return out
 
 
 def observables(V, mass_of, v, epot, W):

@@ -197,6 +197,59 @@ int orc_lj_cells(int64_t n, const double *r, double L, double eps, double sig,
   return ORC_OK;
 }
 
+/* For tests of reduced-precision forces: per atom, the number of
+ * neighbours whose distance lies within band of rc, where the truncated
+ * force jumps by |f(rc)| and a rounded distance may fall on either side of
+ * the cutoff (both results are then valid).  Link cells as above. */
+int orc_lj_near_cutoff(int64_t n, const double *r, double L, double rc, double band,
+                       int32_t *count) {
+  if (n < 0 || rc <= 0.0 || band < 0.0) return ORC_EINVAL;
+  int nc = (int)floor(L / rc);
+  if (nc < 3) return ORC_EINVAL;
+  double edge = L / nc;
+  int64_t ncell = (int64_t)nc * nc * nc;
+  int64_t *head = malloc(sizeof(int64_t) * ncell);
+  int64_t *next = malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+  int64_t *cell = malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+  if (!head || !next || !cell) {
+    free(head); free(next); free(cell);
+    return ORC_ENOMEM;
+  }
+  for (int64_t c = 0; c < ncell; ++c) head[c] = -1;
+  for (int64_t i = 0; i < n; ++i) {
+    int ci[3];
+    for (int a = 0; a < 3; ++a) {
+      ci[a] = (int)floor(wrap_box(r[a * n + i], L) / edge);
+      if (ci[a] >= nc) ci[a] = nc - 1;
+    }
+    cell[i] = ((int64_t)ci[2] * nc + ci[1]) * nc + ci[0];
+    next[i] = head[cell[i]];
+    head[cell[i]] = i;
+  }
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t c = cell[i];
+    int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
+    int32_t k = 0;
+    for (int oz = -1; oz <= 1; ++oz)
+      for (int oy = -1; oy <= 1; ++oy)
+        for (int ox = -1; ox <= 1; ++ox) {
+          int jx = (cx + ox + nc) % nc, jy = (cy + oy + nc) % nc, jz = (cz + oz + nc) % nc;
+          for (int64_t j = head[((int64_t)jz * nc + jy) * nc + jx]; j >= 0; j = next[j]) {
+            if (j == i) continue;
+            double dx = min_image(r[i] - r[j], L);
+            double dy = min_image(r[n + i] - r[n + j], L);
+            double dz = min_image(r[2 * n + i] - r[2 * n + j], L);
+            double d = sqrt(dx * dx + dy * dy + dz * dz);
+            if (fabs(d - rc) <= band) ++k;
+          }
+        }
+    count[i] = k;
+  }
+  free(head); free(next); free(cell);
+  return ORC_OK;
+}
+
 /* ------------------------------------------------- system observables */
 
 #define ORC_NOBS 12 /* U, K, T, sigma[6] (xx yy zz xy xz yz), q[3] */

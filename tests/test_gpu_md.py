@@ -47,10 +47,24 @@ def params(pkg, s, **kw):
     return pkg.make_params(s["n"], s["L"], **kw)
 
 
-def check_mixed_forces(F, Fo):
+F_AT_RC = 24 * (2 * 2.5 ** -12 - 2.5 ** -6) / 2.5  # truncated LJ force at the cutoff
+
+
+def check_mixed_forces(F, Fo, r=None, L=None, oracle_mod=None):
+    """|dF_ia| <= 2e-5 max(|F_ia|, F_rms), plus one force jump |f(rc)| for each
+    pair of atom i lying within 1e-5 rc of the cutoff, where FP32 and FP64
+    distances may fall on opposite sides of rc (both results valid)."""
     frms = np.sqrt((Fo ** 2).mean())
-    ratio = np.abs(F - Fo) / np.maximum(np.abs(Fo), frms)
-    print(f"mixed forces: max |dF|/max(|F|, F_rms) = {ratio.max():.3e} (F_rms {frms:.3f})")
+    allow = np.zeros(F.shape[1])
+    if r is not None:
+        near = oracle_mod.near_cutoff_pairs(r, L, 2.5, 1e-5 * 2.5)
+        allow = 1.001 * abs(F_AT_RC) * near
+    dF = np.abs(F - Fo)
+    ratio = np.maximum(dF - allow[None, :], 0.0) / np.maximum(np.abs(Fo), frms)
+    clean = (allow == 0)[None, :].repeat(3, axis=0)
+    print(f"mixed forces: max |dF|/max(|F|, F_rms) = {ratio.max():.3e} (F_rms {frms:.3f}); "
+          f"atoms with a pair within 1e-5 rc of the cutoff: {(allow > 0).sum()}; "
+          f"max over the others {(dF[clean] / np.maximum(np.abs(Fo[clean]), frms)).max():.3e}")
     assert ratio.max() <= 2e-5
 
 
@@ -83,7 +97,7 @@ def test_initial_forces_mixed(pkg, oracle_mod, cells, mode):
     g = pkg.System(params(pkg, s, precision=pkg.MD_PREC_MIXED, pair_mode=pm), s["r"], s["v"])
     got = g.particles()
     F, e, W = oracle_mod.lj_forces(s["r"], s["L"], method="cells")
-    check_mixed_forces(got["F"], F)
+    check_mixed_forces(got["F"], F, s["r"], s["L"], oracle_mod)
     assert np.abs(got["epot"] - e).max() <= 2e-5 * np.abs(e).max()
     assert np.abs(got["W"] - W).max() <= 2e-5 * np.abs(W).max()
 
@@ -124,7 +138,7 @@ def test_mixed_forces_along_trajectory(pkg, oracle_mod):
         g.step(1)
         got = g.particles()
         F, e, W = oracle_mod.lj_forces(got["r"], s["L"], method="cells")
-        check_mixed_forces(got["F"], F)
+        check_mixed_forces(got["F"], F, got["r"], s["L"], oracle_mod)
         obs = g.observables()
         want = oracle_mod.observables(s["L"] ** 3, np.ones(s["n"]), got["v"], got["epot"], got["W"])
         scale = np.abs(want[3:6]).max()
@@ -252,7 +266,7 @@ def test_full_size_mixed_forces_and_reduction(pkg, oracle_mod):
     g.step(2)
     got = g.particles()
     F, e, W = oracle_mod.lj_forces(got["r"], s["L"], method="cells")
-    check_mixed_forces(got["F"], F)
+    check_mixed_forces(got["F"], F, got["r"], s["L"], oracle_mod)
     obs = g.observables()
     want = oracle_mod.observables(s["L"] ** 3, np.ones(s["n"]), got["v"], got["epot"], got["W"])
     scale = np.abs(want[3:6]).max()
@@ -268,4 +282,4 @@ def test_lattice_start_mixed_forces(pkg, oracle_mod):
     g.step(2)
     got = g.particles()
     F, _, _ = oracle_mod.lj_forces(got["r"], s["L"], method="cells")
-    check_mixed_forces(got["F"], F)
+    check_mixed_forces(got["F"], F, got["r"], s["L"], oracle_mod)
