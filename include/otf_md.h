@@ -111,6 +111,7 @@ typedef struct {
   double sigma[6];     /* pressure tensor: (sum m v v + sum_i W_i) / V */
   double q[3];         /* heat flux: sum_i (E_i v_i + W_i v_i) / V */
   double T_mean;       /* mean of T over the steps since md_init */
+  int64_t rebuilds;    /* cell sorts / neighbour-list builds since md_init */
 } md_obs;
 
 typedef struct md_handle_s md_handle;

@@ -50,7 +50,8 @@ class md_system(C.Structure):
 
 class md_obs(C.Structure):
     _fields_ = [("step", C.c_int64), ("U", C.c_double), ("K", C.c_double), ("T", C.c_double),
-                ("sigma", C.c_double * 6), ("q", C.c_double * 3), ("T_mean", C.c_double)]
+                ("sigma", C.c_double * 6), ("q", C.c_double * 3), ("T_mean", C.c_double),
+                ("rebuilds", C.c_int64)]
 
 
 class corr_params(C.Structure):
@@ -267,7 +268,7 @@ class System:
         o = md_obs()
         _check(lib().md_observables(self._h, C.byref(o)))
         return dict(step=o.step, U=o.U, K=o.K, T=o.T, sigma=np.array(o.sigma[:]), q=np.array(o.q[:]),
-                    T_mean=o.T_mean)
+                    T_mean=o.T_mean, rebuilds=o.rebuilds)
 
     def particles(self):
         n = self.n

@@ -32,6 +32,7 @@ struct ObsDev {
   int64_t step;       // steps completed
   int64_t corr_base;  // step at the last correlator reset
   int64_t Tn;
+  int64_t rebuilds;   // neighbour-list / cell rebuilds since md_init
   double U, K, T;
   double sigma[6];
   double q[3];
@@ -186,7 +187,10 @@ __global__ void __launch_bounds__(1024) k_rb_scan(Sys d) {
     d.cellstart[c] = run;
     run += d.cellcount[c];
   }
-  if (tid == 0) d.cellstart[nc3] = (int)d.n;
+  if (tid == 0) {
+    d.cellstart[nc3] = (int)d.n;
+    d.obs->rebuilds += 1;
+  }
 }
 
 __global__ void __launch_bounds__(kThreads) k_rb_place(Sys d) {
@@ -1000,6 +1004,7 @@ int md_observables(md_handle *h, md_obs *out) {
   for (int a = 0; a < 6; ++a) out->sigma[a] = o.sigma[a];
   for (int a = 0; a < 3; ++a) out->q[a] = o.q[a];
   out->T_mean = o.Tn > 0 ? o.Tsum / (double)o.Tn : o.T;
+  out->rebuilds = o.rebuilds;
   return MD_OK;
 }
 
