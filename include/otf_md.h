@@ -226,6 +226,26 @@ OTF_API void corr_free(corr_handle *c);
 OTF_API int gk_integrate(const double *t, const double *c, int64_t n, double t_cut, double prefactor,
                  double *integral, double *running);
 
+/* Allocation-free observables: the paper has no counterpart to this call.
+ * It exists for host programs that cannot call cudaMalloc while they run,
+ * such as engines that hand all device memory to their own fixed pool at
+ * start-up, or pipelines that must not take the device-wide synchronisation
+ * cudaMalloc / cudaFree may cause.  It computes, from caller device arrays
+ * (FP64): obs[12] = U, K, T = 2K/(3n-3), sigma[6] (xx yy zz xy xz yz) and
+ * q[3], with sigma = (sum_i m_i v_i v_i + sum_i W_i) / volume and
+ * q = sum_i (E_i v_i + W_i v_i) / volume, E_i = m_i v_i^2 / 2 + epot_i;
+ * v [3][n], epot [n], W [6][n], mass_of [n], obs [12] device output.  The
+ * work is enqueued on cuda_stream and the call returns without waiting.
+ * Its scratch is a fixed array inside the library (partial sums for 1024
+ * CTAs, about 90 KB per GPU, held until the process exits); n may be up to
+ * 2^27 - 1 and larger n is rejected with MD_EINVAL.  The first call on each
+ * device looks up that array's address and clears it, so make it before any
+ * stream capture.  All calls on one device share the array: calls that
+ * overlap on the GPU race. */
+OTF_API int md_observables_noalloc(int64_t n, double volume, const double *v, const double *epot,
+                                   const double *W, const double *mass_of, double *obs,
+                                   void *cuda_stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 OTF_API const char *md_last_error(void);
 

@@ -24,4 +24,5 @@ from ._lib import (  # noqa: F401
     gk_integrate,
     lib,
     make_params,
+    observables_noalloc,
 )

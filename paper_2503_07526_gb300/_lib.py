@@ -91,6 +91,7 @@ def lib(build: bool = False):
         "corr_pushes": [vp, C.POINTER(C.c_int64)],
         "corr_reset": [vp],
         "gk_integrate": [dp, dp, i64, C.c_double, C.c_double, dp, dp],
+        "md_observables_noalloc": [i64, C.c_double, vp, vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -109,7 +110,7 @@ def lib(build: bool = False):
 EXPORTS = ("md_init", "md_step", "md_observables", "md_get_particles", "md_scale_velocities",
            "md_reset_correlators", "md_corr", "md_set_timing", "md_kernel_times", "md_free", "corr_create",
            "corr_push", "corr_read", "corr_raw", "corr_pushes", "corr_reset", "corr_free", "gk_integrate",
-           "md_last_error")
+           "md_last_error", "md_observables_noalloc")
 
 
 def _check(rc):
@@ -323,3 +324,11 @@ def gk_integrate(t, c, t_cut=float("inf"), prefactor=1.0):
     _check(lib().gk_integrate(t.ctypes.data_as(dp), c.ctypes.data_as(dp), t.size, float(t_cut), float(prefactor),
                               C.byref(out), run.ctypes.data_as(dp)))
     return out.value, run
+
+
+def observables_noalloc(volume, v, epot, W, mass_of, obs, stream=None):
+    """md_observables_noalloc on CUDA tensors (float64): v [3,n], epot [n],
+    W [6,n], mass_of [n] in, obs [12] out; enqueued on the stream."""
+    n = v.shape[1]
+    _check(lib().md_observables_noalloc(n, float(volume), v.data_ptr(), epot.data_ptr(), W.data_ptr(),
+                                        mass_of.data_ptr(), obs.data_ptr(), _stream_ptr(stream)))
