@@ -29,22 +29,82 @@ __global__ void k_push_series(CorrDev c, const Tin *__restrict__ x, const Tin *_
   }
 }
 
-// Grouped correlators (e.g. the per-atom velocity autocorrelation): block
-// (cx, g) owns a fixed slice of group g's series; per block, each block
-// touched by the push streams its ring planes once, forms the lag products
-// in registers (A = accumulation type: float in the mixed form, double in
-// FP64), reduces them over the CTA with warp shuffles and adds the FP64 sum
-// into its own row of partial lag sums (no atomics: deterministic).
-template <typename T, typename Tin, int PMAX>
+// Vector access of V consecutive elements (16-byte aligned when V > 1).
+template <typename E, int V>
+struct VecIO {
+  __device__ __forceinline__ static void load(const E *p, E *o) {
+#pragma unroll
+    for (int q = 0; q < V; ++q) o[q] = p[q];
+  }
+  __device__ __forceinline__ static void store(E *p, const E *v) {
+#pragma unroll
+    for (int q = 0; q < V; ++q) p[q] = v[q];
+  }
+};
+template <>
+struct VecIO<float, 4> {
+  __device__ __forceinline__ static void load(const float *p, float *o) {
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    o[0] = a.x, o[1] = a.y, o[2] = a.z, o[3] = a.w;
+  }
+  __device__ __forceinline__ static void store(float *p, const float *v) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <>
+struct VecIO<double, 2> {
+  __device__ __forceinline__ static void load(const double *p, double *o) {
+    const double2 a = *reinterpret_cast<const double2 *>(p);
+    o[0] = a.x, o[1] = a.y;
+  }
+  __device__ __forceinline__ static void store(double *p, const double *v) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+  }
+};
+template <>
+struct VecIO<double, 4> {
+  __device__ __forceinline__ static void load(const double *p, double *o) {
+    VecIO<double, 2>::load(p, o);
+    VecIO<double, 2>::load(p + 2, o + 2);
+  }
+};
+
+// Input samples of V series, converted to the ring type.
+template <typename T, typename Tin, int V, bool VIN>
+__device__ __forceinline__ void load_input(const Tin *p, T *o) {
+  Tin a[V];
+  if (VIN)
+    VecIO<Tin, V>::load(p, a);
+  else
+#pragma unroll
+    for (int q = 0; q < V; ++q) a[q] = p[q];
+#pragma unroll
+  for (int q = 0; q < V; ++q) o[q] = (T)a[q];
+}
+
+constexpr int kLagChunk = 8;  // ring loads issued together per thread
+
+// Grouped correlators (e.g. the per-atom velocity autocorrelation).  Thread
+// (cx, g, tid) owns the V consecutive series s = g gs + (cx blockDim + tid) V
+// for good (so the per-block partial sums are deterministic), and each push
+// is a pure stream: for every block the push reaches, the thread stores the
+// new sample and loads kLagChunk older ring vectors at a time (16-byte
+// loads, one plane per lag: coalesced across the warp), forms the lag
+// products in the ring type (FP32 in the mixed form), sums them over its V
+// series and the warp with shuffles, then the CTA adds the FP64 sum over its
+// warps into its own row of partial lag sums.  VIN: the input is 16-byte
+// aligned and can be read as vectors.
+template <typename T, typename Tin, int V, bool VIN>
 __global__ void __launch_bounds__(kPushThreads)
     k_push_grouped(CorrDev c, const Tin *__restrict__ x, const Tin *__restrict__ y, PushIdx pi) {
   int64_t t;
   if (!resolve_push(pi, &t)) return;
-  __shared__ double red[kPushWarps][PMAX];
+  __shared__ double red[kPushWarps][64];
   const int g = blockIdx.y, cx = blockIdx.x;
   const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x / kWarp;
-  const int64_t base = (int64_t)g * c.gs;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = ((int64_t)cx * blockDim.x + threadIdx.x) * V;  // index within the group
+  const bool act = i0 < c.gs;
+  const int64_t s = (int64_t)g * c.gs + (act ? i0 : 0);
   const int64_t plane = c.ns;
   T *rx = static_cast<T *>(c.ringx);
   T *ry = c.cross ? static_cast<T *>(c.ringy) : rx;
@@ -59,59 +119,81 @@ __global__ void __launch_bounds__(kPushThreads)
     const int lo = (k == 0) ? 0 : c.p / c.m;
     const int nl = (int)min((int64_t)c.p - 1, nk - 1) - lo + 1;
     T *rxk = rx + (int64_t)k * c.p * plane;
-    T *ryk = ry + (int64_t)k * c.p * plane;
-    T acc[PMAX];
+    T xk[V], yk[V];
 #pragma unroll
-    for (int l = 0; l < PMAX; ++l) acc[l] = T(0);
-    int jl[PMAX];
-#pragma unroll
-    for (int l = 0; l < PMAX; ++l) {
-      int j = slot - lo - l;
-      if (j < 0) j += c.p;
-      jl[l] = j;
-    }
-    for (int64_t i = cx * (int64_t)blockDim.x + threadIdx.x; i < c.gs; i += stride) {
-      const int64_t s = base + i;
-      T xk, yk;
+    for (int q = 0; q < V; ++q) xk[q] = yk[q] = T(0);
+    if (act) {
       if (k == 0) {
-        xk = (T)x[s];
-        yk = c.cross ? (T)y[s] : xk;
+        load_input<T, Tin, V, VIN>(x + s, xk);
+        if (c.cross)
+          load_input<T, Tin, V, VIN>(y + s, yk);
       } else {
+        // block k's sample: mean of block k-1's last m samples, oldest first
         const int64_t nprev = nk * c.m;
         const T *rp = rx + (int64_t)(k - 1) * c.p * plane;
         const T *rq = ry + (int64_t)(k - 1) * c.p * plane;
-        T sx = T(0), sy = T(0);
+        T sx[V], sy[V], a[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) sx[q] = sy[q] = T(0);
         for (int j = c.m - 1; j >= 0; --j) {
           const int sl = (int)((nprev - 1 - j) % c.p);
-          sx += rp[sl * plane + s];
-          if (c.cross) sy += rq[sl * plane + s];
-        }
-        xk = sx / T(c.m);
-        yk = c.cross ? sy / T(c.m) : xk;
-      }
-      rxk[slot * plane + s] = xk;
-      if (c.cross) ryk[slot * plane + s] = yk;
+          VecIO<T, V>::load(rp + sl * plane + s, a);
 #pragma unroll
-      for (int l = 0; l < PMAX; ++l) {
-        if (l < nl) {
-          const T older = (lo + l == 0) ? xk : rxk[jl[l] * plane + s];
-          acc[l] += older * yk;
+          for (int q = 0; q < V; ++q) sx[q] += a[q];
+          if (c.cross) {
+            VecIO<T, V>::load(rq + sl * plane + s, a);
+#pragma unroll
+            for (int q = 0; q < V; ++q) sy[q] += a[q];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+          xk[q] = sx[q] / T(c.m);
+          yk[q] = sy[q] / T(c.m);
+        }
+      }
+      if (!c.cross)
+#pragma unroll
+        for (int q = 0; q < V; ++q) yk[q] = xk[q];
+      VecIO<T, V>::store(rxk + slot * plane + s, xk);
+      if (c.cross) VecIO<T, V>::store(ry + (int64_t)k * c.p * plane + slot * plane + s, yk);
+    }
+    for (int l0 = 0; l0 < nl; l0 += kLagChunk) {
+      T older[kLagChunk][V];
+#pragma unroll
+      for (int l = 0; l < kLagChunk; ++l) {
+        const int lag = lo + l0 + l;
+        if (act && l0 + l < nl) {
+          if (lag == 0) {
+#pragma unroll
+            for (int q = 0; q < V; ++q) older[l][q] = xk[q];
+          } else {
+            int j = slot - lag;
+            if (j < 0) j += c.p;
+            VecIO<T, V>::load(rxk + j * plane + s, older[l]);
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < V; ++q) older[l][q] = T(0);
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < kLagChunk; ++l) {
+        if (l0 + l < nl) {
+          T a = T(0);
+#pragma unroll
+          for (int q = 0; q < V; ++q) a += older[l][q] * yk[q];
+          a = warp_sum(a);
+          if (lane == 0) red[warp][l0 + l] = (double)a;
         }
       }
     }
     if (nl <= 0) continue;  // uniform over the grid
-#pragma unroll
-    for (int l = 0; l < PMAX; ++l) {
-      if (l < nl) {
-        const T v = warp_sum(acc[l]);
-        if (lane == 0) red[warp][l] = (double)v;
-      }
-    }
     __syncthreads();
     if (threadIdx.x < nl) {
-      double s = 0.0;
-      for (int w = 0; w < kPushWarps; ++w) s += red[w][threadIdx.x];
-      c.vals[(((int64_t)g * c.nchunk + cx) * c.b + k) * c.p + lo + threadIdx.x] += s;
+      double sum = 0.0;
+      for (int w = 0; w < kPushWarps; ++w) sum += red[w][threadIdx.x];
+      c.vals[(((int64_t)g * c.nchunk + cx) * c.b + k) * c.p + lo + threadIdx.x] += sum;
     }
     __syncthreads();
   }
@@ -131,12 +213,17 @@ __global__ void k_fold(CorrDev c, double *__restrict__ out) {
 template <typename T, typename Tin>
 int launch_grouped(const CorrDev &c, const Tin *x, const Tin *y, PushIdx pi, cudaStream_t s) {
   dim3 grid(c.nchunk, (unsigned)c.ng);
-  if (c.p <= 16)
-    k_push_grouped<T, Tin, 16><<<grid, kPushThreads, 0, s>>>(c, x, y, pi);
-  else if (c.p <= 32)
-    k_push_grouped<T, Tin, 32><<<grid, kPushThreads, 0, s>>>(c, x, y, pi);
-  else
-    k_push_grouped<T, Tin, 64><<<grid, kPushThreads, 0, s>>>(c, x, y, pi);
+  constexpr int V = 16 / sizeof(T);
+  if (c.vec == V) {
+    const bool vin = (reinterpret_cast<uintptr_t>(x) % (V * sizeof(Tin)) == 0) &&
+                     (!c.cross || reinterpret_cast<uintptr_t>(y) % (V * sizeof(Tin)) == 0);
+    if (vin)
+      k_push_grouped<T, Tin, V, true><<<grid, kPushThreads, 0, s>>>(c, x, y, pi);
+    else
+      k_push_grouped<T, Tin, V, false><<<grid, kPushThreads, 0, s>>>(c, x, y, pi);
+  } else {
+    k_push_grouped<T, Tin, 1, false><<<grid, kPushThreads, 0, s>>>(c, x, y, pi);
+  }
   OTF_LAUNCH_CHECK();
   return MD_OK;
 }
@@ -187,10 +274,13 @@ int Correlator::create(const corr_params &p, cudaStream_t s) {
   dev.gs = p.group_size;
   dev.ng = p.nseries / p.group_size;
   if (grouped) {
-    const int64_t target = 152 * 8;  // resident CTAs of 256 threads on 152 SMs
-    int64_t per_group = std::max<int64_t>(1, target / dev.ng);
-    dev.nchunk = (int)std::max<int64_t>(1, std::min<int64_t>(per_group, (dev.gs + kPushThreads - 1) / kPushThreads));
+    // one 16-byte vector of series per thread when the group size allows it
+    const int vw = (int)(16 / (p.precision == MD_PREC_FP64 ? sizeof(double) : sizeof(float)));
+    dev.vec = (dev.gs % vw == 0) ? vw : 1;
+    const int64_t per_block = (int64_t)kPushThreads * dev.vec;
+    dev.nchunk = (int)((dev.gs + per_block - 1) / per_block);
   } else {
+    dev.vec = 1;
     dev.nchunk = 1;
   }
   const size_t esz = prec == MD_PREC_FP64 ? sizeof(double) : sizeof(float);

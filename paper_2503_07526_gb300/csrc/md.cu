@@ -26,7 +26,7 @@ constexpr int kThreads = 256;
 constexpr int kPairThreads = 128;
 constexpr int kCellWarps = 4;  // warps (cells) per CTA in the link-cell kernels
 constexpr int kNRed = 11;      // K, U, V*sigma[6], V*q[3]
-constexpr int kMaxRedBlocks = 152 * 4;
+constexpr int kMaxRedBlocks = 152 * 16;
 
 struct ObsDev {
   int64_t step;       // steps completed
@@ -148,46 +148,59 @@ __global__ void __launch_bounds__(kThreads) k_rb_assign(Sys d) {
     d.typeB[i] = t;
     const int c = (ci[2] * nc + ci[1]) * nc + ci[0];
     d.cellB[i] = c;
-    d.slot[i] = atomicAdd(&d.cellcount[c], 1);
+    // lanes binning into the same cell share one atomic (consecutive atoms
+    // are mostly in the same cell): the leader reserves their slots
+    const unsigned grp = __match_any_sync(__activemask(), c);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&d.cellcount[c], __popc(grp));
+    base = __shfl_sync(grp, base, leader);
+    d.slot[i] = base + __popc(grp & ((1u << lane) - 1u));
   }
 }
 
-// Exclusive scan of the cell counts (one CTA of 1024 threads).
+// Exclusive scan of the cell counts (one CTA of 1024 threads).  Warp w owns
+// a contiguous segment and reads it in coalesced rows of 32: pass 1 sums the
+// segments, warp 0 scans the 32 sums, pass 2 scans each row with shuffles
+// and a running carry.
 __global__ void __launch_bounds__(1024) k_rb_scan(Sys d) {
   if (!*d.rebuild) return;
   __shared__ int wsum[32];
   const int64_t nc3 = d.ncell;
-  const int tid = threadIdx.x;
-  const int64_t per = (nc3 + blockDim.x - 1) / blockDim.x;
-  const int64_t c0 = tid * per, c1 = min(nc3, c0 + per);
-  int local = 0;
-  for (int64_t c = c0; c < c1; ++c) local += d.cellcount[c];
-  // block exclusive scan of local
-  const int lane = tid & 31, warp = tid >> 5;
-  int incl = local;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) wsum[warp] = incl;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t seg = (nc3 + 31) / 32;
+  const int64_t c0 = warp * seg, c1 = min(nc3, c0 + seg);
+  int part = 0;
+  for (int64_t c = c0 + lane; c < c1; c += 32) part += d.cellcount[c];
+  part = warp_sum(part);
+  if (lane == 0) wsum[warp] = part;
   __syncthreads();
   if (warp == 0) {
-    int w = wsum[lane];
+    const int v = wsum[lane];
+    int incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
-    wsum[lane] = w;
+    wsum[lane] = incl - v;  // exclusive offset of each segment
   }
   __syncthreads();
-  int run = incl - local + (warp > 0 ? wsum[warp - 1] : 0);
-  for (int64_t c = c0; c < c1; ++c) {
-    d.cellstart[c] = run;
-    run += d.cellcount[c];
+  int carry = wsum[warp];
+  for (int64_t b = c0; b < c1; b += 32) {
+    const int64_t c = b + lane;
+    const int v = c < c1 ? d.cellcount[c] : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (c < c1) d.cellstart[c] = carry + incl - v;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
   }
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     d.cellstart[nc3] = (int)d.n;
     d.obs->rebuilds += 1;
   }
@@ -294,22 +307,26 @@ __device__ __forceinline__ void image_offset(int code, int &ox, int &oy, int &oz
 // time).  The 27 neighbour cells are staged through shared memory 32 atoms
 // at a time; every lane then sweeps the staged atoms (broadcast reads).
 // BUILD: append every j within rlist to i's Verlet list, tagged with the
-// periodic image it was found in.  !BUILD: evaluate the forces directly.
+// periodic image it was found in; the warp's lists are assembled in shared
+// memory (lane-major rows, conflict-free) and written to the [k][n] global
+// list one coalesced row at a time.  !BUILD: evaluate the forces directly.
 template <typename TF, bool BUILD>
 __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
   using V4 = typename Vec4<TF>::type;
   if (BUILD && !*d.rebuild) return;
   __shared__ V4 spos[kCellWarps][32];
   __shared__ int sidx[kCellWarps][32];
+  extern __shared__ uint32_t slist[];  // BUILD: [warps][maxnb][32]
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int warps = blockDim.x >> 5;
   const int64_t n = d.n;
   const int nc = d.nc;
   const V4 *rel = static_cast<const V4 *>(d.rel);
-  const int64_t c = blockIdx.x * (int64_t)kCellWarps + wl;
-  if (c >= d.ncell) return;
+  uint32_t *L = slist + (size_t)wl * d.maxnb * 32;
+  const TF edge = (TF)d.edge;
+  for (int64_t c = blockIdx.x * (int64_t)warps + wl; c < d.ncell; c += (int64_t)gridDim.x * warps) {
   const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
   const int i0 = d.cellstart[c], i1 = d.cellstart[c + 1];
-  const TF edge = (TF)d.edge;
   for (int ib = i0; ib < i1; ib += 32) {
     const int i = ib + lane;
     const bool act = i < i1;
@@ -342,7 +359,7 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
             const TF r2 = dx * dx + dy * dy + dz * dz;
             if (BUILD) {
               if (r2 < lj.rlist2 && j != i) {
-                if (cnt < d.maxnb) d.nbr[(int64_t)cnt * n + i] = (uint32_t)j | ((uint32_t)code << 27);
+                if (cnt < d.maxnb) L[cnt * 32 + lane] = (uint32_t)j | ((uint32_t)code << 27);
                 ++cnt;
               }
             } else {
@@ -352,20 +369,46 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
         }
       }
     }
-    if (act) {
-      if (BUILD) {
-        d.nnb[i] = min(cnt, d.maxnb);
+    if (BUILD) {
+      const int mine = act ? min(cnt, d.maxnb) : 0;
+      const int rows = __reduce_max_sync(0xffffffffu, mine);
+      __syncwarp();
+      for (int k = 0; k < rows; ++k)
+        if (k < mine) d.nbr[(int64_t)k * n + i] = L[k * 32 + lane];
+      if (act) {
+        d.nnb[i] = mine;
         if (cnt > d.maxnb) atomicOr(d.err, ERR_NBR_OVERFLOW);
-      } else {
-        store_pair_out<TF>(d, i, f, e, w);
       }
+      __syncwarp();
+    } else if (act) {
+      store_pair_out<TF>(d, i, f, e, w);
     }
   }
+  }  // cells of this warp
 }
 
 // Verlet-list pair kernel: one thread per atom (cell-sorted, so a warp's
 // neighbours overlap and their coordinates come from L1), full neighbour
-// shell, no atomics; FP32 FMA work on the CUDA cores in the mixed form.
+// shell, no atomics; FP32 FMA work on the CUDA cores in the mixed form.  The
+// list is streamed with evict-first loads; the loop is unrolled by kUnroll
+// so that kUnroll index loads and then kUnroll coordinate gathers are in
+// flight before the arithmetic that needs them.
+constexpr int kUnroll = 4;
+
+template <typename TF>
+__device__ __forceinline__ void pair_from_entry(const LJ<TF> &lj, const TF (*off)[3], uint32_t ent,
+                                                const typename Vec4<TF>::type &pi,
+                                                const typename Vec4<TF>::type &pj, TF f[3], TF &e, TF w[6]) {
+  const int code = (int)(ent >> 27);
+  // j moved into i's cell frame first: for a close pair across a cell face
+  // pj + off lands next to pi, so the final subtraction is exact.
+  const TF dx = pi.x - (pj.x + off[code][0]);
+  const TF dy = pi.y - (pj.y + off[code][1]);
+  const TF dz = pi.z - (pj.z + off[code][2]);
+  const TF r2 = dx * dx + dy * dy + dz * dz;
+  if (r2 < lj.rc2) lj_accumulate<TF>(lj, dx, dy, dz, r2, f, e, w);
+}
+
 template <typename TF>
 __global__ void __launch_bounds__(kPairThreads) k_pair_list(Sys d, LJ<TF> lj) {
   using V4 = typename Vec4<TF>::type;
@@ -386,18 +429,21 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_list(Sys d, LJ<TF> lj) {
   TF f[3] = {0, 0, 0}, e = 0, w[6] = {0, 0, 0, 0, 0, 0};
   const int nn = d.nnb[i];
   const uint32_t *nb = d.nbr + i;
-  for (int k = 0; k < nn; ++k) {
-    const uint32_t ent = __ldg(nb + (int64_t)k * n);
-    const int j = (int)(ent & 0x07ffffffu);
-    const int code = (int)(ent >> 27);
-    const V4 pj = Vec4<TF>::load(rel + j);
-    // j moved into i's cell frame first: for a close pair across a cell face
-    // pj + off lands next to pi, so the final subtraction is exact.
-    const TF dx = pi.x - (pj.x + off[code][0]);
-    const TF dy = pi.y - (pj.y + off[code][1]);
-    const TF dz = pi.z - (pj.z + off[code][2]);
-    const TF r2 = dx * dx + dy * dy + dz * dz;
-    if (r2 < lj.rc2) lj_accumulate<TF>(lj, dx, dy, dz, r2, f, e, w);
+  int k = 0;
+  for (; k + kUnroll <= nn; k += kUnroll) {
+    uint32_t ent[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) ent[u] = __ldcs(nb + (int64_t)(k + u) * n);
+    V4 pj[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) pj[u] = Vec4<TF>::load(rel + (ent[u] & 0x07ffffffu));
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) pair_from_entry<TF>(lj, off, ent[u], pi, pj[u], f, e, w);
+  }
+  for (; k < nn; ++k) {
+    const uint32_t ent = __ldcs(nb + (int64_t)k * n);
+    const V4 pj = Vec4<TF>::load(rel + (ent & 0x07ffffffu));
+    pair_from_entry<TF>(lj, off, ent, pi, pj, f, e, w);
   }
   store_pair_out<TF>(d, i, f, e, w);
 }
@@ -571,6 +617,7 @@ struct md_handle_s {
   cudaGraphExec_t graph = nullptr;
   bool fp64 = true;
   int red_blocks = 1;
+  int build_warps = 2;  // warps per CTA of the list build (shared-memory lists)
   int64_t steps_done = 0;
   int64_t corr_base = 0;
   corr_handle banks[3];  // system-owned correlators (borrowed by md_corr)
@@ -638,7 +685,8 @@ int launch_rebuild(md_handle *h, cudaStream_t s) {
   k_rb_place<<<grid_for(d.n, kThreads), kThreads, 0, s>>>(d);
   k_rb_rank<TF><<<grid_for(d.ncell * 32, kCellWarps * 32), kCellWarps * 32, 0, s>>>(d);
   if (h->prm.pair_mode == MD_PAIR_VERLET)
-    k_cells<TF, true><<<ceil_div(d.ncell, kCellWarps), kCellWarps * 32, 0, s>>>(d, lj_of<TF>(h->prm));
+    k_cells<TF, true><<<std::min(ceil_div(d.ncell, h->build_warps), 152 * 16), h->build_warps * 32,
+                        (size_t)h->build_warps * d.maxnb * 32 * sizeof(uint32_t), s>>>(d, lj_of<TF>(h->prm));
   OTF_LAUNCH_CHECK();
   return MD_OK;
 }
@@ -650,7 +698,8 @@ int launch_pair(md_handle *h, cudaStream_t s) {
   if (h->prm.pair_mode == MD_PAIR_VERLET)
     k_pair_list<TF><<<ceil_div(d.n, kPairThreads), kPairThreads, 0, s>>>(d, lj_of<TF>(h->prm));
   else
-    k_cells<TF, false><<<ceil_div(d.ncell, kCellWarps), kCellWarps * 32, 0, s>>>(d, lj_of<TF>(h->prm));
+    k_cells<TF, false><<<std::min(ceil_div(d.ncell, kCellWarps), 152 * 16), kCellWarps * 32, 0, s>>>(
+        d, lj_of<TF>(h->prm));
   OTF_LAUNCH_CHECK();
   return MD_OK;
 }
@@ -672,7 +721,7 @@ int launch_step(md_handle *h, cudaStream_t s) {
   const Sys &d = h->d;
   {
     KTimer tm(h, s, MD_K_INTEGRATE);
-    k_kick_drift<TF><<<grid_for(d.n, kThreads), kThreads, 0, s>>>(d, 0.5 * h->prm.dt);
+    k_kick_drift<TF><<<ceil_div(d.n, kThreads), kThreads, 0, s>>>(d, 0.5 * h->prm.dt);
     OTF_LAUNCH_CHECK();
   }
   int rc = launch_rebuild<TF>(h, s);
@@ -846,10 +895,23 @@ int init_impl(md_handle *h, const md_params *p, const md_system *s) {
   int maxnb = p->max_neighbors;
   if (maxnb <= 0) {
     const double mean = rho * 4.18879020478639 * rl * rl * rl;
-    maxnb = ((int)(1.35 * mean + 24.0) + 31) / 32 * 32;
+    maxnb = ((int)(1.35 * mean + 24.0) + 7) / 8 * 8;
   }
   d.maxnb = maxnb;
   d.vacf_u = p->vacf.u;
+  {
+    // warps per CTA of the list build: each holds maxnb x 32 list words in
+    // shared memory; keep a CTA within 96 KB so several fit on an SM
+    const size_t per_warp = (size_t)maxnb * 32 * sizeof(uint32_t);
+    h->build_warps = (int)std::max<size_t>(1, std::min<size_t>(kCellWarps, (96 * 1024) / per_warp));
+    const int bytes = (int)(h->build_warps * per_warp);
+    if (per_warp > 200 * 1024) {
+      set_error("md_init: max_neighbors %d needs more shared memory than a CTA has", maxnb);
+      return MD_EINVAL;
+    }
+    OTF_CUDA(cudaFuncSetAttribute(k_cells<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    OTF_CUDA(cudaFuncSetAttribute(k_cells<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  }
   const size_t tf = h->fp64 ? sizeof(double) : sizeof(float);
   const size_t v4 = h->fp64 ? sizeof(dvec4) : sizeof(float4);
   h->red_blocks = grid_for(n, kThreads, kMaxRedBlocks);
