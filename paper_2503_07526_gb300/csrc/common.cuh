@@ -91,6 +91,54 @@ __device__ __forceinline__ float pair_rcp(float x) {
 }
 __device__ __forceinline__ double pair_rcp(double x) { return 1.0 / x; }
 
+// Double-float numbers: an unevaluated sum h + l of two FP32 words with
+// |l| <= ulp(h)/2 (about 48 significant bits).  GB300 runs FP64 at a small
+// fraction of its FP32 rate, so the mixed form carries positions and
+// velocities this way.  Built from the classical error-free transformations
+// (Knuth's TwoSum, Dekker's FastTwoSum, the FMA form of Dekker's TwoProduct);
+// the code is compiled without fast-math, so the compiler neither
+// re-associates these sums nor flushes the small low words.
+struct dfloat {
+  float h, l;
+};
+
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {  // needs |a| >= |b|
+  const float s = a + b;
+  return dfloat{s, b - (s - a)};
+}
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return dfloat{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+  dfloat s = df_two_sum(a.h, b.h);
+  const dfloat t = df_two_sum(a.l, b.l);
+  s.l += t.h;
+  s = df_fast_two_sum(s.h, s.l);
+  s.l += t.l;
+  return df_fast_two_sum(s.h, s.l);
+}
+__device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfloat df_mul_f(dfloat a, float b) {
+  const float p = a.h * b;
+  float e = fmaf(a.h, b, -p);
+  e = fmaf(a.l, b, e);
+  return df_fast_two_sum(p, e);
+}
+// Host / FP64 conversions (used at set-up and output only).
+__host__ __device__ __forceinline__ dfloat df_from_double(double x) {
+  const float h = (float)x;
+  return dfloat{h, (float)(x - (double)h)};
+}
+__host__ __device__ __forceinline__ double df_to_double(dfloat a) { return (double)a.h + (double)a.l; }
+
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 }  // namespace otf

@@ -4,17 +4,31 @@
 //
 // GB300 design.  Atoms live in a cell-sorted structure of arrays that is
 // rebuilt by a counting sort when any atom has moved half the skin.  Each
-// atom also carries its coordinates relative to the origin of the cell it
-// was sorted into, measured from the cell centre (|rel| <= edge/2, which
-// halves their FP32 rounding), in the arithmetic type of the pair path, so
-// the FP32 form never subtracts two large absolute coordinates.  A step is a fixed
-// sequence of kernels (no host decision inside it), so it is captured once
-// as a CUDA graph and replayed; the rebuild kernels read a device flag and
-// return at once when no rebuild is due.
+// atom carries its coordinates relative to the centre of the cell it was
+// sorted into (|rel| <= edge/2) in the arithmetic type of the pair path, so
+// the FP32 form never subtracts two large absolute coordinates.
+//
+// State.  The FP64 form keeps absolute FP64 positions and velocities.  The
+// mixed form keeps each position as a cell index plus a double-float offset
+// from that cell's centre (the high words are the FP32 coordinates the pair
+// kernel reads) and each velocity as a double-float: about 48 significant
+// bits, integrated with FP32 error-free transformations, because GB300's
+// FP64 pipe runs at a small fraction of its FP32 rate.  Moving an atom to
+// another cell shifts its offset by whole cell edges; crossing the periodic
+// boundary only changes the cell index.
+//
+// Neighbour lists are stored per chunk of up to 32 consecutive atoms of a
+// cell: a block of max_neighbors rows of 32 words, so the list build writes
+// rows that stay together in L2 and the pair kernel reads them coalesced.
+//
+// A step is a fixed sequence of kernels (no host decision inside it), so it
+// is captured once as a CUDA graph and replayed; the rebuild kernels read a
+// device flag and return at once when no rebuild is due.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "corr.cuh"
@@ -26,7 +40,7 @@ constexpr int kThreads = 256;
 constexpr int kPairThreads = 128;
 constexpr int kCellWarps = 4;  // warps (cells) per CTA in the link-cell kernels
 constexpr int kNRed = 11;      // K, U, V*sigma[6], V*q[3]
-constexpr int kMaxRedBlocks = 152 * 16;
+constexpr int kMaxRedBlocks = 152 * 4;
 
 struct ObsDev {
   int64_t step;       // steps completed
@@ -40,21 +54,25 @@ struct ObsDev {
 };
 
 struct Sys {
-  int64_t n, ncell;
+  int64_t n, ncell, maxchunks;
   int nc, ntypes, maxnb, always_rebuild, vacf_u;
   double L, edge, dt, lim2;
   double invm[8], mass[8];
+  float hdtm_h[8], hdtm_l[8];  // mixed form: dt / (2 m) per type, double-float
+  float dt_h, dt_l, edge_h, edge_l;
   // cell-sorted state
-  double *r, *v;        // [3][n]
-  void *F, *epot, *W;   // [3][n], [n], [6][n] in the pair type
-  void *rel, *relb;     // Vec4 of the pair type: current / at last rebuild
-  void *vbuf;           // [3][n] velocities in atom-id order (correlator input)
-  int *id, *type, *cpk; // atom id, type, packed cell coordinates
-  // rebuild scratch
+  double *r, *v;             // FP64 form: absolute positions, velocities [3][n]
+  float *offl, *vh, *vl;     // mixed form: offset low words, velocity words [3][n]
+  void *F, *epot, *W;        // [3][n], [n], [6][n] in the pair type
+  void *rel, *relb;          // Vec4 of the pair type: current / at last rebuild
+  void *vbuf;                // [3][n] velocities in atom-id order (correlator input)
+  int *id, *type, *cpk;      // atom id, type, packed cell coordinates
+  // rebuild scratch (24 bytes per atom each)
   double *rB, *vB;
-  int *idB, *typeB, *cellB, *slot, *perm, *cellcount, *cellstart;
-  uint32_t *nbr;        // [maxnb][n] neighbour j | (image code << 27)
-  int *nnb;
+  int *idB, *typeB, *cellB, *slot, *perm, *cellcount, *cellstart, *chunkstart;
+  uint32_t *nbr;             // [maxchunks][maxnb][32]: j | (image code << 27)
+  int *nnb;                  // list length per atom
+  uint32_t *nref;            // chunk << 5 | lane per atom
   // reductions and flags
   double *partials;
   unsigned *counter;
@@ -74,40 +92,79 @@ __device__ __forceinline__ void unpack_cell(int c, int &x, int &y, int &z) {
   y = (c >> 10) & 1023;
   z = c >> 20;
 }
+__device__ __forceinline__ int type_of(const Sys &d, int64_t i) { return min(max(d.type[i], 0), 7); }
 
 // ------------------------------------------------------------ integrate
 
-// First half kick and drift (velocity Verlet), new cell-relative
-// coordinates, and the skin test that decides the next rebuild.
-template <typename TF>
-__global__ void __launch_bounds__(kThreads) k_kick_drift(Sys d, double hdt) {
-  using V4 = typename Vec4<TF>::type;
-  const TF *F = static_cast<const TF *>(d.F);
-  V4 *rel = static_cast<V4 *>(d.rel);
-  const V4 *relb = static_cast<const V4 *>(d.relb);
+// FP64 form: first half kick and drift (velocity Verlet), new
+// cell-relative coordinates, and the skin test that decides the next
+// rebuild.
+__global__ void __launch_bounds__(kThreads) k_kick_drift64(Sys d, double hdt) {
+  const double *F = static_cast<const double *>(d.F);
+  dvec4 *rel = static_cast<dvec4 *>(d.rel);
+  const dvec4 *relb = static_cast<const dvec4 *>(d.relb);
   bool over = false, bad = false;
   const int64_t n = d.n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double h = hdt * d.invm[min(max(d.type[i], 0), 7)];
+    const double h = hdt * d.invm[type_of(d, i)];
     double x[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double va = fma(h, (double)F[a * n + i], d.v[a * n + i]);
+      const double va = fma(h, F[a * n + i], d.v[a * n + i]);
       d.v[a * n + i] = va;
       x[a] = fma(d.dt, va, d.r[a * n + i]);
       d.r[a * n + i] = x[a];
     }
     int cx, cy, cz;
     unpack_cell(d.cpk[i], cx, cy, cz);
-    const TF px = (TF)fma(-(cx + 0.5), d.edge, x[0]);
-    const TF py = (TF)fma(-(cy + 0.5), d.edge, x[1]);
-    const TF pz = (TF)fma(-(cz + 0.5), d.edge, x[2]);
-    Vec4<TF>::store(rel + i, px, py, pz);
-    const V4 b = Vec4<TF>::load(relb + i);
-    const TF dx = px - b.x, dy = py - b.y, dz = pz - b.z;
-    over |= (double)(dx * dx + dy * dy + dz * dz) > d.lim2;
+    const double px = fma(-(cx + 0.5), d.edge, x[0]);
+    const double py = fma(-(cy + 0.5), d.edge, x[1]);
+    const double pz = fma(-(cz + 0.5), d.edge, x[2]);
+    Vec4<double>::store(rel + i, px, py, pz);
+    const dvec4 b = Vec4<double>::load(relb + i);
+    const double dx = px - b.x, dy = py - b.y, dz = pz - b.z;
+    over |= (dx * dx + dy * dy + dz * dz) > d.lim2;
     bad |= !(isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]));
+  }
+  if (__any_sync(0xffffffffu, over || d.always_rebuild) && (threadIdx.x & 31) == 0) *d.rebuild = 1;
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(d.err, ERR_NONFINITE);
+}
+
+// Mixed form: the same half kick and drift in double-float arithmetic on
+// the velocity and on the offset from the cell centre (no FP64 instruction
+// per atom).  The offset's high words are the FP32 coordinates of the pair
+// kernel.
+__global__ void __launch_bounds__(kThreads) k_kick_drift_df(Sys d) {
+  const float *F = static_cast<const float *>(d.F);
+  float4 *rel = static_cast<float4 *>(d.rel);
+  const float4 *relb = static_cast<const float4 *>(d.relb);
+  const dfloat dt{d.dt_h, d.dt_l};
+  const float lim2 = (float)d.lim2;
+  bool over = false, bad = false;
+  const int64_t n = d.n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int t = type_of(d, i);
+    const dfloat h{d.hdtm_h[t], d.hdtm_l[t]};
+    const float4 o = rel[i];
+    float oh[3] = {o.x, o.y, o.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      dfloat v{d.vh[a * n + i], d.vl[a * n + i]};
+      v = df_add(v, df_mul_f(h, F[a * n + i]));
+      d.vh[a * n + i] = v.h;
+      d.vl[a * n + i] = v.l;
+      dfloat x{oh[a], d.offl[a * n + i]};
+      x = df_add(x, df_mul(dt, v));
+      oh[a] = x.h;
+      d.offl[a * n + i] = x.l;
+    }
+    rel[i] = make_float4(oh[0], oh[1], oh[2], 0.f);
+    const float4 b = relb[i];
+    const float dx = oh[0] - b.x, dy = oh[1] - b.y, dz = oh[2] - b.z;
+    over |= (dx * dx + dy * dy + dz * dz) > lim2;
+    bad |= !(isfinite(oh[0]) && isfinite(oh[1]) && isfinite(oh[2]));
   }
   if (__any_sync(0xffffffffu, over || d.always_rebuild) && (threadIdx.x & 31) == 0) *d.rebuild = 1;
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(d.err, ERR_NONFINITE);
@@ -122,9 +179,22 @@ __global__ void k_rb_zero(Sys d) {
     d.cellcount[c] = 0;
 }
 
-// Wraps positions into the box, bins every atom into its cell and takes a
-// provisional slot in it; copies the state aside for the gather.
-__global__ void __launch_bounds__(kThreads) k_rb_assign(Sys d) {
+// Takes a provisional slot in cell c for atom i: lanes binning into the
+// same cell share one atomic (consecutive atoms are mostly in one cell).
+__device__ __forceinline__ void bin_atom(const Sys &d, int64_t i, int c) {
+  d.cellB[i] = c;
+  const unsigned grp = __match_any_sync(__activemask(), c);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(grp) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(&d.cellcount[c], __popc(grp));
+  base = __shfl_sync(grp, base, leader);
+  d.slot[i] = base + __popc(grp & ((1u << lane) - 1u));
+}
+
+// FP64 form: wraps positions into the box, bins every atom into its cell
+// and copies the state aside for the gather.
+__global__ void __launch_bounds__(kThreads) k_rb_assign64(Sys d) {
   if (!*d.rebuild) return;
   const int64_t n = d.n;
   const int nc = d.nc;
@@ -137,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_assign(Sys d) {
       x -= d.L * floor(x / d.L);
       if (x >= d.L) x -= d.L;
       if (x < 0.0) x = 0.0;
-      int c = (int)(x / d.edge);
+      const int c = (int)(x / d.edge);
       ci[a] = c < nc ? c : nc - 1;
       d.rB[a * n + i] = x;
       d.vB[a * n + i] = d.v[a * n + i];
@@ -146,64 +216,113 @@ __global__ void __launch_bounds__(kThreads) k_rb_assign(Sys d) {
     if (t < 0 || t >= d.ntypes) atomicOr(d.err, ERR_BAD_TYPE);
     d.idB[i] = d.id[i];
     d.typeB[i] = t;
-    const int c = (ci[2] * nc + ci[1]) * nc + ci[0];
-    d.cellB[i] = c;
-    // lanes binning into the same cell share one atomic (consecutive atoms
-    // are mostly in the same cell): the leader reserves their slots
-    const unsigned grp = __match_any_sync(__activemask(), c);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(grp) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(&d.cellcount[c], __popc(grp));
-    base = __shfl_sync(grp, base, leader);
-    d.slot[i] = base + __popc(grp & ((1u << lane) - 1u));
+    bin_atom(d, i, (ci[2] * nc + ci[1]) * nc + ci[0]);
   }
 }
 
-// Exclusive scan of the cell counts (one CTA of 1024 threads).  Warp w owns
-// a contiguous segment and reads it in coalesced rows of 32: pass 1 sums the
-// segments, warp 0 scans the 32 sums, pass 2 scans each row with shuffles
-// and a running carry.
+// Mixed form: the new cell is the old one moved by the nearest whole number
+// of cell edges along each axis (periodic), and the offset loses the same
+// multiple of the edge, in double-float.  Scratch layout: rB = offset high
+// then low words, vB = velocity high then low words (float [3][n] each).
+__global__ void __launch_bounds__(kThreads) k_rb_assign_df(Sys d) {
+  if (!*d.rebuild) return;
+  const int64_t n = d.n;
+  const int nc = d.nc;
+  const float4 *rel = static_cast<const float4 *>(d.rel);
+  const dfloat edge{d.edge_h, d.edge_l};
+  float *oB = reinterpret_cast<float *>(d.rB);
+  float *wB = reinterpret_cast<float *>(d.vB);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 o = rel[i];
+    const float oh[3] = {o.x, o.y, o.z};
+    int cc[3];
+    unpack_cell(d.cpk[i], cc[0], cc[1], cc[2]);
+    int ci[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      dfloat x{oh[a], d.offl[a * n + i]};
+      int k = (int)rintf(x.h / d.edge_h);  // NaN converts to 0
+      k = max(-nc, min(nc, k));
+      if (k != 0) x = df_add(x, df_mul_f(edge, (float)(-k)));
+      int c = (cc[a] + k) % nc;
+      if (c < 0) c += nc;
+      ci[a] = c;
+      oB[a * n + i] = x.h;
+      oB[3 * n + a * n + i] = x.l;
+      wB[a * n + i] = d.vh[a * n + i];
+      wB[3 * n + a * n + i] = d.vl[a * n + i];
+    }
+    const int t = d.type[i];
+    if (t < 0 || t >= d.ntypes) atomicOr(d.err, ERR_BAD_TYPE);
+    d.idB[i] = d.id[i];
+    d.typeB[i] = t;
+    bin_atom(d, i, (ci[2] * nc + ci[1]) * nc + ci[0]);
+  }
+}
+
+// Exclusive scans of the cell counts and of the cells' 32-atom chunk counts
+// (one CTA of 1024 threads).  Warp w owns a contiguous segment and reads it
+// in coalesced rows of 32: pass 1 sums the segments, warp 0 scans the 32
+// sums, pass 2 scans each row with shuffles and a running carry.
 __global__ void __launch_bounds__(1024) k_rb_scan(Sys d) {
   if (!*d.rebuild) return;
-  __shared__ int wsum[32];
+  __shared__ int wsum[2][32];
   const int64_t nc3 = d.ncell;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t seg = (nc3 + 31) / 32;
   const int64_t c0 = warp * seg, c1 = min(nc3, c0 + seg);
-  int part = 0;
-  for (int64_t c = c0 + lane; c < c1; c += 32) part += d.cellcount[c];
-  part = warp_sum(part);
-  if (lane == 0) wsum[warp] = part;
-  __syncthreads();
-  if (warp == 0) {
-    const int v = wsum[lane];
-    int incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    wsum[lane] = incl - v;  // exclusive offset of each segment
+  int pa = 0, pb = 0;
+  for (int64_t c = c0 + lane; c < c1; c += 32) {
+    const int v = d.cellcount[c];
+    pa += v;
+    pb += (v + 31) >> 5;
+  }
+  pa = warp_sum(pa);
+  pb = warp_sum(pb);
+  if (lane == 0) {
+    wsum[0][warp] = pa;
+    wsum[1][warp] = pb;
   }
   __syncthreads();
-  int carry = wsum[warp];
-  for (int64_t b = c0; b < c1; b += 32) {
-    const int64_t c = b + lane;
-    const int v = c < c1 ? d.cellcount[c] : 0;
+  if (warp < 2) {
+    const int v = wsum[warp][lane];
     int incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += y;
     }
-    if (c < c1) d.cellstart[c] = carry + incl - v;
-    carry += __shfl_sync(0xffffffffu, incl, 31);
+    wsum[warp][lane] = incl - v;  // exclusive offset of each segment
+  }
+  __syncthreads();
+  int ca = wsum[0][warp], cb = wsum[1][warp];
+  for (int64_t b = c0; b < c1; b += 32) {
+    const int64_t c = b + lane;
+    const int va = c < c1 ? d.cellcount[c] : 0;
+    const int vb = (va + 31) >> 5;
+    int ia = va, ib = vb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int ya = __shfl_up_sync(0xffffffffu, ia, o);
+      const int yb = __shfl_up_sync(0xffffffffu, ib, o);
+      if (lane >= o) {
+        ia += ya;
+        ib += yb;
+      }
+    }
+    if (c < c1) {
+      d.cellstart[c] = ca + ia - va;
+      d.chunkstart[c] = cb + ib - vb;
+    }
+    ca += __shfl_sync(0xffffffffu, ia, 31);
+    cb += __shfl_sync(0xffffffffu, ib, 31);
   }
   if (threadIdx.x == 0) {
     d.cellstart[nc3] = (int)d.n;
     d.obs->rebuilds += 1;
   }
+  if (warp == 31 && lane == 0) d.chunkstart[nc3] = cb;  // total chunks
 }
 
 __global__ void __launch_bounds__(kThreads) k_rb_place(Sys d) {
@@ -219,7 +338,6 @@ __global__ void __launch_bounds__(kThreads) k_rb_place(Sys d) {
 template <typename TF>
 __global__ void __launch_bounds__(kCellWarps * 32) k_rb_rank(Sys d) {
   if (!*d.rebuild) return;
-  using V4 = typename Vec4<TF>::type;
   const int lane = threadIdx.x & 31;
   const int64_t n = d.n;
   const int64_t wglobal = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -238,21 +356,37 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_rb_rank(Sys d) {
       }
       if (e < cnt) {
         const int dst = s0 + rank;
-        double x[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          x[q] = d.rB[q * n + a];
-          d.r[q * n + dst] = x[q];
-          d.v[q * n + dst] = d.vB[q * n + a];
-        }
         d.id[dst] = key;
         d.type[dst] = d.typeB[a];
         d.cpk[dst] = pack_cell(cx, cy, cz);
-        const TF px = (TF)fma(-(cx + 0.5), d.edge, x[0]);
-        const TF py = (TF)fma(-(cy + 0.5), d.edge, x[1]);
-        const TF pz = (TF)fma(-(cz + 0.5), d.edge, x[2]);
-        Vec4<TF>::store(static_cast<V4 *>(d.rel) + dst, px, py, pz);
-        Vec4<TF>::store(static_cast<V4 *>(d.relb) + dst, px, py, pz);
+        if constexpr (std::is_same<TF, double>::value) {
+          double x[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            x[q] = d.rB[q * n + a];
+            d.r[q * n + dst] = x[q];
+            d.v[q * n + dst] = d.vB[q * n + a];
+          }
+          const double px = fma(-(cx + 0.5), d.edge, x[0]);
+          const double py = fma(-(cy + 0.5), d.edge, x[1]);
+          const double pz = fma(-(cz + 0.5), d.edge, x[2]);
+          Vec4<double>::store(static_cast<dvec4 *>(d.rel) + dst, px, py, pz);
+          Vec4<double>::store(static_cast<dvec4 *>(d.relb) + dst, px, py, pz);
+        } else {
+          const float *oB = reinterpret_cast<const float *>(d.rB);
+          const float *wB = reinterpret_cast<const float *>(d.vB);
+          float oh[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            oh[q] = oB[q * n + a];
+            d.offl[q * n + dst] = oB[3 * n + q * n + a];
+            d.vh[q * n + dst] = wB[q * n + a];
+            d.vl[q * n + dst] = wB[3 * n + q * n + a];
+          }
+          const float4 o = make_float4(oh[0], oh[1], oh[2], 0.f);
+          static_cast<float4 *>(d.rel)[dst] = o;
+          static_cast<float4 *>(d.relb)[dst] = o;
+        }
       }
     }
   }
@@ -304,87 +438,87 @@ __device__ __forceinline__ void image_offset(int code, int &ox, int &oy, int &oz
 }
 
 // Link-cell kernel, one warp per cell (lanes = the cell's atoms, 32 at a
-// time).  The 27 neighbour cells are staged through shared memory 32 atoms
-// at a time; every lane then sweeps the staged atoms (broadcast reads).
+// time; warps stride over the cells).  The 27 neighbour cells are staged
+// through shared memory 32 atoms at a time, already moved into the i cell's
+// frame; every lane then sweeps the staged atoms (broadcast reads).
 // BUILD: append every j within rlist to i's Verlet list, tagged with the
-// periodic image it was found in; the warp's lists are assembled in shared
-// memory (lane-major rows, conflict-free) and written to the [k][n] global
-// list one coalesced row at a time.  !BUILD: evaluate the forces directly.
+// periodic image it was found in; the 32 atoms of a chunk own one block of
+// maxnb rows x 32 lanes.  !BUILD: evaluate the forces directly.
 template <typename TF, bool BUILD>
 __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
   using V4 = typename Vec4<TF>::type;
   if (BUILD && !*d.rebuild) return;
   __shared__ V4 spos[kCellWarps][32];
   __shared__ int sidx[kCellWarps][32];
-  extern __shared__ uint32_t slist[];  // BUILD: [warps][maxnb][32]
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  const int warps = blockDim.x >> 5;
-  const int64_t n = d.n;
   const int nc = d.nc;
   const V4 *rel = static_cast<const V4 *>(d.rel);
-  uint32_t *L = slist + (size_t)wl * d.maxnb * 32;
   const TF edge = (TF)d.edge;
-  for (int64_t c = blockIdx.x * (int64_t)warps + wl; c < d.ncell; c += (int64_t)gridDim.x * warps) {
-  const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
-  const int i0 = d.cellstart[c], i1 = d.cellstart[c + 1];
-  for (int ib = i0; ib < i1; ib += 32) {
-    const int i = ib + lane;
-    const bool act = i < i1;
-    V4 pi;
-    if (act) pi = Vec4<TF>::load(rel + i);
-    TF f[3] = {0, 0, 0}, e = 0, w[6] = {0, 0, 0, 0, 0, 0};
-    int cnt = 0;
-    for (int code = 0; code < 27; ++code) {
-      int ox, oy, oz;
-      image_offset(code, ox, oy, oz);
-      const int jx = (cx + ox + nc) % nc, jy = (cy + oy + nc) % nc, jz = (cz + oz + nc) % nc;
-      const int64_t cj = ((int64_t)jz * nc + jy) * nc + jx;
-      const int j0 = d.cellstart[cj], j1 = d.cellstart[cj + 1];
-      const TF offx = ox * edge, offy = oy * edge, offz = oz * edge;
-      for (int jb = j0; jb < j1; jb += 32) {
-        __syncwarp();
-        if (jb + lane < j1) {
-          spos[wl][lane] = Vec4<TF>::load(rel + jb + lane);
-          sidx[wl][lane] = jb + lane;
-        }
-        __syncwarp();
-        const int nj = min(32, j1 - jb);
-        if (act) {
-          for (int t = 0; t < nj; ++t) {
-            const V4 pj = spos[wl][t];
-            const int j = sidx[wl][t];
-            const TF dx = pi.x - (pj.x + offx);
-            const TF dy = pi.y - (pj.y + offy);
-            const TF dz = pi.z - (pj.z + offz);
-            const TF r2 = dx * dx + dy * dy + dz * dz;
-            if (BUILD) {
-              if (r2 < lj.rlist2 && j != i) {
-                if (cnt < d.maxnb) L[cnt * 32 + lane] = (uint32_t)j | ((uint32_t)code << 27);
-                ++cnt;
+  for (int64_t c = blockIdx.x * (int64_t)kCellWarps + wl; c < d.ncell; c += (int64_t)gridDim.x * kCellWarps) {
+    const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
+    const int i0 = d.cellstart[c], i1 = d.cellstart[c + 1];
+    for (int ib = i0; ib < i1; ib += 32) {
+      const int i = ib + lane;
+      const bool act = i < i1;
+      V4 pi;
+      if (act) pi = Vec4<TF>::load(rel + i);
+      TF f[3] = {0, 0, 0}, e = 0, w[6] = {0, 0, 0, 0, 0, 0};
+      int cnt = 0;
+      const uint32_t chunk = BUILD ? (uint32_t)(d.chunkstart[c] + ((ib - i0) >> 5)) : 0u;
+      uint32_t *L = BUILD ? d.nbr + (int64_t)chunk * d.maxnb * 32 + lane : nullptr;
+      for (int code = 0; code < 27; ++code) {
+        int ox, oy, oz;
+        image_offset(code, ox, oy, oz);
+        const int jx = (cx + ox + nc) % nc, jy = (cy + oy + nc) % nc, jz = (cz + oz + nc) % nc;
+        const int64_t cj = ((int64_t)jz * nc + jy) * nc + jx;
+        const int j0 = d.cellstart[cj], j1 = d.cellstart[cj + 1];
+        const TF offx = ox * edge, offy = oy * edge, offz = oz * edge;
+        for (int jb = j0; jb < j1; jb += 32) {
+          __syncwarp();
+          if (jb + lane < j1) {
+            const V4 pj = Vec4<TF>::load(rel + jb + lane);
+            V4 t;
+            t.x = pj.x + offx;
+            t.y = pj.y + offy;
+            t.z = pj.z + offz;
+            spos[wl][lane] = t;
+            sidx[wl][lane] = jb + lane;
+          }
+          __syncwarp();
+          const int nj = min(32, j1 - jb);
+          if (act) {
+            for (int t = 0; t < nj; ++t) {
+              const V4 pj = spos[wl][t];
+              const int j = sidx[wl][t];
+              // pj already holds j in i's cell frame: the subtraction is the
+              // one the list kernel performs
+              const TF dx = pi.x - pj.x;
+              const TF dy = pi.y - pj.y;
+              const TF dz = pi.z - pj.z;
+              const TF r2 = dx * dx + dy * dy + dz * dz;
+              if (BUILD) {
+                if (r2 < lj.rlist2 && j != i) {
+                  if (cnt < d.maxnb) L[cnt * 32] = (uint32_t)j | ((uint32_t)code << 27);
+                  ++cnt;
+                }
+              } else {
+                if (r2 < lj.rc2 && j != i) lj_accumulate<TF>(lj, dx, dy, dz, r2, f, e, w);
               }
-            } else {
-              if (r2 < lj.rc2 && j != i) lj_accumulate<TF>(lj, dx, dy, dz, r2, f, e, w);
             }
           }
         }
       }
-    }
-    if (BUILD) {
-      const int mine = act ? min(cnt, d.maxnb) : 0;
-      const int rows = __reduce_max_sync(0xffffffffu, mine);
-      __syncwarp();
-      for (int k = 0; k < rows; ++k)
-        if (k < mine) d.nbr[(int64_t)k * n + i] = L[k * 32 + lane];
       if (act) {
-        d.nnb[i] = mine;
-        if (cnt > d.maxnb) atomicOr(d.err, ERR_NBR_OVERFLOW);
+        if (BUILD) {
+          d.nnb[i] = min(cnt, d.maxnb);
+          d.nref[i] = (chunk << 5) | (uint32_t)lane;
+          if (cnt > d.maxnb) atomicOr(d.err, ERR_NBR_OVERFLOW);
+        } else {
+          store_pair_out<TF>(d, i, f, e, w);
+        }
       }
-      __syncwarp();
-    } else if (act) {
-      store_pair_out<TF>(d, i, f, e, w);
     }
   }
-  }  // cells of this warp
 }
 
 // Verlet-list pair kernel: one thread per atom (cell-sorted, so a warp's
@@ -423,17 +557,17 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_list(Sys d, LJ<TF> lj) {
   __syncthreads();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= d.n) return;
-  const int64_t n = d.n;
   const V4 *rel = static_cast<const V4 *>(d.rel);
   const V4 pi = Vec4<TF>::load(rel + i);
   TF f[3] = {0, 0, 0}, e = 0, w[6] = {0, 0, 0, 0, 0, 0};
   const int nn = d.nnb[i];
-  const uint32_t *nb = d.nbr + i;
+  const uint32_t ref = d.nref[i];
+  const uint32_t *nb = d.nbr + (int64_t)(ref >> 5) * d.maxnb * 32 + (ref & 31u);
   int k = 0;
   for (; k + kUnroll <= nn; k += kUnroll) {
     uint32_t ent[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) ent[u] = __ldcs(nb + (int64_t)(k + u) * n);
+    for (int u = 0; u < kUnroll; ++u) ent[u] = __ldcs(nb + (k + u) * 32);
     V4 pj[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) pj[u] = Vec4<TF>::load(rel + (ent[u] & 0x07ffffffu));
@@ -441,7 +575,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_list(Sys d, LJ<TF> lj) {
     for (int u = 0; u < kUnroll; ++u) pair_from_entry<TF>(lj, off, ent[u], pi, pj[u], f, e, w);
   }
   for (; k < nn; ++k) {
-    const uint32_t ent = __ldcs(nb + (int64_t)k * n);
+    const uint32_t ent = __ldcs(nb + k * 32);
     const V4 pj = Vec4<TF>::load(rel + (ent & 0x07ffffffu));
     pair_from_entry<TF>(lj, off, ent, pi, pj, f, e, w);
   }
@@ -452,11 +586,12 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_list(Sys d, LJ<TF> lj) {
 
 // Second half kick, then the per-step system observables (Sec. 2.3):
 // K, U, V sigma_ab = sum m v_a v_b + sum W_i,ab, V q = sum (E_i v_i + W_i v_i).
-// Per-thread partial sums in A (float in the mixed form, double in FP64),
-// the CTA and grid tree in FP64 (fixed order: deterministic).  The last CTA
-// to finish writes the observables, advances the step counter and takes
-// the stress and heat-flux correlator samples (Algorithm 1).  When a
-// velocity sample is due, velocities are also scattered to atom-id order.
+// Per-thread partial sums in A (float in the mixed form, from the FP32 high
+// words of the velocities; double in FP64), the CTA and grid tree in FP64
+// (fixed order: deterministic).  The last CTA to finish writes the
+// observables, advances the step counter and takes the stress and
+// heat-flux correlator samples (Algorithm 1).  When a velocity sample is
+// due, velocities are also scattered to atom-id order.
 template <typename TF, typename A, bool KICK>
 __global__ void __launch_bounds__(kThreads)
     k_kick_reduce(Sys d, double hdt, CorrDev cs, int64_t us, CorrDev ch, int64_t uh) {
@@ -476,14 +611,29 @@ __global__ void __launch_bounds__(kThreads)
   for (int q = 0; q < kNRed; ++q) acc[q] = A(0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int t = min(max(d.type[i], 0), 7);  // out-of-range types are flagged by the sort
-    double v[3];
+    const int t = type_of(d, i);
+    A v[3];
+    if constexpr (std::is_same<TF, double>::value) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      v[a] = d.v[a * n + i];
-      if (KICK) {
-        v[a] = fma(hdt * d.invm[t], (double)F[a * n + i], v[a]);
-        d.v[a * n + i] = v[a];
+      for (int a = 0; a < 3; ++a) {
+        double va = d.v[a * n + i];
+        if (KICK) {
+          va = fma(hdt * d.invm[t], F[a * n + i], va);
+          d.v[a * n + i] = va;
+        }
+        v[a] = (A)va;
+      }
+    } else {
+      const dfloat h{d.hdtm_h[t], d.hdtm_l[t]};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        dfloat va{d.vh[a * n + i], d.vl[a * n + i]};
+        if (KICK) {
+          va = df_add(va, df_mul_f(h, (float)F[a * n + i]));
+          d.vh[a * n + i] = va.h;
+          d.vl[a * n + i] = va.l;
+        }
+        v[a] = (A)va.h;
       }
     }
     if (vacf_due) {
@@ -492,7 +642,7 @@ __global__ void __launch_bounds__(kThreads)
       for (int a = 0; a < 3; ++a) vb[a * n + id] = (TF)v[a];
     }
     const A m = (A)d.mass[t];
-    const A vx = (A)v[0], vy = (A)v[1], vz = (A)v[2];
+    const A vx = v[0], vy = v[1], vz = v[2];
     const A ep = (A)Ep[i];
     A w[6];
 #pragma unroll
@@ -514,8 +664,8 @@ __global__ void __launch_bounds__(kThreads)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < kNRed; ++q) {
-    const double s = warp_sum((double)acc[q]);
-    if (lane == 0) red[warp][q] = s;
+    const A s = warp_sum(acc[q]);
+    if (lane == 0) red[warp][q] = (double)s;
   }
   __syncthreads();
   if (threadIdx.x < kNRed) {
@@ -566,16 +716,56 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+template <typename TF>
 __global__ void k_scale_v(Sys d, double lam) {
+  const dfloat l = df_from_double(lam);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * d.n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    d.v[i] *= lam;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (std::is_same<TF, double>::value) {
+      d.v[i] *= lam;
+    } else {
+      const dfloat v = df_mul(dfloat{d.vh[i], d.vl[i]}, l);
+      d.vh[i] = v.h;
+      d.vl[i] = v.l;
+    }
+  }
 }
 
 __global__ void k_iota(int *id, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     id[i] = (int)i;
+}
+
+// Mixed form set-up: FP64 input positions and velocities (in the rB, vB
+// scratch, input order) become cell index + double-float offset from the
+// cell centre and double-float velocities.  FP64 arithmetic, once.
+__global__ void k_init_df(Sys d) {
+  const int64_t n = d.n;
+  const int nc = d.nc;
+  float4 *rel = static_cast<float4 *>(d.rel);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int ci[3];
+    float oh[3];
+    for (int a = 0; a < 3; ++a) {
+      double x = d.rB[a * n + i];
+      x -= d.L * floor(x / d.L);
+      if (x >= d.L) x -= d.L;
+      if (x < 0.0) x = 0.0;
+      int c = (int)(x / d.edge);
+      c = c < nc ? c : nc - 1;
+      ci[a] = c;
+      const dfloat off = df_from_double(x - (c + 0.5) * d.edge);
+      oh[a] = off.h;
+      d.offl[a * n + i] = off.l;
+      const dfloat v = df_from_double(d.vB[a * n + i]);
+      d.vh[a * n + i] = v.h;
+      d.vl[a * n + i] = v.l;
+    }
+    rel[i] = make_float4(oh[0], oh[1], oh[2], 0.f);
+    d.cpk[i] = pack_cell(ci[0], ci[1], ci[2]);
+  }
 }
 
 // Per-particle outputs back in atom-id order (FP64), positions wrapped.
@@ -588,14 +778,28 @@ __global__ void k_unsort(Sys d, double *r, double *v, double *F, double *epot, d
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t id = d.id[i];
+    int cc[3];
+    unpack_cell(d.cpk[i], cc[0], cc[1], cc[2]);
     for (int a = 0; a < 3; ++a) {
       if (r) {
-        double x = d.r[a * n + i];
+        double x;
+        if constexpr (std::is_same<TF, double>::value) {
+          x = d.r[a * n + i];
+        } else {
+          const float4 o = static_cast<const float4 *>(d.rel)[i];
+          const float oh = a == 0 ? o.x : (a == 1 ? o.y : o.z);
+          x = (cc[a] + 0.5) * d.edge + df_to_double(dfloat{oh, d.offl[a * n + i]});
+        }
         x -= d.L * floor(x / d.L);
         if (x >= d.L) x -= d.L;
         r[a * n + id] = x;
       }
-      if (v) v[a * n + id] = d.v[a * n + i];
+      if (v) {
+        if constexpr (std::is_same<TF, double>::value)
+          v[a * n + id] = d.v[a * n + i];
+        else
+          v[a * n + id] = df_to_double(dfloat{d.vh[a * n + i], d.vl[a * n + i]});
+      }
       if (F) F[a * n + id] = (double)Fs[a * n + i];
     }
     if (epot) epot[id] = (double)Es[i];
@@ -617,7 +821,6 @@ struct md_handle_s {
   cudaGraphExec_t graph = nullptr;
   bool fp64 = true;
   int red_blocks = 1;
-  int build_warps = 2;  // warps per CTA of the list build (shared-memory lists)
   int64_t steps_done = 0;
   int64_t corr_base = 0;
   corr_handle banks[3];  // system-owned correlators (borrowed by md_corr)
@@ -680,13 +883,16 @@ int launch_rebuild(md_handle *h, cudaStream_t s) {
   const Sys &d = h->d;
   KTimer tm(h, s, MD_K_REBUILD);
   k_rb_zero<<<grid_for(d.ncell, kThreads), kThreads, 0, s>>>(d);
-  k_rb_assign<<<grid_for(d.n, kThreads), kThreads, 0, s>>>(d);
+  if (h->fp64)
+    k_rb_assign64<<<grid_for(d.n, kThreads), kThreads, 0, s>>>(d);
+  else
+    k_rb_assign_df<<<grid_for(d.n, kThreads), kThreads, 0, s>>>(d);
   k_rb_scan<<<1, 1024, 0, s>>>(d);
   k_rb_place<<<grid_for(d.n, kThreads), kThreads, 0, s>>>(d);
   k_rb_rank<TF><<<grid_for(d.ncell * 32, kCellWarps * 32), kCellWarps * 32, 0, s>>>(d);
   if (h->prm.pair_mode == MD_PAIR_VERLET)
-    k_cells<TF, true><<<std::min(ceil_div(d.ncell, h->build_warps), 152 * 16), h->build_warps * 32,
-                        (size_t)h->build_warps * d.maxnb * 32 * sizeof(uint32_t), s>>>(d, lj_of<TF>(h->prm));
+    k_cells<TF, true><<<std::min(ceil_div(d.ncell, kCellWarps), 152 * 16), kCellWarps * 32, 0, s>>>(
+        d, lj_of<TF>(h->prm));
   OTF_LAUNCH_CHECK();
   return MD_OK;
 }
@@ -721,7 +927,10 @@ int launch_step(md_handle *h, cudaStream_t s) {
   const Sys &d = h->d;
   {
     KTimer tm(h, s, MD_K_INTEGRATE);
-    k_kick_drift<TF><<<ceil_div(d.n, kThreads), kThreads, 0, s>>>(d, 0.5 * h->prm.dt);
+    if constexpr (std::is_same<TF, double>::value)
+      k_kick_drift64<<<ceil_div(d.n, kThreads), kThreads, 0, s>>>(d, 0.5 * h->prm.dt);
+    else
+      k_kick_drift_df<<<ceil_div(d.n, kThreads), kThreads, 0, s>>>(d);
     OTF_LAUNCH_CHECK();
   }
   int rc = launch_rebuild<TF>(h, s);
@@ -858,9 +1067,10 @@ void release(md_handle *h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   Sys &d = h->d;
-  void *ptrs[] = {d.r, d.v, d.F, d.epot, d.W, d.rel, d.relb, d.vbuf, d.id, d.type, d.cpk, d.rB, d.vB,
-                  d.idB, d.typeB, d.cellB, d.slot, d.perm, d.cellcount, d.cellstart, d.nbr, d.nnb,
-                  d.partials, d.counter, d.obs, d.rebuild, d.err, h->d_out};
+  void *ptrs[] = {d.r, d.v, d.offl, d.vh, d.vl, d.F, d.epot, d.W, d.rel, d.relb, d.vbuf, d.id, d.type,
+                  d.cpk, d.rB, d.vB, d.idB, d.typeB, d.cellB, d.slot, d.perm, d.cellcount, d.cellstart,
+                  d.chunkstart, d.nbr, d.nnb, d.nref, d.partials, d.counter, d.obs, d.rebuild, d.err,
+                  h->d_out};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (int k = 0; k < 3; ++k)
@@ -899,25 +1109,36 @@ int init_impl(md_handle *h, const md_params *p, const md_system *s) {
   }
   d.maxnb = maxnb;
   d.vacf_u = p->vacf.u;
+  // chunk blocks of the neighbour lists: a cell of k atoms needs ceil(k/32)
+  d.maxchunks = n / 32 + d.ncell;
+  if (d.maxchunks >= (int64_t(1) << 27)) {
+    set_error("md_init: %lld neighbour-list chunks exceed the 2^27 supported", (long long)d.maxchunks);
+    return MD_EINVAL;
+  }
+  for (int t = 0; t < 8; ++t) {
+    const dfloat h = df_from_double(0.5 * p->dt * d.invm[t]);
+    d.hdtm_h[t] = h.h;
+    d.hdtm_l[t] = h.l;
+  }
   {
-    // warps per CTA of the list build: each holds maxnb x 32 list words in
-    // shared memory; keep a CTA within 96 KB so several fit on an SM
-    const size_t per_warp = (size_t)maxnb * 32 * sizeof(uint32_t);
-    h->build_warps = (int)std::max<size_t>(1, std::min<size_t>(kCellWarps, (96 * 1024) / per_warp));
-    const int bytes = (int)(h->build_warps * per_warp);
-    if (per_warp > 200 * 1024) {
-      set_error("md_init: max_neighbors %d needs more shared memory than a CTA has", maxnb);
-      return MD_EINVAL;
-    }
-    OTF_CUDA(cudaFuncSetAttribute(k_cells<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    OTF_CUDA(cudaFuncSetAttribute(k_cells<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    const dfloat dtf = df_from_double(p->dt), ef = df_from_double(d.edge);
+    d.dt_h = dtf.h;
+    d.dt_l = dtf.l;
+    d.edge_h = ef.h;
+    d.edge_l = ef.l;
   }
   const size_t tf = h->fp64 ? sizeof(double) : sizeof(float);
   const size_t v4 = h->fp64 ? sizeof(dvec4) : sizeof(float4);
   h->red_blocks = grid_for(n, kThreads, kMaxRedBlocks);
   OTF_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-  OTF_CUDA(cudaMalloc(&d.r, 3 * n * sizeof(double)));
-  OTF_CUDA(cudaMalloc(&d.v, 3 * n * sizeof(double)));
+  if (h->fp64) {
+    OTF_CUDA(cudaMalloc(&d.r, 3 * n * sizeof(double)));
+    OTF_CUDA(cudaMalloc(&d.v, 3 * n * sizeof(double)));
+  } else {
+    OTF_CUDA(cudaMalloc(&d.offl, 3 * n * sizeof(float)));
+    OTF_CUDA(cudaMalloc(&d.vh, 3 * n * sizeof(float)));
+    OTF_CUDA(cudaMalloc(&d.vl, 3 * n * sizeof(float)));
+  }
   OTF_CUDA(cudaMalloc(&d.F, 3 * n * tf));
   OTF_CUDA(cudaMalloc(&d.epot, n * tf));
   OTF_CUDA(cudaMalloc(&d.W, 6 * n * tf));
@@ -936,8 +1157,11 @@ int init_impl(md_handle *h, const md_params *p, const md_system *s) {
   OTF_CUDA(cudaMalloc(&d.perm, n * sizeof(int)));
   OTF_CUDA(cudaMalloc(&d.cellcount, d.ncell * sizeof(int)));
   OTF_CUDA(cudaMalloc(&d.cellstart, (d.ncell + 1) * sizeof(int)));
-  if (p->pair_mode == MD_PAIR_VERLET) OTF_CUDA(cudaMalloc(&d.nbr, (size_t)maxnb * n * sizeof(uint32_t)));
+  OTF_CUDA(cudaMalloc(&d.chunkstart, (d.ncell + 1) * sizeof(int)));
+  if (p->pair_mode == MD_PAIR_VERLET)
+    OTF_CUDA(cudaMalloc(&d.nbr, (size_t)d.maxchunks * maxnb * 32 * sizeof(uint32_t)));
   OTF_CUDA(cudaMalloc(&d.nnb, n * sizeof(int)));
+  OTF_CUDA(cudaMalloc(&d.nref, n * sizeof(uint32_t)));
   OTF_CUDA(cudaMalloc(&d.partials, (size_t)h->red_blocks * kNRed * sizeof(double)));
   OTF_CUDA(cudaMalloc(&d.counter, sizeof(unsigned)));
   OTF_CUDA(cudaMalloc(&d.obs, sizeof(ObsDev)));
@@ -954,14 +1178,20 @@ int init_impl(md_handle *h, const md_params *p, const md_system *s) {
   const int one = 1;
   OTF_CUDA(cudaMemcpyAsync(d.rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, st));
   const cudaMemcpyKind kind = s->mem == MD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  OTF_CUDA(cudaMemcpyAsync(d.r, s->r, 3 * n * sizeof(double), kind, st));
-  OTF_CUDA(cudaMemcpyAsync(d.v, s->v, 3 * n * sizeof(double), kind, st));
+  // FP64 form: straight into the state; mixed form: through the scratch,
+  // converted to cell + double-float offset by k_init_df below
+  OTF_CUDA(cudaMemcpyAsync(h->fp64 ? d.r : d.rB, s->r, 3 * n * sizeof(double), kind, st));
+  OTF_CUDA(cudaMemcpyAsync(h->fp64 ? d.v : d.vB, s->v, 3 * n * sizeof(double), kind, st));
   if (s->type)
     OTF_CUDA(cudaMemcpyAsync(d.type, s->type, n * sizeof(int), kind, st));
   else
     OTF_CUDA(cudaMemsetAsync(d.type, 0, n * sizeof(int), st));
   k_iota<<<grid_for(n, kThreads), kThreads, 0, st>>>(d.id, n);
   OTF_LAUNCH_CHECK();
+  if (!h->fp64) {
+    k_init_df<<<grid_for(n, kThreads), kThreads, 0, st>>>(d);
+    OTF_LAUNCH_CHECK();
+  }
   // host-side copies of the inputs must be done before returning
   OTF_CUDA(cudaStreamSynchronize(st));
   // correlators
@@ -1111,7 +1341,10 @@ int md_scale_velocities(md_handle *h, double lambda) {
     set_error("md_scale_velocities: bad argument");
     return MD_EINVAL;
   }
-  k_scale_v<<<grid_for(3 * h->d.n, kThreads), kThreads, 0, h->stream>>>(h->d, lambda);
+  if (h->fp64)
+    k_scale_v<double><<<grid_for(3 * h->d.n, kThreads), kThreads, 0, h->stream>>>(h->d, lambda);
+  else
+    k_scale_v<float><<<grid_for(3 * h->d.n, kThreads), kThreads, 0, h->stream>>>(h->d, lambda);
   OTF_LAUNCH_CHECK();
   int rc = refresh_obs(h);
   if (rc) return rc;
