@@ -437,17 +437,14 @@ __device__ __forceinline__ void image_offset(int code, int &ox, int &oy, int &oz
   oz = code / 9 - 1;
 }
 
-// Link-cell kernel, one warp per cell (lanes = the cell's atoms, 32 at a
-// time; warps stride over the cells).  The 27 neighbour cells are staged
-// through shared memory 32 atoms at a time, already moved into the i cell's
-// frame; every lane then sweeps the staged atoms (broadcast reads).
-// BUILD: append every j within rlist to i's Verlet list, tagged with the
-// periodic image it was found in; the 32 atoms of a chunk own one block of
-// maxnb rows x 32 lanes.  !BUILD: evaluate the forces directly.
-template <typename TF, bool BUILD>
+// Direct link-cell forces (MD_PAIR_CELLS), one warp per cell (lanes = the
+// cell's atoms, 32 at a time; warps stride over the cells).  The 27
+// neighbour cells are staged through shared memory 32 atoms at a time,
+// already moved into the i cell's frame; every lane then sweeps the staged
+// atoms (broadcast reads).
+template <typename TF>
 __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
   using V4 = typename Vec4<TF>::type;
-  if (BUILD && !*d.rebuild) return;
   __shared__ V4 spos[kCellWarps][32];
   __shared__ int sidx[kCellWarps][32];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -463,9 +460,6 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
       V4 pi;
       if (act) pi = Vec4<TF>::load(rel + i);
       TF f[3] = {0, 0, 0}, e = 0, w[6] = {0, 0, 0, 0, 0, 0};
-      int cnt = 0;
-      const uint32_t chunk = BUILD ? (uint32_t)(d.chunkstart[c] + ((ib - i0) >> 5)) : 0u;
-      uint32_t *L = BUILD ? d.nbr + (int64_t)chunk * d.maxnb * 32 + lane : nullptr;
       for (int code = 0; code < 27; ++code) {
         int ox, oy, oz;
         image_offset(code, ox, oy, oz);
@@ -489,33 +483,110 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
           if (act) {
             for (int t = 0; t < nj; ++t) {
               const V4 pj = spos[wl][t];
-              const int j = sidx[wl][t];
-              // pj already holds j in i's cell frame: the subtraction is the
-              // one the list kernel performs
+              // pj already holds j in i's cell frame: the same subtraction
+              // the list kernel performs
               const TF dx = pi.x - pj.x;
               const TF dy = pi.y - pj.y;
               const TF dz = pi.z - pj.z;
               const TF r2 = dx * dx + dy * dy + dz * dz;
-              if (BUILD) {
-                if (r2 < lj.rlist2 && j != i) {
-                  if (cnt < d.maxnb) L[cnt * 32] = (uint32_t)j | ((uint32_t)code << 27);
-                  ++cnt;
-                }
-              } else {
-                if (r2 < lj.rc2 && j != i) lj_accumulate<TF>(lj, dx, dy, dz, r2, f, e, w);
-              }
+              if (r2 < lj.rc2 && sidx[wl][t] != i) lj_accumulate<TF>(lj, dx, dy, dz, r2, f, e, w);
             }
           }
         }
       }
-      if (act) {
-        if (BUILD) {
-          d.nnb[i] = min(cnt, d.maxnb);
-          d.nref[i] = (chunk << 5) | (uint32_t)lane;
-          if (cnt > d.maxnb) atomicOr(d.err, ERR_NBR_OVERFLOW);
+      if (act) store_pair_out<TF>(d, i, f, e, w);
+    }
+  }
+}
+
+// Verlet-list build, one warp per 32-atom chunk of a cell, j-parallel: the
+// chunk's i coordinates sit in shared memory; the lanes take 32 candidate
+// atoms at a time from a row of three x-adjacent neighbour cells (one
+// contiguous range of the cell-sorted order unless the row wraps), move
+// them into the i cell's frame, and for each i test all 32 at once; a
+// ballot and a population count give every accepted j its list slot.  The
+// chunk owns a block of maxnb rows x 32 lanes, so list rows stay together
+// in L2 while they fill.  Entries are j | (image code << 27).
+template <typename TF>
+__device__ __forceinline__ void build_range(const Sys &d, const LJ<TF> &lj, const typename Vec4<TF>::type *spi,
+                                            int ni, int ib, int a, int b, int b1, int b2, int oy, int oz,
+                                            uint32_t *blk, int &cnt) {
+  using V4 = typename Vec4<TF>::type;
+  const int lane = threadIdx.x & 31;
+  const V4 *rel = static_cast<const V4 *>(d.rel);
+  const TF edge = (TF)d.edge;
+  const unsigned below = (1u << lane) - 1u;
+  for (int jb = a; jb < b; jb += 32) {
+    const int j = jb + lane;
+    const bool jv = j < b;
+    const int ox = j < b1 ? -1 : (j < b2 ? 0 : 1);
+    V4 t;
+    t.x = t.y = t.z = TF(0);
+    if (jv) {
+      const V4 pj = Vec4<TF>::load(rel + j);
+      t.x = pj.x + ox * edge;
+      t.y = pj.y + oy * edge;
+      t.z = pj.z + oz * edge;
+    }
+    const uint32_t tag = (uint32_t)j | ((uint32_t)((ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)) << 27);
+    for (int ii = 0; ii < ni; ++ii) {
+      const V4 pi = spi[ii];
+      const TF dx = pi.x - t.x, dy = pi.y - t.y, dz = pi.z - t.z;
+      const TF r2 = dx * dx + dy * dy + dz * dz;
+      const bool acc = jv && r2 < lj.rlist2 && j != ib + ii;
+      const unsigned m = __ballot_sync(0xffffffffu, acc);
+      if (m) {
+        const int base = __shfl_sync(0xffffffffu, cnt, ii);
+        const int pos = base + __popc(m & below);
+        if (acc && pos < d.maxnb) blk[pos * 32 + ii] = tag;
+        if (lane == ii) cnt += __popc(m);
+      }
+    }
+  }
+}
+
+template <typename TF>
+__global__ void __launch_bounds__(kCellWarps * 32) k_build(Sys d, LJ<TF> lj) {
+  using V4 = typename Vec4<TF>::type;
+  if (!*d.rebuild) return;
+  __shared__ V4 spi[kCellWarps][32];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int nc = d.nc;
+  const V4 *rel = static_cast<const V4 *>(d.rel);
+  for (int64_t c = blockIdx.x * (int64_t)kCellWarps + wl; c < d.ncell; c += (int64_t)gridDim.x * kCellWarps) {
+    const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
+    const int i0 = d.cellstart[c], i1 = d.cellstart[c + 1];
+    for (int ib = i0; ib < i1; ib += 32) {
+      const int ni = min(32, i1 - ib);
+      __syncwarp();
+      if (lane < ni) spi[wl][lane] = Vec4<TF>::load(rel + ib + lane);
+      __syncwarp();
+      const uint32_t chunk = (uint32_t)(d.chunkstart[c] + ((ib - i0) >> 5));
+      uint32_t *blk = d.nbr + (int64_t)chunk * d.maxnb * 32;
+      int cnt = 0;  // lane l counts the list of atom ib + l
+      for (int row = 0; row < 9; ++row) {
+        const int oy = row % 3 - 1, oz = row / 3 - 1;
+        const int jy = (cy + oy + nc) % nc, jz = (cz + oz + nc) % nc;
+        const int64_t rb = ((int64_t)jz * nc + jy) * nc;
+        if (cx >= 1 && cx <= nc - 2) {
+          // cells cx-1, cx, cx+1 of the row are contiguous
+          build_range<TF>(d, lj, spi[wl], ni, ib, d.cellstart[rb + cx - 1], d.cellstart[rb + cx + 2],
+                          d.cellstart[rb + cx], d.cellstart[rb + cx + 1], oy, oz, blk, cnt);
         } else {
-          store_pair_out<TF>(d, i, f, e, w);
+          for (int ox = -1; ox <= 1; ++ox) {
+            const int jx = (cx + ox + nc) % nc;
+            const int a = d.cellstart[rb + jx], b = d.cellstart[rb + jx + 1];
+            // boundaries that give every j of this cell the offset ox
+            const int b1 = ox == -1 ? b : a, b2 = ox == 1 ? a : b;
+            build_range<TF>(d, lj, spi[wl], ni, ib, a, b, b1, b2, oy, oz, blk, cnt);
+          }
         }
+      }
+      if (lane < ni) {
+        const int i = ib + lane;
+        d.nnb[i] = min(cnt, d.maxnb);
+        d.nref[i] = (chunk << 5) | (uint32_t)lane;
+        if (cnt > d.maxnb) atomicOr(d.err, ERR_NBR_OVERFLOW);
       }
     }
   }
@@ -530,15 +601,15 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
 constexpr int kUnroll = 4;
 
 template <typename TF>
-__device__ __forceinline__ void pair_from_entry(const LJ<TF> &lj, const TF (*off)[3], uint32_t ent,
-                                                const typename Vec4<TF>::type &pi,
+__device__ __forceinline__ void pair_from_entry(const LJ<TF> &lj, const typename Vec4<TF>::type *off,
+                                                uint32_t ent, const typename Vec4<TF>::type &pi,
                                                 const typename Vec4<TF>::type &pj, TF f[3], TF &e, TF w[6]) {
-  const int code = (int)(ent >> 27);
+  const typename Vec4<TF>::type o = off[ent >> 27];
   // j moved into i's cell frame first: for a close pair across a cell face
   // pj + off lands next to pi, so the final subtraction is exact.
-  const TF dx = pi.x - (pj.x + off[code][0]);
-  const TF dy = pi.y - (pj.y + off[code][1]);
-  const TF dz = pi.z - (pj.z + off[code][2]);
+  const TF dx = pi.x - (pj.x + o.x);
+  const TF dy = pi.y - (pj.y + o.y);
+  const TF dz = pi.z - (pj.z + o.z);
   const TF r2 = dx * dx + dy * dy + dz * dz;
   if (r2 < lj.rc2) lj_accumulate<TF>(lj, dx, dy, dz, r2, f, e, w);
 }
@@ -546,13 +617,14 @@ __device__ __forceinline__ void pair_from_entry(const LJ<TF> &lj, const TF (*off
 template <typename TF>
 __global__ void __launch_bounds__(kPairThreads) k_pair_list(Sys d, LJ<TF> lj) {
   using V4 = typename Vec4<TF>::type;
-  __shared__ TF off[27][3];
+  __shared__ V4 off[27];  // image offsets, one vector load per pair
   if (threadIdx.x < 27) {
     int ox, oy, oz;
     image_offset(threadIdx.x, ox, oy, oz);
-    off[threadIdx.x][0] = ox * (TF)d.edge;
-    off[threadIdx.x][1] = oy * (TF)d.edge;
-    off[threadIdx.x][2] = oz * (TF)d.edge;
+    off[threadIdx.x].x = ox * (TF)d.edge;
+    off[threadIdx.x].y = oy * (TF)d.edge;
+    off[threadIdx.x].z = oz * (TF)d.edge;
+    off[threadIdx.x].w = TF(0);
   }
   __syncthreads();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -891,7 +963,7 @@ int launch_rebuild(md_handle *h, cudaStream_t s) {
   k_rb_place<<<grid_for(d.n, kThreads), kThreads, 0, s>>>(d);
   k_rb_rank<TF><<<grid_for(d.ncell * 32, kCellWarps * 32), kCellWarps * 32, 0, s>>>(d);
   if (h->prm.pair_mode == MD_PAIR_VERLET)
-    k_cells<TF, true><<<std::min(ceil_div(d.ncell, kCellWarps), 152 * 16), kCellWarps * 32, 0, s>>>(
+    k_build<TF><<<std::min(ceil_div(d.ncell, kCellWarps), 152 * 16), kCellWarps * 32, 0, s>>>(
         d, lj_of<TF>(h->prm));
   OTF_LAUNCH_CHECK();
   return MD_OK;
@@ -904,7 +976,7 @@ int launch_pair(md_handle *h, cudaStream_t s) {
   if (h->prm.pair_mode == MD_PAIR_VERLET)
     k_pair_list<TF><<<ceil_div(d.n, kPairThreads), kPairThreads, 0, s>>>(d, lj_of<TF>(h->prm));
   else
-    k_cells<TF, false><<<std::min(ceil_div(d.ncell, kCellWarps), 152 * 16), kCellWarps * 32, 0, s>>>(
+    k_cells<TF><<<std::min(ceil_div(d.ncell, kCellWarps), 152 * 16), kCellWarps * 32, 0, s>>>(
         d, lj_of<TF>(h->prm));
   OTF_LAUNCH_CHECK();
   return MD_OK;
