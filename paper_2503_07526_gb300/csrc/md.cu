@@ -69,10 +69,9 @@ struct Sys {
   int *id, *type, *cpk;      // atom id, type, packed cell coordinates
   // rebuild scratch (24 bytes per atom each)
   double *rB, *vB;
-  int *idB, *typeB, *cellB, *slot, *perm, *cellcount, *cellstart, *chunkstart;
-  uint32_t *nbr;             // [maxchunks][maxnb][32]: j | (image code << 27)
+  int *idB, *typeB, *cellB, *slot, *perm, *cellcount, *cellstart;
+  uint32_t *nbr;             // [n/32 chunks][maxnb][32]: j | (image code << 27)
   int *nnb;                  // list length per atom
-  uint32_t *nref;            // chunk << 5 | lane per atom
   // reductions and flags
   double *partials;
   unsigned *counter;
@@ -261,68 +260,50 @@ __global__ void __launch_bounds__(kThreads) k_rb_assign_df(Sys d) {
   }
 }
 
-// Exclusive scans of the cell counts and of the cells' 32-atom chunk counts
-// (one CTA of 1024 threads).  Warp w owns a contiguous segment and reads it
-// in coalesced rows of 32: pass 1 sums the segments, warp 0 scans the 32
-// sums, pass 2 scans each row with shuffles and a running carry.
+// Exclusive scan of the cell counts (one CTA of 1024 threads).  Warp w owns
+// a contiguous segment and reads it in coalesced rows of 32: pass 1 sums the
+// segments, warp 0 scans the 32 sums, pass 2 scans each row with shuffles
+// and a running carry.
 __global__ void __launch_bounds__(1024) k_rb_scan(Sys d) {
   if (!*d.rebuild) return;
-  __shared__ int wsum[2][32];
+  __shared__ int wsum[32];
   const int64_t nc3 = d.ncell;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t seg = (nc3 + 31) / 32;
   const int64_t c0 = warp * seg, c1 = min(nc3, c0 + seg);
-  int pa = 0, pb = 0;
-  for (int64_t c = c0 + lane; c < c1; c += 32) {
-    const int v = d.cellcount[c];
-    pa += v;
-    pb += (v + 31) >> 5;
-  }
-  pa = warp_sum(pa);
-  pb = warp_sum(pb);
-  if (lane == 0) {
-    wsum[0][warp] = pa;
-    wsum[1][warp] = pb;
-  }
+  int part = 0;
+  for (int64_t c = c0 + lane; c < c1; c += 32) part += d.cellcount[c];
+  part = warp_sum(part);
+  if (lane == 0) wsum[warp] = part;
   __syncthreads();
-  if (warp < 2) {
-    const int v = wsum[warp][lane];
+  if (warp == 0) {
+    const int v = wsum[lane];
     int incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += y;
     }
-    wsum[warp][lane] = incl - v;  // exclusive offset of each segment
+    wsum[lane] = incl - v;  // exclusive offset of each segment
   }
   __syncthreads();
-  int ca = wsum[0][warp], cb = wsum[1][warp];
+  int carry = wsum[warp];
   for (int64_t b = c0; b < c1; b += 32) {
     const int64_t c = b + lane;
-    const int va = c < c1 ? d.cellcount[c] : 0;
-    const int vb = (va + 31) >> 5;
-    int ia = va, ib = vb;
+    const int v = c < c1 ? d.cellcount[c] : 0;
+    int incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int ya = __shfl_up_sync(0xffffffffu, ia, o);
-      const int yb = __shfl_up_sync(0xffffffffu, ib, o);
-      if (lane >= o) {
-        ia += ya;
-        ib += yb;
-      }
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
-    if (c < c1) {
-      d.cellstart[c] = ca + ia - va;
-      d.chunkstart[c] = cb + ib - vb;
-    }
-    ca += __shfl_sync(0xffffffffu, ia, 31);
-    cb += __shfl_sync(0xffffffffu, ib, 31);
+    if (c < c1) d.cellstart[c] = carry + incl - v;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
   }
   if (threadIdx.x == 0) {
     d.cellstart[nc3] = (int)d.n;
     d.obs->rebuilds += 1;
   }
-  if (warp == 31 && lane == 0) d.chunkstart[nc3] = cb;  // total chunks
 }
 
 __global__ void __launch_bounds__(kThreads) k_rb_place(Sys d) {
@@ -499,95 +480,133 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
   }
 }
 
-// Verlet-list build, one warp per 32-atom chunk of a cell, j-parallel: the
-// chunk's i coordinates sit in shared memory; the lanes take 32 candidate
-// atoms at a time from a row of three x-adjacent neighbour cells (one
-// contiguous range of the cell-sorted order unless the row wraps), move
-// them into the i cell's frame, and for each i test all 32 at once; a
-// ballot and a population count give every accepted j its list slot.  The
-// chunk owns a block of maxnb rows x 32 lanes, so list rows stay together
-// in L2 while they fill.  Entries are j | (image code << 27).
-template <typename TF>
-__device__ __forceinline__ void build_range(const Sys &d, const LJ<TF> &lj, const typename Vec4<TF>::type *spi,
-                                            int ni, int ib, int a, int b, int b1, int b2, int oy, int oz,
-                                            uint32_t *blk, int &cnt) {
-  using V4 = typename Vec4<TF>::type;
-  const int lane = threadIdx.x & 31;
-  const V4 *rel = static_cast<const V4 *>(d.rel);
-  const TF edge = (TF)d.edge;
-  const unsigned below = (1u << lane) - 1u;
-  for (int jb = a; jb < b; jb += 32) {
-    const int j = jb + lane;
-    const bool jv = j < b;
-    const int ox = j < b1 ? -1 : (j < b2 ? 0 : 1);
-    V4 t;
-    t.x = t.y = t.z = TF(0);
-    if (jv) {
-      const V4 pj = Vec4<TF>::load(rel + j);
-      t.x = pj.x + ox * edge;
-      t.y = pj.y + oy * edge;
-      t.z = pj.z + oz * edge;
-    }
-    const uint32_t tag = (uint32_t)j | ((uint32_t)((ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)) << 27);
-    for (int ii = 0; ii < ni; ++ii) {
-      const V4 pi = spi[ii];
-      const TF dx = pi.x - t.x, dy = pi.y - t.y, dz = pi.z - t.z;
-      const TF r2 = dx * dx + dy * dy + dz * dz;
-      const bool acc = jv && r2 < lj.rlist2 && j != ib + ii;
-      const unsigned m = __ballot_sync(0xffffffffu, acc);
-      if (m) {
-        const int base = __shfl_sync(0xffffffffu, cnt, ii);
-        const int pos = base + __popc(m & below);
-        if (acc && pos < d.maxnb) blk[pos * 32 + ii] = tag;
-        if (lane == ii) cnt += __popc(m);
-      }
-    }
-  }
-}
+// Verlet-list build, one warp per chunk of 32 consecutive atoms of the
+// cell-sorted order; the lists of a chunk fill one block of maxnb rows x 32
+// lanes (entry k of atom i at block(i / 32) + 32 k + i % 32), so the pair
+// kernel reads a row of 128 bytes per step of its loop.  The chunk's atoms
+// fall into one or a few cells ("segments"); for each segment:
+//  pass 1, j-parallel: the lanes take 32 candidate atoms at a time from a
+//   row of three x-adjacent neighbour cells (one contiguous range of the
+//   sorted order unless the row wraps), move them into the i cell's frame
+//   and test them against every i of the segment; the ballot of the
+//   accepted lanes is stored as a 32-bit mask per (i, candidate block);
+//  pass 2, i-parallel: each lane walks its own masks in order and writes its
+//   list, one row per entry, all lanes advancing together.
+// Entries are j | (image code << 27).  kMaxBlk masks are kept per lane; a
+// segment with more candidate blocks is flushed through pass 2 in parts.
+constexpr int kMaxBlk = 48;
+constexpr int kMaskPitch = kMaxBlk + 1;  // odd pitch: conflict-free pass 2
+
+struct CandBlock {
+  int jstart;  // first candidate atom of the block
+  int b1, b2;  // j < b1: image x offset -1, j < b2: 0, else +1
+  int yz;      // (oy + 1) + 3 (oz + 1)
+};
 
 template <typename TF>
 __global__ void __launch_bounds__(kCellWarps * 32) k_build(Sys d, LJ<TF> lj) {
   using V4 = typename Vec4<TF>::type;
   if (!*d.rebuild) return;
   __shared__ V4 spi[kCellWarps][32];
+  __shared__ uint32_t smask[kCellWarps][32 * kMaskPitch];
+  __shared__ CandBlock sblk[kCellWarps][kMaxBlk];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int nc = d.nc;
+  const int64_t n = d.n;
   const V4 *rel = static_cast<const V4 *>(d.rel);
-  for (int64_t c = blockIdx.x * (int64_t)kCellWarps + wl; c < d.ncell; c += (int64_t)gridDim.x * kCellWarps) {
-    const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
-    const int i0 = d.cellstart[c], i1 = d.cellstart[c + 1];
-    for (int ib = i0; ib < i1; ib += 32) {
-      const int ni = min(32, i1 - ib);
+  const TF edge = (TF)d.edge;
+  uint32_t *masks = smask[wl];
+  CandBlock *blks = sblk[wl];
+  const int64_t nchunks = (n + 31) / 32;
+  for (int64_t q = blockIdx.x * (int64_t)kCellWarps + wl; q < nchunks; q += (int64_t)gridDim.x * kCellWarps) {
+    const int a0 = (int)(q * 32), a1 = (int)min((int64_t)a0 + 32, n);
+    __syncwarp();
+    if (a0 + lane < a1) spi[wl][lane] = Vec4<TF>::load(rel + a0 + lane);
+    __syncwarp();
+    uint32_t *blk = d.nbr + q * d.maxnb * 32 + lane;
+    int cnt = 0;  // lane l: list length of atom a0 + l
+    int nblk = 0;
+    // pass 2 for the masks gathered so far (lanes of [s, e) only)
+    auto flush = [&](int s, int e) {
       __syncwarp();
-      if (lane < ni) spi[wl][lane] = Vec4<TF>::load(rel + ib + lane);
+      if (a0 + lane >= s && a0 + lane < e) {
+        for (int k = 0; k < nblk; ++k) {
+          uint32_t m = masks[lane * kMaskPitch + k];
+          const CandBlock cb = blks[k];
+          const uint32_t yzc = (uint32_t)(3 * cb.yz) << 27;  // 3 (oy+1) + 9 (oz+1)
+          while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1u;
+            const int j = cb.jstart + b;
+            const uint32_t xc = j < cb.b1 ? 0u : (j < cb.b2 ? 1u : 2u);
+            if (cnt < d.maxnb) blk[cnt * 32] = (uint32_t)j | yzc | (xc << 27);
+            ++cnt;
+          }
+        }
+      }
+      nblk = 0;
       __syncwarp();
-      const uint32_t chunk = (uint32_t)(d.chunkstart[c] + ((ib - i0) >> 5));
-      uint32_t *blk = d.nbr + (int64_t)chunk * d.maxnb * 32;
-      int cnt = 0;  // lane l counts the list of atom ib + l
+    };
+    int s = a0;
+    while (s < a1) {
+      const int c = [&] {
+        int cx, cy, cz;
+        unpack_cell(d.cpk[s], cx, cy, cz);
+        return (cz * nc + cy) * nc + cx;
+      }();
+      const int e = min(d.cellstart[c + 1], a1);
+      const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
       for (int row = 0; row < 9; ++row) {
         const int oy = row % 3 - 1, oz = row / 3 - 1;
         const int jy = (cy + oy + nc) % nc, jz = (cz + oz + nc) % nc;
         const int64_t rb = ((int64_t)jz * nc + jy) * nc;
-        if (cx >= 1 && cx <= nc - 2) {
-          // cells cx-1, cx, cx+1 of the row are contiguous
-          build_range<TF>(d, lj, spi[wl], ni, ib, d.cellstart[rb + cx - 1], d.cellstart[rb + cx + 2],
-                          d.cellstart[rb + cx], d.cellstart[rb + cx + 1], oy, oz, blk, cnt);
-        } else {
-          for (int ox = -1; ox <= 1; ++ox) {
+        const bool contig = cx >= 1 && cx <= nc - 2;
+        for (int piece = 0; piece < (contig ? 1 : 3); ++piece) {
+          int ra, rbnd, b1, b2;
+          if (contig) {  // cells cx-1, cx, cx+1 of the row are contiguous
+            ra = d.cellstart[rb + cx - 1];
+            rbnd = d.cellstart[rb + cx + 2];
+            b1 = d.cellstart[rb + cx];
+            b2 = d.cellstart[rb + cx + 1];
+          } else {
+            const int ox = piece - 1;
             const int jx = (cx + ox + nc) % nc;
-            const int a = d.cellstart[rb + jx], b = d.cellstart[rb + jx + 1];
-            // boundaries that give every j of this cell the offset ox
-            const int b1 = ox == -1 ? b : a, b2 = ox == 1 ? a : b;
-            build_range<TF>(d, lj, spi[wl], ni, ib, a, b, b1, b2, oy, oz, blk, cnt);
+            ra = d.cellstart[rb + jx];
+            rbnd = d.cellstart[rb + jx + 1];
+            b1 = ox == -1 ? rbnd : ra;  // every j of this cell gets offset ox
+            b2 = ox == 1 ? ra : rbnd;
+          }
+          for (int jb = ra; jb < rbnd; jb += 32) {
+            if (nblk == kMaxBlk) flush(s, e);
+            const int j = jb + lane;
+            const bool jv = j < rbnd;
+            const int ox = j < b1 ? -1 : (j < b2 ? 0 : 1);
+            V4 t;
+            t.x = t.y = t.z = TF(0);
+            if (jv) {
+              const V4 pj = Vec4<TF>::load(rel + j);
+              t.x = pj.x + ox * edge;
+              t.y = pj.y + oy * edge;
+              t.z = pj.z + oz * edge;
+            }
+            for (int ii = s; ii < e; ++ii) {
+              const V4 pi = spi[wl][ii - a0];
+              const TF dx = pi.x - t.x, dy = pi.y - t.y, dz = pi.z - t.z;
+              const TF r2 = dx * dx + dy * dy + dz * dz;
+              const unsigned m = __ballot_sync(0xffffffffu, jv && r2 < lj.rlist2 && j != ii);
+              if (lane == 0) masks[(ii - a0) * kMaskPitch + nblk] = m;
+            }
+            if (lane == 0) blks[nblk] = CandBlock{jb, b1, b2, row};
+            ++nblk;
           }
         }
       }
-      if (lane < ni) {
-        const int i = ib + lane;
-        d.nnb[i] = min(cnt, d.maxnb);
-        d.nref[i] = (chunk << 5) | (uint32_t)lane;
-        if (cnt > d.maxnb) atomicOr(d.err, ERR_NBR_OVERFLOW);
-      }
+      flush(s, e);
+      s = e;
+    }
+    if (a0 + lane < a1) {
+      d.nnb[a0 + lane] = min(cnt, d.maxnb);
+      if (cnt > d.maxnb) atomicOr(d.err, ERR_NBR_OVERFLOW);
     }
   }
 }
@@ -633,8 +652,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_list(Sys d, LJ<TF> lj) {
   const V4 pi = Vec4<TF>::load(rel + i);
   TF f[3] = {0, 0, 0}, e = 0, w[6] = {0, 0, 0, 0, 0, 0};
   const int nn = d.nnb[i];
-  const uint32_t ref = d.nref[i];
-  const uint32_t *nb = d.nbr + (int64_t)(ref >> 5) * d.maxnb * 32 + (ref & 31u);
+  const uint32_t *nb = d.nbr + (i >> 5) * d.maxnb * 32 + (i & 31);
   int k = 0;
   for (; k + kUnroll <= nn; k += kUnroll) {
     uint32_t ent[kUnroll];
@@ -1141,7 +1159,7 @@ void release(md_handle *h) {
   Sys &d = h->d;
   void *ptrs[] = {d.r, d.v, d.offl, d.vh, d.vl, d.F, d.epot, d.W, d.rel, d.relb, d.vbuf, d.id, d.type,
                   d.cpk, d.rB, d.vB, d.idB, d.typeB, d.cellB, d.slot, d.perm, d.cellcount, d.cellstart,
-                  d.chunkstart, d.nbr, d.nnb, d.nref, d.partials, d.counter, d.obs, d.rebuild, d.err,
+                  d.nbr, d.nnb, d.partials, d.counter, d.obs, d.rebuild, d.err,
                   h->d_out};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -1181,12 +1199,7 @@ int init_impl(md_handle *h, const md_params *p, const md_system *s) {
   }
   d.maxnb = maxnb;
   d.vacf_u = p->vacf.u;
-  // chunk blocks of the neighbour lists: a cell of k atoms needs ceil(k/32)
-  d.maxchunks = n / 32 + d.ncell;
-  if (d.maxchunks >= (int64_t(1) << 27)) {
-    set_error("md_init: %lld neighbour-list chunks exceed the 2^27 supported", (long long)d.maxchunks);
-    return MD_EINVAL;
-  }
+  d.maxchunks = (n + 31) / 32;  // 32-atom chunks of the neighbour lists
   for (int t = 0; t < 8; ++t) {
     const dfloat h = df_from_double(0.5 * p->dt * d.invm[t]);
     d.hdtm_h[t] = h.h;
@@ -1229,11 +1242,9 @@ int init_impl(md_handle *h, const md_params *p, const md_system *s) {
   OTF_CUDA(cudaMalloc(&d.perm, n * sizeof(int)));
   OTF_CUDA(cudaMalloc(&d.cellcount, d.ncell * sizeof(int)));
   OTF_CUDA(cudaMalloc(&d.cellstart, (d.ncell + 1) * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&d.chunkstart, (d.ncell + 1) * sizeof(int)));
   if (p->pair_mode == MD_PAIR_VERLET)
     OTF_CUDA(cudaMalloc(&d.nbr, (size_t)d.maxchunks * maxnb * 32 * sizeof(uint32_t)));
   OTF_CUDA(cudaMalloc(&d.nnb, n * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&d.nref, n * sizeof(uint32_t)));
   OTF_CUDA(cudaMalloc(&d.partials, (size_t)h->red_blocks * kNRed * sizeof(double)));
   OTF_CUDA(cudaMalloc(&d.counter, sizeof(unsigned)));
   OTF_CUDA(cudaMalloc(&d.obs, sizeof(ObsDev)));
