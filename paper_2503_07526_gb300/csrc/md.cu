@@ -533,13 +533,13 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_build(Sys d, LJ<TF> lj) {
         for (int k = 0; k < nblk; ++k) {
           uint32_t m = masks[lane * kMaskPitch + k];
           const CandBlock cb = blks[k];
-          const uint32_t yzc = (uint32_t)(3 * cb.yz) << 27;  // 3 (oy+1) + 9 (oz+1)
+          const uint32_t yz3 = (uint32_t)(3 * cb.yz);  // 3 (oy+1) + 9 (oz+1)
           while (m) {
             const int b = __ffs(m) - 1;
             m &= m - 1u;
             const int j = cb.jstart + b;
-            const uint32_t xc = j < cb.b1 ? 0u : (j < cb.b2 ? 1u : 2u);
-            if (cnt < d.maxnb) blk[cnt * 32] = (uint32_t)j | yzc | (xc << 27);
+            const uint32_t code = yz3 + (j < cb.b1 ? 0u : (j < cb.b2 ? 1u : 2u));  // + (ox+1)
+            if (cnt < d.maxnb) blk[cnt * 32] = (uint32_t)j | (code << 27);
             ++cnt;
           }
         }
