@@ -483,79 +483,39 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
 // Verlet-list build, one warp per chunk of 32 consecutive atoms of the
 // cell-sorted order; the lists of a chunk fill one block of maxnb rows x 32
 // lanes (entry k of atom i at block(i / 32) + 32 k + i % 32), so the pair
-// kernel reads a row of 128 bytes per step of its loop.  The chunk's atoms
-// fall into one or a few cells ("segments"); for each segment:
-//  pass 1, j-parallel: the lanes take 32 candidate atoms at a time from a
-//   row of three x-adjacent neighbour cells (one contiguous range of the
-//   sorted order unless the row wraps), move them into the i cell's frame
-//   and test them against every i of the segment; the ballot of the
-//   accepted lanes is stored as a 32-bit mask per (i, candidate block);
-//  pass 2, i-parallel: each lane walks its own masks in order and writes its
-//   list, one row per entry, all lanes advancing together.
-// Entries are j | (image code << 27).  kMaxBlk masks are kept per lane; a
-// segment with more candidate blocks is flushed through pass 2 in parts.
-constexpr int kMaxBlk = 48;
-constexpr int kMaskPitch = kMaxBlk + 1;  // odd pitch: conflict-free pass 2
-
-struct CandBlock {
-  int jstart;  // first candidate atom of the block
-  int b1, b2;  // j < b1: image x offset -1, j < b2: 0, else +1
-  int yz;      // (oy + 1) + 3 (oz + 1)
-};
-
+// kernel reads a row of 128 bytes per step of its loop and the rows being
+// written stay together in L2.  The chunk's atoms fall into one or a few
+// cells ("segments").  For each segment, j-parallel: the chunk's i
+// coordinates sit in shared memory; the lanes take 32 candidate atoms at a
+// time from a row of three x-adjacent neighbour cells (one contiguous range
+// of the sorted order unless the row wraps), move them into the i cell's
+// frame and, for each i of the segment, test all 32 at once; a ballot and a
+// population count give every accepted j its list slot.  Entries are
+// j | (image code << 27).
 template <typename TF>
 __global__ void __launch_bounds__(kCellWarps * 32) k_build(Sys d, LJ<TF> lj) {
   using V4 = typename Vec4<TF>::type;
   if (!*d.rebuild) return;
   __shared__ V4 spi[kCellWarps][32];
-  __shared__ uint32_t smask[kCellWarps][32 * kMaskPitch];
-  __shared__ CandBlock sblk[kCellWarps][kMaxBlk];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int nc = d.nc;
   const int64_t n = d.n;
   const V4 *rel = static_cast<const V4 *>(d.rel);
   const TF edge = (TF)d.edge;
-  uint32_t *masks = smask[wl];
-  CandBlock *blks = sblk[wl];
+  const unsigned below = (1u << lane) - 1u;
   const int64_t nchunks = (n + 31) / 32;
   for (int64_t q = blockIdx.x * (int64_t)kCellWarps + wl; q < nchunks; q += (int64_t)gridDim.x * kCellWarps) {
     const int a0 = (int)(q * 32), a1 = (int)min((int64_t)a0 + 32, n);
     __syncwarp();
     if (a0 + lane < a1) spi[wl][lane] = Vec4<TF>::load(rel + a0 + lane);
     __syncwarp();
-    uint32_t *blk = d.nbr + q * d.maxnb * 32 + lane;
+    uint32_t *blk = d.nbr + q * d.maxnb * 32;
     int cnt = 0;  // lane l: list length of atom a0 + l
-    int nblk = 0;
-    // pass 2 for the masks gathered so far (lanes of [s, e) only)
-    auto flush = [&](int s, int e) {
-      __syncwarp();
-      if (a0 + lane >= s && a0 + lane < e) {
-        for (int k = 0; k < nblk; ++k) {
-          uint32_t m = masks[lane * kMaskPitch + k];
-          const CandBlock cb = blks[k];
-          const uint32_t yz3 = (uint32_t)(3 * cb.yz);  // 3 (oy+1) + 9 (oz+1)
-          while (m) {
-            const int b = __ffs(m) - 1;
-            m &= m - 1u;
-            const int j = cb.jstart + b;
-            const uint32_t code = yz3 + (j < cb.b1 ? 0u : (j < cb.b2 ? 1u : 2u));  // + (ox+1)
-            if (cnt < d.maxnb) blk[cnt * 32] = (uint32_t)j | (code << 27);
-            ++cnt;
-          }
-        }
-      }
-      nblk = 0;
-      __syncwarp();
-    };
     int s = a0;
     while (s < a1) {
-      const int c = [&] {
-        int cx, cy, cz;
-        unpack_cell(d.cpk[s], cx, cy, cz);
-        return (cz * nc + cy) * nc + cx;
-      }();
-      const int e = min(d.cellstart[c + 1], a1);
-      const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+      int cx, cy, cz;
+      unpack_cell(d.cpk[s], cx, cy, cz);
+      const int e = min(d.cellstart[(cz * nc + cy) * nc + cx + 1], a1);
       for (int row = 0; row < 9; ++row) {
         const int oy = row % 3 - 1, oz = row / 3 - 1;
         const int jy = (cy + oy + nc) % nc, jz = (cz + oz + nc) % nc;
@@ -577,7 +537,6 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_build(Sys d, LJ<TF> lj) {
             b2 = ox == 1 ? ra : rbnd;
           }
           for (int jb = ra; jb < rbnd; jb += 32) {
-            if (nblk == kMaxBlk) flush(s, e);
             const int j = jb + lane;
             const bool jv = j < rbnd;
             const int ox = j < b1 ? -1 : (j < b2 ? 0 : 1);
@@ -589,19 +548,24 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_build(Sys d, LJ<TF> lj) {
               t.y = pj.y + oy * edge;
               t.z = pj.z + oz * edge;
             }
+            const uint32_t tag = (uint32_t)j | ((uint32_t)((ox + 1) + 3 * row) << 27);
             for (int ii = s; ii < e; ++ii) {
-              const V4 pi = spi[wl][ii - a0];
+              const int li = ii - a0;  // lane that owns atom ii
+              const V4 pi = spi[wl][li];
               const TF dx = pi.x - t.x, dy = pi.y - t.y, dz = pi.z - t.z;
               const TF r2 = dx * dx + dy * dy + dz * dz;
-              const unsigned m = __ballot_sync(0xffffffffu, jv && r2 < lj.rlist2 && j != ii);
-              if (lane == 0) masks[(ii - a0) * kMaskPitch + nblk] = m;
+              const bool acc = jv && r2 < lj.rlist2 && j != ii;
+              const unsigned m = __ballot_sync(0xffffffffu, acc);
+              if (m) {
+                const int base = __shfl_sync(0xffffffffu, cnt, li);
+                const int pos = base + __popc(m & below);
+                if (acc && pos < d.maxnb) blk[pos * 32 + li] = tag;
+                if (lane == li) cnt += __popc(m);
+              }
             }
-            if (lane == 0) blks[nblk] = CandBlock{jb, b1, b2, row};
-            ++nblk;
           }
         }
       }
-      flush(s, e);
       s = e;
     }
     if (a0 + lane < a1) {
