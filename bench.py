@@ -46,13 +46,6 @@ def workload_name(n):
             f"(b=12,p=16,m=2,u=1), per-atom VACF over all atoms (b=8,p=16,m=2,u=1)")
 
 
-def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", str(rank)))
-    return rank, world, local
-
-
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -170,7 +163,9 @@ def prepare_state(pkg, synth, seed, cells=CELLS, melt_steps=600):
 def run_ours(args):
     import torch
 
-    rank, world, local = dist_env()
+    from paper_2503_07526_gb300 import replicas
+
+    rank, world, local = replicas.dist_env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -181,7 +176,8 @@ def run_ours(args):
     from paper_2503_07526_gb300 import synth
 
     pkg.lib()
-    s, st = prepare_state(pkg, synth, seed=1 + rank, cells=args.cells, melt_steps=100 if args.quick else 600)
+    s, st = prepare_state(pkg, synth, seed=replicas.replica_seed(1, rank), cells=args.cells,
+                          melt_steps=100 if args.quick else 600)
     n, L = s["n"], s["L"]
     p = pkg.make_params(n, L, rc=RC, dt=DT, skin=SKIN, precision=pkg.MD_PREC_MIXED, **SPEC)
     g = pkg.System(p, st["r"], st["v"])
@@ -207,12 +203,9 @@ def run_ours(args):
     ms_total = e0.elapsed_time(e1)
     ktimes = g.kernel_times()
     g.set_timing(False)
-    if dist:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = replicas.max_over_ranks(ms_total, dist, device="cuda")  # the slowest rank
     ms_step = ms_total / args.steps
-    value = world * n * args.steps / (ms_total / 1e3)
+    value = replicas.weak_scaling_rate(n, args.steps, world, ms_total / 1e3)
 
     # graph-replay time of the same step (product default), for reference
     barrier()
@@ -252,10 +245,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     ge.close()
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = replicas.max_over_ranks(e2e_s, dist, device="cuda")
     h2d = (2 * 3 * n * 8) / args.steps
     d2h = (8 * 16 + 3 * 2 * 8 * (12 * 16 + 12 * 16 + 8 * 16)) / args.steps
 
@@ -311,7 +301,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (state + neighbour lists + VACF ring about 5 GB)",
                    "timing": "CUDA events around every kernel on the system stream; eager launches"},
         "clocks": clk.summary(),
-        "e2e": {"value": world * n * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": replicas.weak_scaling_rate(n, args.steps, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "what": "md_init from host arrays + md_step(K) + md_observables + corr_read of all correlators"},
         "gpu_launches": launches_per_step * args.steps,
@@ -375,7 +365,9 @@ def cpu_baseline(st, s, budget_s=20.0):
 
 def run_reference(args):
     """The oracle on the host cores, on this arm's workload (rank 0 only)."""
-    rank, world, _ = dist_env()
+    from paper_2503_07526_gb300 import replicas
+
+    rank, world, _ = replicas.dist_env()
     if rank != 0:
         return
     from paper_2503_07526_gb300 import synth
