@@ -94,6 +94,9 @@ typedef struct {
   double skin;        /* Verlet skin (MD_PAIR_VERLET); 0 rebuilds every step */
   int32_t max_neighbors; /* neighbour-list capacity per atom; 0 = automatic */
   int32_t use_graph;  /* 1: md_step replays a captured CUDA graph of a step */
+  int32_t autotune;   /* 1: md_init times the pair kernel (64/128/256 threads
+                         per CTA) and the list build (2/4/8 warps per CTA) on
+                         the system and keeps the fastest (md_get_config) */
   corr_spec stress, heatflux, vacf; /* the three correlators of Sec. 2.3/2.7 */
 } md_params;
 
@@ -103,6 +106,25 @@ typedef struct {
   const int32_t *type; /* [n] type of each atom, or NULL for all type 0 */
   int32_t mem;         /* MD_MEM_HOST or MD_MEM_DEVICE for the three arrays */
 } md_system;
+
+/* One replica of a batch (md_init_replicas): its own atoms, box, positions
+ * [3][n], velocities [3][n] and types (NULL: all type 0). */
+typedef struct {
+  int64_t n;
+  double box;
+  const double *r;
+  const double *v;
+  const int32_t *type;
+} md_replica;
+
+/* Launch shapes and sizes chosen for a system (md_get_config). */
+typedef struct {
+  int32_t replicas;
+  int32_t pair_threads;   /* threads per CTA of the pair kernel */
+  int32_t build_warps;    /* warps per CTA of the neighbour-list build */
+  int32_t max_neighbors;  /* neighbour-list capacity per atom */
+  int64_t atoms, cells;   /* totals over all replicas */
+} md_config;
 
 /* Observables of the last completed step (Sec. 2.3). */
 typedef struct {
@@ -125,6 +147,20 @@ typedef struct corr_handle_s corr_handle;
  * MD_ESTATE for non-finite input. */
 OTF_API int md_init(const md_params *p, const md_system *s, void *cuda_stream, md_handle **out);
 
+/* A batch of independent replicas (sizes, densities and temperatures may
+ * differ; the LJ parameters, time step, precision and correlator settings of
+ * p are shared; p->n and p->box are ignored).  Their atoms, cells and
+ * reduction CTAs are laid end to end, so every kernel of a step covers all
+ * replicas and one captured graph launch advances the whole batch.  Every
+ * replica needs at least 256 atoms and 3 cells per side; the per-atom
+ * velocity correlator must be off (vacf.u = 0).  The stress and heat-flux
+ * correlators then hold 3 series per replica (replica r: series 3r..3r+2,
+ * read with corr_read(group = 3r + k)).  mem says where all the replicas'
+ * arrays live.  Otherwise as md_init; the other md_* calls apply to all
+ * replicas (md_observables reports replica 0). */
+OTF_API int md_init_replicas(const md_params *p, const md_replica *reps, int32_t count, int32_t mem,
+                             void *cuda_stream, md_handle **out);
+
 /* Advances nsteps velocity-Verlet NVE steps (Sec. 1).  Each step: half
  * kick and drift; neighbour-list rebuild when needed; pair forces with
  * per-particle energy and virial; half kick; reduction to U, K, sigma, q;
@@ -135,8 +171,11 @@ OTF_API int md_init(const md_params *p, const md_system *s, void *cuda_stream, m
  * then undefined). */
 OTF_API int md_step(md_handle *h, int64_t nsteps);
 
-/* Observables of the last step (synchronises). */
+/* Observables of the last step (synchronises); replica 0 of a batch. */
 OTF_API int md_observables(md_handle *h, md_obs *out);
+
+/* Observables of replica r of a batch (synchronises). */
+OTF_API int md_replica_observables(md_handle *h, int32_t r, md_obs *out);
 
 /* Per-particle state in the caller's atom order: positions (wrapped into
  * [0, box)), velocities, forces, potential energies [n] and virials [6][n]
@@ -148,6 +187,14 @@ OTF_API int md_get_particles(md_handle *h, double *r, double *v, double *F, doub
 /* Multiplies every velocity by lambda (velocity-rescaling equilibration;
  * not part of the correlated run) and refreshes the observables. */
 OTF_API int md_scale_velocities(md_handle *h, double lambda);
+
+/* Per-replica velocity rescaling: replica r's velocities times lambda[r]
+ * (host array of one factor per replica). */
+OTF_API int md_replica_scale_velocities(md_handle *h, const double *lambda);
+
+/* Replica count, total atoms and cells, list capacity and the launch shapes
+ * in use (after autotuning when md_params.autotune was set). */
+OTF_API int md_get_config(md_handle *h, md_config *out);
 
 /* Clears the correlators and the running temperature mean of a system, so
  * that a production run can start after equilibration. */

@@ -40,12 +40,21 @@ class md_params(C.Structure):
     _fields_ = [("n", C.c_int64), ("box", C.c_double), ("eps", C.c_double), ("sigma", C.c_double),
                 ("rc", C.c_double), ("shift", C.c_int32), ("ntypes", C.c_int32), ("mass", C.c_double * 8),
                 ("dt", C.c_double), ("precision", C.c_int32), ("pair_mode", C.c_int32), ("skin", C.c_double),
-                ("max_neighbors", C.c_int32), ("use_graph", C.c_int32), ("stress", corr_spec),
+                ("max_neighbors", C.c_int32), ("use_graph", C.c_int32), ("autotune", C.c_int32), ("stress", corr_spec),
                 ("heatflux", corr_spec), ("vacf", corr_spec)]
 
 
 class md_system(C.Structure):
     _fields_ = [("r", C.c_void_p), ("v", C.c_void_p), ("type", C.c_void_p), ("mem", C.c_int32)]
+
+
+class md_replica(C.Structure):
+    _fields_ = [("n", C.c_int64), ("box", C.c_double), ("r", C.c_void_p), ("v", C.c_void_p), ("type", C.c_void_p)]
+
+
+class md_config(C.Structure):
+    _fields_ = [("replicas", C.c_int32), ("pair_threads", C.c_int32), ("build_warps", C.c_int32),
+                ("max_neighbors", C.c_int32), ("atoms", C.c_int64), ("cells", C.c_int64)]
 
 
 class md_obs(C.Structure):
@@ -76,6 +85,10 @@ def lib(build: bool = False):
     vp, i64, i32, dp = C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_double)
     sig = {
         "md_init": [C.POINTER(md_params), C.POINTER(md_system), vp, C.POINTER(vp)],
+        "md_init_replicas": [C.POINTER(md_params), C.POINTER(md_replica), i32, i32, vp, C.POINTER(vp)],
+        "md_replica_observables": [vp, i32, C.POINTER(md_obs)],
+        "md_replica_scale_velocities": [vp, dp],
+        "md_get_config": [vp, C.POINTER(md_config)],
         "md_step": [vp, i64],
         "md_observables": [vp, C.POINTER(md_obs)],
         "md_get_particles": [vp, vp, vp, vp, vp, vp, i32],
@@ -110,7 +123,8 @@ def lib(build: bool = False):
 EXPORTS = ("md_init", "md_step", "md_observables", "md_get_particles", "md_scale_velocities",
            "md_reset_correlators", "md_corr", "md_set_timing", "md_kernel_times", "md_free", "corr_create",
            "corr_push", "corr_read", "corr_raw", "corr_pushes", "corr_reset", "corr_free", "gk_integrate",
-           "md_last_error", "md_observables_noalloc")
+           "md_last_error", "md_observables_noalloc", "md_init_replicas", "md_replica_observables",
+           "md_replica_scale_velocities", "md_get_config")
 
 
 def _check(rc):
@@ -169,14 +183,14 @@ _init_dtypes()
 
 def make_params(n, box, *, eps=1.0, sigma=1.0, rc=2.5, shift=True, masses=(1.0,), dt=0.005,
                 precision=MD_PREC_FP64, pair_mode=MD_PAIR_VERLET, skin=0.3, max_neighbors=0, use_graph=True,
-                stress=(12, 16, 2, 1), heatflux=(12, 16, 2, 1), vacf=(8, 16, 2, 1)):
+                autotune=False, stress=(12, 16, 2, 1), heatflux=(12, 16, 2, 1), vacf=(8, 16, 2, 1)):
     p = md_params()
     p.n, p.box, p.eps, p.sigma, p.rc, p.shift = int(n), float(box), eps, sigma, rc, int(bool(shift))
     p.ntypes = len(masses)
     for t, m in enumerate(masses):
         p.mass[t] = float(m)
     p.dt, p.precision, p.pair_mode, p.skin = dt, int(precision), int(pair_mode), float(skin)
-    p.max_neighbors, p.use_graph = int(max_neighbors), int(bool(use_graph))
+    p.max_neighbors, p.use_graph, p.autotune = int(max_neighbors), int(bool(use_graph)), int(bool(autotune))
     for name, spec in (("stress", stress), ("heatflux", heatflux), ("vacf", vacf)):
         cs = getattr(p, name)
         cs.b, cs.p, cs.m, cs.u = spec if spec is not None else (1, 2, 1, 0)
@@ -244,9 +258,13 @@ class Corr:
 class System:
     """An MD system on the GPU behind md_init / md_step / md_free."""
 
-    def __init__(self, params: md_params, r, v, types=None, stream=None):
+    def __init__(self, params: md_params, r=None, v=None, types=None, stream=None, replicas=None):
         self.params = params
+        if replicas is not None:
+            self._init_replicas(params, replicas, stream)
+            return
         self.n = params.n
+        self.nrep = 1
         pr, mem, kr = _ptr(r, F64)
         pv, memv, kv = _ptr(v, F64)
         pt, kt = None, None
@@ -261,6 +279,47 @@ class System:
         self.stream = _stream_ptr(stream)
         _check(lib().md_init(C.byref(params), C.byref(sysd), self.stream, C.byref(h)))
         self._h = h
+
+    def _init_replicas(self, params, replicas, stream):
+        """replicas: list of dicts with r [3,n], v [3,n], box and optional types
+        (numpy arrays or CUDA tensors, all in the same memory)."""
+        arr = (md_replica * len(replicas))()
+        keep, mems = [], set()
+        for k, rp in enumerate(replicas):
+            pr, mem, kr = _ptr(rp["r"], F64)
+            pv, memv, kv = _ptr(rp["v"], F64)
+            pt, kt = None, None
+            if rp.get("types") is not None:
+                pt, memt, kt = _ptr(rp["types"], I32)
+                mems.add(memt)
+            mems |= {mem, memv}
+            keep += [kr, kv, kt]
+            n = int(np.asarray(rp["r"].shape)[1]) if hasattr(rp["r"], "shape") else len(rp["r"][0])
+            arr[k] = md_replica(n, float(rp["box"]), pr, pv, pt)
+        if len(mems) != 1:
+            raise ValueError("all replica arrays must live in the same memory")
+        h = C.c_void_p()
+        self.stream = _stream_ptr(stream)
+        _check(lib().md_init_replicas(C.byref(params), arr, len(replicas), mems.pop(), self.stream, C.byref(h)))
+        self._h = h
+        self.nrep = len(replicas)
+        self.n = sum(arr[k].n for k in range(self.nrep))
+
+    def replica_observables(self, r):
+        o = md_obs()
+        _check(lib().md_replica_observables(self._h, int(r), C.byref(o)))
+        return dict(step=o.step, U=o.U, K=o.K, T=o.T, sigma=np.array(o.sigma[:]), q=np.array(o.q[:]),
+                    T_mean=o.T_mean, rebuilds=o.rebuilds)
+
+    def replica_scale_velocities(self, lams):
+        lam = np.ascontiguousarray(lams, dtype=np.float64)
+        _check(lib().md_replica_scale_velocities(self._h, lam.ctypes.data_as(C.POINTER(C.c_double))))
+
+    def config(self):
+        c = md_config()
+        _check(lib().md_get_config(self._h, C.byref(c)))
+        return dict(replicas=c.replicas, pair_threads=c.pair_threads, build_warps=c.build_warps,
+                    max_neighbors=c.max_neighbors, atoms=c.atoms, cells=c.cells)
 
     def step(self, nsteps):
         _check(lib().md_step(self._h, int(nsteps)))
@@ -293,7 +352,7 @@ class System:
         h = C.c_void_p()
         _check(lib().md_corr(self._h, int(which), C.byref(h)))
         spec = (self.params.stress, self.params.heatflux, self.params.vacf)[which]
-        ns, ng = (3 * self.n, 3) if which == MD_CORR_VACF else (3, 3)
+        ns, ng = (3 * self.n, 3) if which == MD_CORR_VACF else (3 * self.nrep, 3 * self.nrep)
         return Corr(h, False, ns, ng, False, spec.b, spec.p, keep=self)
 
     def set_timing(self, on=True):

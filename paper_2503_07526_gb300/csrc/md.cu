@@ -21,6 +21,12 @@
 // cell: a block of max_neighbors rows of 32 words, so the list build writes
 // rows that stay together in L2 and the pair kernel reads them coalesced.
 //
+// Replicas.  One handle can hold many independent systems ("replicas", of
+// uneven sizes, densities and temperatures).  Their atoms, cells and
+// reduction CTAs are laid end to end and every kernel covers all of them at
+// once, looking up a replica's box, cell grid and offsets in a small
+// descriptor table; a single system is one replica.
+//
 // A step is a fixed sequence of kernels (no host decision inside it), so it
 // is captured once as a CUDA graph and replayed; the rebuild kernels read a
 // device flag and return at once when no rebuild is due.
@@ -37,29 +43,52 @@ namespace otf {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kPairThreads = 128;
+constexpr int kPairThreads = 128;     // default CTA of the pair kernel (the autotuner may pick 64 or 256)
+constexpr int kMaxPairThreads = 256;
 constexpr int kCellWarps = 4;  // warps (cells) per CTA in the link-cell kernels
 constexpr int kNRed = 11;      // K, U, V*sigma[6], V*q[3]
 constexpr int kMaxRedBlocks = 152 * 4;
 
-struct ObsDev {
+// Step counters shared by all replicas.
+struct StepDev {
   int64_t step;       // steps completed
   int64_t corr_base;  // step at the last correlator reset
-  int64_t Tn;
   int64_t rebuilds;   // neighbour-list / cell rebuilds since md_init
+  unsigned reps_done; // replicas whose reduction finished in this launch
+};
+
+// Observables of one replica.
+struct ObsDev {
+  int64_t Tn;
   double U, K, T;
   double sigma[6];
   double q[3];
   double Tsum;
 };
 
+// Constants of one replica.  Its atoms occupy [atom0, atom1) of the
+// cell-sorted order (the counting sort never moves an atom across replicas,
+// since a replica's cells are contiguous), its cells [cell0, cell0 + nc^3),
+// its reduction CTAs [block0, block0 + nblk).
+struct Rep {
+  int64_t atom0, atom1, cell0, block0;
+  int nc, nblk;
+  double L, edge;
+  float edge_h, edge_l;  // double-float edge (mixed form)
+};
+
 struct Sys {
-  int64_t n, ncell, maxchunks;
-  int nc, ntypes, maxnb, always_rebuild, vacf_u;
-  double L, edge, dt, lim2;
+  int64_t n, ncell, maxchunks;  // totals over all replicas
+  int nrep, ntypes, maxnb, always_rebuild, vacf_u;
+  double dt, lim2;
   double invm[8], mass[8];
   float hdtm_h[8], hdtm_l[8];  // mixed form: dt / (2 m) per type, double-float
-  float dt_h, dt_l, edge_h, edge_l;
+  float dt_h, dt_l;
+  const Rep *rep;            // [nrep]
+  const int *rep_of_atom;    // [n] (sorted order = input order of replicas)
+  const int *rep_of_cell;    // [ncell]
+  const int *rep_of_block;   // [reduction CTAs]
+  const double *lam;         // [nrep] velocity scale factors (md_scale_velocities)
   // cell-sorted state
   double *r, *v;             // FP64 form: absolute positions, velocities [3][n]
   float *offl, *vh, *vl;     // mixed form: offset low words, velocity words [3][n]
@@ -73,9 +102,10 @@ struct Sys {
   uint32_t *nbr;             // [n/32 chunks][maxnb][32]: j | (image code << 27)
   int *nnb;                  // list length per atom
   // reductions and flags
-  double *partials;
-  unsigned *counter;
-  ObsDev *obs;
+  double *partials;          // [reduction CTAs][kNRed]
+  unsigned *counter;         // [nrep] finished CTAs per replica
+  ObsDev *obs;               // [nrep]
+  StepDev *st;
   int *rebuild;
   unsigned *err;
 };
@@ -92,6 +122,7 @@ __device__ __forceinline__ void unpack_cell(int c, int &x, int &y, int &z) {
   z = c >> 20;
 }
 __device__ __forceinline__ int type_of(const Sys &d, int64_t i) { return min(max(d.type[i], 0), 7); }
+__device__ __forceinline__ const Rep &rep_of(const Sys &d, int64_t i) { return d.rep[d.rep_of_atom[i]]; }
 
 // ------------------------------------------------------------ integrate
 
@@ -117,9 +148,10 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift64(Sys d, double hdt) {
     }
     int cx, cy, cz;
     unpack_cell(d.cpk[i], cx, cy, cz);
-    const double px = fma(-(cx + 0.5), d.edge, x[0]);
-    const double py = fma(-(cy + 0.5), d.edge, x[1]);
-    const double pz = fma(-(cz + 0.5), d.edge, x[2]);
+    const double edge = rep_of(d, i).edge;
+    const double px = fma(-(cx + 0.5), edge, x[0]);
+    const double py = fma(-(cy + 0.5), edge, x[1]);
+    const double pz = fma(-(cz + 0.5), edge, x[2]);
     Vec4<double>::store(rel + i, px, py, pz);
     const dvec4 b = Vec4<double>::load(relb + i);
     const double dx = px - b.x, dy = py - b.y, dz = pz - b.z;
@@ -196,17 +228,18 @@ __device__ __forceinline__ void bin_atom(const Sys &d, int64_t i, int c) {
 __global__ void __launch_bounds__(kThreads) k_rb_assign64(Sys d) {
   if (!*d.rebuild) return;
   const int64_t n = d.n;
-  const int nc = d.nc;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    const Rep &R = rep_of(d, i);
+    const int nc = R.nc;
     int ci[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       double x = d.r[a * n + i];
-      x -= d.L * floor(x / d.L);
-      if (x >= d.L) x -= d.L;
+      x -= R.L * floor(x / R.L);
+      if (x >= R.L) x -= R.L;
       if (x < 0.0) x = 0.0;
-      const int c = (int)(x / d.edge);
+      const int c = (int)(x / R.edge);
       ci[a] = c < nc ? c : nc - 1;
       d.rB[a * n + i] = x;
       d.vB[a * n + i] = d.v[a * n + i];
@@ -215,7 +248,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_assign64(Sys d) {
     if (t < 0 || t >= d.ntypes) atomicOr(d.err, ERR_BAD_TYPE);
     d.idB[i] = d.id[i];
     d.typeB[i] = t;
-    bin_atom(d, i, (ci[2] * nc + ci[1]) * nc + ci[0]);
+    bin_atom(d, i, (int)R.cell0 + (ci[2] * nc + ci[1]) * nc + ci[0]);
   }
 }
 
@@ -226,13 +259,14 @@ __global__ void __launch_bounds__(kThreads) k_rb_assign64(Sys d) {
 __global__ void __launch_bounds__(kThreads) k_rb_assign_df(Sys d) {
   if (!*d.rebuild) return;
   const int64_t n = d.n;
-  const int nc = d.nc;
   const float4 *rel = static_cast<const float4 *>(d.rel);
-  const dfloat edge{d.edge_h, d.edge_l};
   float *oB = reinterpret_cast<float *>(d.rB);
   float *wB = reinterpret_cast<float *>(d.vB);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    const Rep &R = rep_of(d, i);
+    const int nc = R.nc;
+    const dfloat edge{R.edge_h, R.edge_l};
     const float4 o = rel[i];
     const float oh[3] = {o.x, o.y, o.z};
     int cc[3];
@@ -241,7 +275,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_assign_df(Sys d) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       dfloat x{oh[a], d.offl[a * n + i]};
-      int k = (int)rintf(x.h / d.edge_h);  // NaN converts to 0
+      int k = (int)rintf(x.h / R.edge_h);  // NaN converts to 0
       k = max(-nc, min(nc, k));
       if (k != 0) x = df_add(x, df_mul_f(edge, (float)(-k)));
       int c = (cc[a] + k) % nc;
@@ -256,7 +290,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_assign_df(Sys d) {
     if (t < 0 || t >= d.ntypes) atomicOr(d.err, ERR_BAD_TYPE);
     d.idB[i] = d.id[i];
     d.typeB[i] = t;
-    bin_atom(d, i, (ci[2] * nc + ci[1]) * nc + ci[0]);
+    bin_atom(d, i, (int)R.cell0 + (ci[2] * nc + ci[1]) * nc + ci[0]);
   }
 }
 
@@ -302,7 +336,7 @@ __global__ void __launch_bounds__(1024) k_rb_scan(Sys d) {
   }
   if (threadIdx.x == 0) {
     d.cellstart[nc3] = (int)d.n;
-    d.obs->rebuilds += 1;
+    d.st->rebuilds += 1;
   }
 }
 
@@ -325,7 +359,9 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_rb_rank(Sys d) {
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t c = wglobal; c < d.ncell; c += nwarps) {
     const int s0 = d.cellstart[c], cnt = d.cellstart[c + 1] - s0;
-    const int cx = (int)(c % d.nc), cy = (int)((c / d.nc) % d.nc), cz = (int)(c / ((int64_t)d.nc * d.nc));
+    const Rep &R = d.rep[d.rep_of_cell[c]];
+    const int64_t lc = c - R.cell0;
+    const int cx = (int)(lc % R.nc), cy = (int)((lc / R.nc) % R.nc), cz = (int)(lc / ((int64_t)R.nc * R.nc));
     for (int e0 = 0; e0 < cnt; e0 += 32) {
       const int e = e0 + lane;
       const int a = e < cnt ? d.perm[s0 + e] : 0;
@@ -348,9 +384,9 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_rb_rank(Sys d) {
             d.r[q * n + dst] = x[q];
             d.v[q * n + dst] = d.vB[q * n + a];
           }
-          const double px = fma(-(cx + 0.5), d.edge, x[0]);
-          const double py = fma(-(cy + 0.5), d.edge, x[1]);
-          const double pz = fma(-(cz + 0.5), d.edge, x[2]);
+          const double px = fma(-(cx + 0.5), R.edge, x[0]);
+          const double py = fma(-(cy + 0.5), R.edge, x[1]);
+          const double pz = fma(-(cz + 0.5), R.edge, x[2]);
           Vec4<double>::store(static_cast<dvec4 *>(d.rel) + dst, px, py, pz);
           Vec4<double>::store(static_cast<dvec4 *>(d.relb) + dst, px, py, pz);
         } else {
@@ -429,11 +465,13 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
   __shared__ V4 spos[kCellWarps][32];
   __shared__ int sidx[kCellWarps][32];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  const int nc = d.nc;
   const V4 *rel = static_cast<const V4 *>(d.rel);
-  const TF edge = (TF)d.edge;
   for (int64_t c = blockIdx.x * (int64_t)kCellWarps + wl; c < d.ncell; c += (int64_t)gridDim.x * kCellWarps) {
-    const int cx = (int)(c % nc), cy = (int)((c / nc) % nc), cz = (int)(c / ((int64_t)nc * nc));
+    const Rep &R = d.rep[d.rep_of_cell[c]];
+    const int nc = R.nc;
+    const TF edge = (TF)R.edge;
+    const int64_t lc = c - R.cell0;
+    const int cx = (int)(lc % nc), cy = (int)((lc / nc) % nc), cz = (int)(lc / ((int64_t)nc * nc));
     const int i0 = d.cellstart[c], i1 = d.cellstart[c + 1];
     for (int ib = i0; ib < i1; ib += 32) {
       const int i = ib + lane;
@@ -445,7 +483,7 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
         int ox, oy, oz;
         image_offset(code, ox, oy, oz);
         const int jx = (cx + ox + nc) % nc, jy = (cy + oy + nc) % nc, jz = (cz + oz + nc) % nc;
-        const int64_t cj = ((int64_t)jz * nc + jy) * nc + jx;
+        const int64_t cj = R.cell0 + ((int64_t)jz * nc + jy) * nc + jx;
         const int j0 = d.cellstart[cj], j1 = d.cellstart[cj + 1];
         const TF offx = ox * edge, offy = oy * edge, offz = oz * edge;
         for (int jb = j0; jb < j1; jb += 32) {
@@ -492,19 +530,17 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
 // frame and, for each i of the segment, test all 32 at once; a ballot and a
 // population count give every accepted j its list slot.  Entries are
 // j | (image code << 27).
-template <typename TF>
-__global__ void __launch_bounds__(kCellWarps * 32) k_build(Sys d, LJ<TF> lj) {
+template <typename TF, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_build(Sys d, LJ<TF> lj) {
   using V4 = typename Vec4<TF>::type;
   if (!*d.rebuild) return;
-  __shared__ V4 spi[kCellWarps][32];
+  __shared__ V4 spi[WARPS][32];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  const int nc = d.nc;
   const int64_t n = d.n;
   const V4 *rel = static_cast<const V4 *>(d.rel);
-  const TF edge = (TF)d.edge;
   const unsigned below = (1u << lane) - 1u;
   const int64_t nchunks = (n + 31) / 32;
-  for (int64_t q = blockIdx.x * (int64_t)kCellWarps + wl; q < nchunks; q += (int64_t)gridDim.x * kCellWarps) {
+  for (int64_t q = blockIdx.x * (int64_t)WARPS + wl; q < nchunks; q += (int64_t)gridDim.x * WARPS) {
     const int a0 = (int)(q * 32), a1 = (int)min((int64_t)a0 + 32, n);
     __syncwarp();
     if (a0 + lane < a1) spi[wl][lane] = Vec4<TF>::load(rel + a0 + lane);
@@ -513,13 +549,17 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_build(Sys d, LJ<TF> lj) {
     int cnt = 0;  // lane l: list length of atom a0 + l
     int s = a0;
     while (s < a1) {
+      // the segment: atoms of s's cell within the chunk (one replica)
+      const Rep &R = rep_of(d, s);
+      const int nc = R.nc;
+      const TF edge = (TF)R.edge;
       int cx, cy, cz;
       unpack_cell(d.cpk[s], cx, cy, cz);
-      const int e = min(d.cellstart[(cz * nc + cy) * nc + cx + 1], a1);
+      const int e = min(d.cellstart[R.cell0 + (cz * nc + cy) * nc + cx + 1], a1);
       for (int row = 0; row < 9; ++row) {
         const int oy = row % 3 - 1, oz = row / 3 - 1;
         const int jy = (cy + oy + nc) % nc, jz = (cz + oz + nc) % nc;
-        const int64_t rb = ((int64_t)jz * nc + jy) * nc;
+        const int64_t rb = R.cell0 + ((int64_t)jz * nc + jy) * nc;
         const bool contig = cx >= 1 && cx <= nc - 2;
         for (int piece = 0; piece < (contig ? 1 : 3); ++piece) {
           int ra, rbnd, b1, b2;
@@ -597,21 +637,29 @@ __device__ __forceinline__ void pair_from_entry(const LJ<TF> &lj, const typename
   if (r2 < lj.rc2) lj_accumulate<TF>(lj, dx, dy, dz, r2, f, e, w);
 }
 
+// A CTA spans at most two replicas (replicas hold at least kMaxPairThreads
+// atoms), so it keeps the image offsets of both in shared memory.
 template <typename TF>
-__global__ void __launch_bounds__(kPairThreads) k_pair_list(Sys d, LJ<TF> lj) {
+__global__ void __launch_bounds__(kMaxPairThreads) k_pair_list(Sys d, LJ<TF> lj) {
   using V4 = typename Vec4<TF>::type;
-  __shared__ V4 off[27];  // image offsets, one vector load per pair
-  if (threadIdx.x < 27) {
+  __shared__ V4 offs[2][27];  // image offsets, one vector load per pair
+  const int64_t blk0 = blockIdx.x * (int64_t)blockDim.x;
+  const int r0 = d.rep_of_atom[blk0];
+  const int r1 = d.rep_of_atom[min(blk0 + blockDim.x, d.n) - 1];
+  if (threadIdx.x < 54) {
+    const int which = threadIdx.x / 27, code = threadIdx.x % 27;
+    const TF edge = (TF)d.rep[which ? r1 : r0].edge;
     int ox, oy, oz;
-    image_offset(threadIdx.x, ox, oy, oz);
-    off[threadIdx.x].x = ox * (TF)d.edge;
-    off[threadIdx.x].y = oy * (TF)d.edge;
-    off[threadIdx.x].z = oz * (TF)d.edge;
-    off[threadIdx.x].w = TF(0);
+    image_offset(code, ox, oy, oz);
+    offs[which][code].x = ox * edge;
+    offs[which][code].y = oy * edge;
+    offs[which][code].z = oz * edge;
+    offs[which][code].w = TF(0);
   }
   __syncthreads();
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i = blk0 + threadIdx.x;
   if (i >= d.n) return;
+  const V4 *off = offs[d.rep_of_atom[i] == r0 ? 0 : 1];
   const V4 *rel = static_cast<const V4 *>(d.rel);
   const V4 pi = Vec4<TF>::load(rel + i);
   TF f[3] = {0, 0, 0}, e = 0, w[6] = {0, 0, 0, 0, 0, 0};
@@ -638,14 +686,17 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_list(Sys d, LJ<TF> lj) {
 
 // ---------------------------------------------------- reduce and sample
 
-// Second half kick, then the per-step system observables (Sec. 2.3):
-// K, U, V sigma_ab = sum m v_a v_b + sum W_i,ab, V q = sum (E_i v_i + W_i v_i).
-// Per-thread partial sums in A (float in the mixed form, from the FP32 high
-// words of the velocities; double in FP64), the CTA and grid tree in FP64
-// (fixed order: deterministic).  The last CTA to finish writes the
-// observables, advances the step counter and takes the stress and
-// heat-flux correlator samples (Algorithm 1).  When a velocity sample is
-// due, velocities are also scattered to atom-id order.
+// Second half kick, then the per-step observables of every replica
+// (Sec. 2.3): K, U, V sigma_ab = sum m v_a v_b + sum W_i,ab,
+// V q = sum (E_i v_i + W_i v_i).  Each CTA works on one replica (rep_of_block)
+// and strides over that replica's atoms.  Per-thread partial sums in A
+// (float in the mixed form, from the FP32 high words of the velocities;
+// double in FP64), the CTA and replica tree in FP64 (fixed order:
+// deterministic).  The last CTA of a replica writes its observables and
+// takes its stress and heat-flux correlator samples (Algorithm 1; series
+// 3r..3r+2 of the two correlators); the last replica to finish advances the
+// step counter.  When a velocity sample is due, velocities are also
+// scattered to atom-id order.
 template <typename TF, typename A, bool KICK>
 __global__ void __launch_bounds__(kThreads)
     k_kick_reduce(Sys d, double hdt, CorrDev cs, int64_t us, CorrDev ch, int64_t uh) {
@@ -657,14 +708,17 @@ __global__ void __launch_bounds__(kThreads)
   const TF *Wp = static_cast<const TF *>(d.W);
   TF *vb = static_cast<TF *>(d.vbuf);
   const int64_t n = d.n;
-  const ObsDev *o = d.obs;
-  const int64_t step_now = o->step + (KICK ? 1 : 0);
-  const bool vacf_due = KICK && d.vacf_u > 0 && ((step_now - o->corr_base) % d.vacf_u == 0);
+  const StepDev *st = d.st;
+  const int64_t step_now = st->step + (KICK ? 1 : 0);
+  const bool vacf_due = KICK && d.vacf_u > 0 && ((step_now - st->corr_base) % d.vacf_u == 0);
+  const int r = d.rep_of_block[blockIdx.x];
+  const Rep &R = d.rep[r];
+  const int lb = (int)(blockIdx.x - R.block0);
   A acc[kNRed];
 #pragma unroll
   for (int q = 0; q < kNRed; ++q) acc[q] = A(0);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = R.atom0 + (int64_t)lb * blockDim.x + threadIdx.x; i < R.atom1;
+       i += (int64_t)R.nblk * blockDim.x) {
     const int t = type_of(d, i);
     A v[3];
     if constexpr (std::is_same<TF, double>::value) {
@@ -718,67 +772,76 @@ __global__ void __launch_bounds__(kThreads)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < kNRed; ++q) {
-    const A s = warp_sum(acc[q]);
-    if (lane == 0) red[warp][q] = (double)s;
+    const A sm = warp_sum(acc[q]);
+    if (lane == 0) red[warp][q] = (double)sm;
   }
   __syncthreads();
   if (threadIdx.x < kNRed) {
-    double s = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) s += red[w][threadIdx.x];
-    d.partials[blockIdx.x * kNRed + threadIdx.x] = s;
+    double sm = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) sm += red[w][threadIdx.x];
+    d.partials[blockIdx.x * kNRed + threadIdx.x] = sm;
   }
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(d.counter, 1u) == gridDim.x - 1);
+  if (threadIdx.x == 0) last = (atomicAdd(d.counter + r, 1u) == (unsigned)R.nblk - 1);
   __syncthreads();
   if (!last) return;
   __threadfence();
   for (int q = warp; q < kNRed; q += kThreads / 32) {
-    double s = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(d.partials + b * kNRed + q);
-    s = warp_sum(s);
-    if (lane == 0) tot[q] = s;
+    double sm = 0.0;
+    for (int b = lane; b < R.nblk; b += 32) sm += __ldcg(d.partials + (R.block0 + b) * kNRed + q);
+    sm = warp_sum(sm);
+    if (lane == 0) tot[q] = sm;
   }
   __syncthreads();
+  const int64_t nr = R.atom1 - R.atom0;
+  const double V = R.L * R.L * R.L;
   if (threadIdx.x == 0) {
-    ObsDev *ow = d.obs;
-    const double V = d.L * d.L * d.L;
+    ObsDev *ow = d.obs + r;
     ow->K = tot[0];
     ow->U = tot[1];
-    ow->T = n > 1 ? 2.0 * tot[0] / (3.0 * (double)n - 3.0) : 0.0;
+    ow->T = nr > 1 ? 2.0 * tot[0] / (3.0 * (double)nr - 3.0) : 0.0;
     for (int a = 0; a < 6; ++a) ow->sigma[a] = tot[2 + a] / V;
     for (int a = 0; a < 3; ++a) ow->q[a] = tot[8 + a] / V;
     if (KICK) {
-      ow->step = step_now;
       ow->Tsum += ow->T;
       ow->Tn += 1;
     }
-    *d.counter = 0u;
-    *d.rebuild = 0;
+    d.counter[r] = 0u;
   }
-  if (!KICK) return;
-  __syncthreads();
-  const int64_t tc = step_now - o->corr_base;
-  const int tid = threadIdx.x;
-  const double V = d.L * d.L * d.L;
-  if (tid < 3 && us > 0 && cs.b > 0 && tc % us == 0) {
-    const double x = tot[5 + tid] / V;  // sigma_xy, sigma_xz, sigma_yz
-    push_one_series<double>(cs, tid, x, x, tc / us);
-  } else if (tid >= 3 && tid < 6 && uh > 0 && ch.b > 0 && tc % uh == 0) {
-    const double x = tot[8 + tid - 3] / V;  // q_x, q_y, q_z
-    push_one_series<double>(ch, tid - 3, x, x, tc / uh);
+  if (KICK) {
+    const int64_t tc = step_now - st->corr_base;
+    const int tid = threadIdx.x;
+    if (tid < 3 && us > 0 && cs.b > 0 && tc % us == 0) {
+      const double x = tot[5 + tid] / V;  // sigma_xy, sigma_xz, sigma_yz
+      push_one_series<double>(cs, 3 * r + tid, x, x, tc / us);
+    } else if (tid >= 3 && tid < 6 && uh > 0 && ch.b > 0 && tc % uh == 0) {
+      const double x = tot[8 + tid - 3] / V;  // q_x, q_y, q_z
+      push_one_series<double>(ch, 3 * r + tid - 3, x, x, tc / uh);
+    }
+  }
+  // the last replica to finish closes the step
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&d.st->reps_done, 1u) == (unsigned)d.nrep - 1) {
+      d.st->reps_done = 0u;
+      if (KICK) d.st->step = step_now;
+      *d.rebuild = 0;
+    }
   }
 }
 
+// Multiplies velocities by their replica's factor lam[r].
 template <typename TF>
-__global__ void k_scale_v(Sys d, double lam) {
-  const dfloat l = df_from_double(lam);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * d.n;
+__global__ void k_scale_v(Sys d) {
+  const int64_t n = d.n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    const double lam = d.lam[d.rep_of_atom[i % n]];
     if constexpr (std::is_same<TF, double>::value) {
       d.v[i] *= lam;
     } else {
-      const dfloat v = df_mul(dfloat{d.vh[i], d.vl[i]}, l);
+      const dfloat v = df_mul(dfloat{d.vh[i], d.vl[i]}, df_from_double(lam));
       d.vh[i] = v.h;
       d.vl[i] = v.l;
     }
@@ -796,21 +859,22 @@ __global__ void k_iota(int *id, int64_t n) {
 // cell centre and double-float velocities.  FP64 arithmetic, once.
 __global__ void k_init_df(Sys d) {
   const int64_t n = d.n;
-  const int nc = d.nc;
   float4 *rel = static_cast<float4 *>(d.rel);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    const Rep &R = rep_of(d, i);
+    const int nc = R.nc;
     int ci[3];
     float oh[3];
     for (int a = 0; a < 3; ++a) {
       double x = d.rB[a * n + i];
-      x -= d.L * floor(x / d.L);
-      if (x >= d.L) x -= d.L;
+      x -= R.L * floor(x / R.L);
+      if (x >= R.L) x -= R.L;
       if (x < 0.0) x = 0.0;
-      int c = (int)(x / d.edge);
+      int c = (int)(x / R.edge);
       c = c < nc ? c : nc - 1;
       ci[a] = c;
-      const dfloat off = df_from_double(x - (c + 0.5) * d.edge);
+      const dfloat off = df_from_double(x - (c + 0.5) * R.edge);
       oh[a] = off.h;
       d.offl[a * n + i] = off.l;
       const dfloat v = df_from_double(d.vB[a * n + i]);
@@ -822,7 +886,8 @@ __global__ void k_init_df(Sys d) {
   }
 }
 
-// Per-particle outputs back in atom-id order (FP64), positions wrapped.
+// Per-particle outputs back in atom-id order (FP64), positions wrapped into
+// their replica's box.
 template <typename TF>
 __global__ void k_unsort(Sys d, double *r, double *v, double *F, double *epot, double *W) {
   const int64_t n = d.n;
@@ -831,6 +896,7 @@ __global__ void k_unsort(Sys d, double *r, double *v, double *F, double *epot, d
   const TF *Ws = static_cast<const TF *>(d.W);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    const Rep &R = rep_of(d, i);
     const int64_t id = d.id[i];
     int cc[3];
     unpack_cell(d.cpk[i], cc[0], cc[1], cc[2]);
@@ -842,10 +908,10 @@ __global__ void k_unsort(Sys d, double *r, double *v, double *F, double *epot, d
         } else {
           const float4 o = static_cast<const float4 *>(d.rel)[i];
           const float oh = a == 0 ? o.x : (a == 1 ? o.y : o.z);
-          x = (cc[a] + 0.5) * d.edge + df_to_double(dfloat{oh, d.offl[a * n + i]});
+          x = (cc[a] + 0.5) * R.edge + df_to_double(dfloat{oh, d.offl[a * n + i]});
         }
-        x -= d.L * floor(x / d.L);
-        if (x >= d.L) x -= d.L;
+        x -= R.L * floor(x / R.L);
+        if (x >= R.L) x -= R.L;
         r[a * n + id] = x;
       }
       if (v) {
@@ -874,14 +940,23 @@ struct md_handle_s {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   bool fp64 = true;
-  int red_blocks = 1;
+  int nrep = 1;
+  int red_blocks = 1;                // reduction CTAs over all replicas
+  int pair_threads = kPairThreads;   // launch shapes (autotuned when asked)
+  int build_warps = kCellWarps;
+  std::vector<Rep> reps;             // host copy of the descriptor table
+  Rep *d_rep = nullptr;
+  int *d_rep_of_atom = nullptr, *d_rep_of_cell = nullptr, *d_rep_of_block = nullptr;
+  double *d_lam = nullptr;
   int64_t steps_done = 0;
   int64_t corr_base = 0;
   corr_handle banks[3];  // system-owned correlators (borrowed by md_corr)
   bool bank_on[3] = {false, false, false};
   double *d_out = nullptr;  // unsort staging [16][n]
-  ObsDev *h_obs = nullptr;  // pinned
+  ObsDev *h_obs = nullptr;  // pinned [nrep]
+  StepDev *h_st = nullptr;  // pinned
   unsigned *h_err = nullptr;
+  double *h_lam = nullptr;  // pinned [nrep]
   // timing
   bool timing = false;
   std::vector<cudaEvent_t> ev;
@@ -933,6 +1008,23 @@ struct KTimer {
 };
 
 template <typename TF>
+void launch_build(const md_handle *h, cudaStream_t s) {
+  const Sys &d = h->d;
+  const int64_t chunks = (d.n + 31) / 32;
+  const LJ<TF> lj = lj_of<TF>(h->prm);
+  switch (h->build_warps) {
+    case 2:
+      k_build<TF, 2><<<std::min(ceil_div(chunks, 2), 152 * 16), 64, 0, s>>>(d, lj);
+      break;
+    case 8:
+      k_build<TF, 8><<<std::min(ceil_div(chunks, 8), 152 * 8), 256, 0, s>>>(d, lj);
+      break;
+    default:
+      k_build<TF, 4><<<std::min(ceil_div(chunks, 4), 152 * 16), 128, 0, s>>>(d, lj);
+  }
+}
+
+template <typename TF>
 int launch_rebuild(md_handle *h, cudaStream_t s) {
   const Sys &d = h->d;
   KTimer tm(h, s, MD_K_REBUILD);
@@ -944,9 +1036,7 @@ int launch_rebuild(md_handle *h, cudaStream_t s) {
   k_rb_scan<<<1, 1024, 0, s>>>(d);
   k_rb_place<<<grid_for(d.n, kThreads), kThreads, 0, s>>>(d);
   k_rb_rank<TF><<<grid_for(d.ncell * 32, kCellWarps * 32), kCellWarps * 32, 0, s>>>(d);
-  if (h->prm.pair_mode == MD_PAIR_VERLET)
-    k_build<TF><<<std::min(ceil_div(d.ncell, kCellWarps), 152 * 16), kCellWarps * 32, 0, s>>>(
-        d, lj_of<TF>(h->prm));
+  if (h->prm.pair_mode == MD_PAIR_VERLET) launch_build<TF>(h, s);
   OTF_LAUNCH_CHECK();
   return MD_OK;
 }
@@ -956,7 +1046,7 @@ int launch_pair(md_handle *h, cudaStream_t s) {
   const Sys &d = h->d;
   KTimer tm(h, s, MD_K_PAIR);
   if (h->prm.pair_mode == MD_PAIR_VERLET)
-    k_pair_list<TF><<<ceil_div(d.n, kPairThreads), kPairThreads, 0, s>>>(d, lj_of<TF>(h->prm));
+    k_pair_list<TF><<<ceil_div(d.n, h->pair_threads), h->pair_threads, 0, s>>>(d, lj_of<TF>(h->prm));
   else
     k_cells<TF><<<std::min(ceil_div(d.ncell, kCellWarps), 152 * 16), kCellWarps * 32, 0, s>>>(
         d, lj_of<TF>(h->prm));
@@ -993,7 +1083,7 @@ int launch_step(md_handle *h, cudaStream_t s) {
   if ((rc = launch_reduce<TF, A, true>(h, s))) return rc;
   if (h->bank_on[2]) {
     KTimer tm(h, s, MD_K_VACF);
-    const PushIdx pi{&h->d.obs->step, &h->d.obs->corr_base, h->prm.vacf.u, 0};
+    const PushIdx pi{&h->d.st->step, &h->d.st->corr_base, h->prm.vacf.u, 0};
     if ((rc = h->banks[2].c.launch_push(h->d.vbuf, h->d.vbuf, !h->fp64, pi, s))) return rc;
   }
   return MD_OK;
@@ -1044,18 +1134,13 @@ int build_graph(md_handle *h) {
   return MD_OK;
 }
 
-int validate(const md_params *p, const md_system *s) {
-  if (!p || !s) {
-    set_error("md_init: null argument");
+int validate_params(const md_params *p) {
+  if (!p) {
+    set_error("md_init: null parameters");
     return MD_EINVAL;
   }
-  if (p->n < 2 || p->n >= (1 << 27)) {
-    set_error("md_init: n must be in [2, 2^27)");
-    return MD_EINVAL;
-  }
-  if (!(p->box > 0) || !(p->rc > 0) || !(p->sigma > 0) || !(p->dt > 0) || p->skin < 0 ||
-      !std::isfinite(p->eps)) {
-    set_error("md_init: box, rc, sigma, dt must be positive and skin >= 0");
+  if (!(p->rc > 0) || !(p->sigma > 0) || !(p->dt > 0) || p->skin < 0 || !std::isfinite(p->eps)) {
+    set_error("md_init: rc, sigma, dt must be positive and skin >= 0");
     return MD_EINVAL;
   }
   if (p->ntypes < 1 || p->ntypes > 8) {
@@ -1075,16 +1160,6 @@ int validate(const md_params *p, const md_system *s) {
     set_error("md_init: unknown pair_mode");
     return MD_EINVAL;
   }
-  const double rl = p->rc + (p->pair_mode == MD_PAIR_VERLET ? p->skin : 0.0);
-  const int nc = (int)std::floor(p->box / rl);
-  if (nc < 3) {
-    set_error("md_init: box %.6g holds fewer than 3 cells of edge rc + skin = %.6g", p->box, rl);
-    return MD_EINVAL;
-  }
-  if (nc > 1023) {
-    set_error("md_init: more than 1023 cells per side");
-    return MD_EINVAL;
-  }
   const corr_spec *cs[3] = {&p->stress, &p->heatflux, &p->vacf};
   for (int k = 0; k < 3; ++k) {
     if (cs[k]->u < 0) {
@@ -1095,22 +1170,63 @@ int validate(const md_params *p, const md_system *s) {
     corr_params cp{cs[k]->b, cs[k]->p, cs[k]->m, 0, 3, 1, MD_PREC_FP64, 1.0};
     if (validate_corr_params(cp)) return MD_EINVAL;
   }
-  if (!s->r || !s->v || (s->mem != MD_MEM_HOST && s->mem != MD_MEM_DEVICE)) {
-    set_error("md_init: system needs r, v and a valid mem flag");
+  return MD_OK;
+}
+
+int validate_replicas(const md_params *p, const md_replica *reps, int count, int mem) {
+  if (!reps || count < 1) {
+    set_error("md_init: at least one replica is needed");
     return MD_EINVAL;
   }
-  if (s->mem == MD_MEM_HOST) {
-    for (int64_t i = 0; i < 3 * p->n; ++i)
-      if (!std::isfinite(s->r[i]) || !std::isfinite(s->v[i])) {
-        set_error("md_init: non-finite position or velocity at %lld", (long long)i);
-        return MD_ESTATE;
-      }
-    if (s->type)
-      for (int64_t i = 0; i < p->n; ++i)
-        if (s->type[i] < 0 || s->type[i] >= p->ntypes) {
-          set_error("md_init: atom %lld has type %d outside [0, %d)", (long long)i, s->type[i], p->ntypes);
-          return MD_EINVAL;
+  if (mem != MD_MEM_HOST && mem != MD_MEM_DEVICE) {
+    set_error("md_init: mem must be MD_MEM_HOST or MD_MEM_DEVICE");
+    return MD_EINVAL;
+  }
+  if (count > 1 && p->vacf.u > 0) {
+    set_error("md_init: the per-atom velocity correlator is for a single system (set vacf.u = 0)");
+    return MD_EINVAL;
+  }
+  const double rl = p->rc + (p->pair_mode == MD_PAIR_VERLET ? p->skin : 0.0);
+  int64_t total = 0;
+  for (int k = 0; k < count; ++k) {
+    const md_replica &R = reps[k];
+    if (R.n < 2 || (count > 1 && R.n < kMaxPairThreads)) {
+      set_error("md_init: replica %d has %lld atoms (at least %d per replica when there are several)", k,
+                (long long)R.n, count > 1 ? kMaxPairThreads : 2);
+      return MD_EINVAL;
+    }
+    if (!(R.box > 0) || !R.r || !R.v) {
+      set_error("md_init: replica %d needs a positive box and r, v arrays", k);
+      return MD_EINVAL;
+    }
+    const int nc = (int)std::floor(R.box / rl);
+    if (nc < 3) {
+      set_error("md_init: replica %d: box %.6g holds fewer than 3 cells of edge rc + skin = %.6g", k, R.box, rl);
+      return MD_EINVAL;
+    }
+    if (nc > 1023) {
+      set_error("md_init: replica %d has more than 1023 cells per side", k);
+      return MD_EINVAL;
+    }
+    total += R.n;
+    if (mem == MD_MEM_HOST) {
+      for (int64_t i = 0; i < 3 * R.n; ++i)
+        if (!std::isfinite(R.r[i]) || !std::isfinite(R.v[i])) {
+          set_error("md_init: replica %d: non-finite position or velocity at %lld", k, (long long)i);
+          return MD_ESTATE;
         }
+      if (R.type)
+        for (int64_t i = 0; i < R.n; ++i)
+          if (R.type[i] < 0 || R.type[i] >= p->ntypes) {
+            set_error("md_init: replica %d: atom %lld has type %d outside [0, %d)", k, (long long)i, R.type[i],
+                      p->ntypes);
+            return MD_EINVAL;
+          }
+    }
+  }
+  if (total >= (int64_t(1) << 27)) {
+    set_error("md_init: %lld atoms in total; at most 2^27 - 1", (long long)total);
+    return MD_EINVAL;
   }
   return MD_OK;
 }
@@ -1123,29 +1239,108 @@ void release(md_handle *h) {
   Sys &d = h->d;
   void *ptrs[] = {d.r, d.v, d.offl, d.vh, d.vl, d.F, d.epot, d.W, d.rel, d.relb, d.vbuf, d.id, d.type,
                   d.cpk, d.rB, d.vB, d.idB, d.typeB, d.cellB, d.slot, d.perm, d.cellcount, d.cellstart,
-                  d.nbr, d.nnb, d.partials, d.counter, d.obs, d.rebuild, d.err,
-                  h->d_out};
+                  d.nbr, d.nnb, d.partials, d.counter, d.obs, d.st, d.rebuild, d.err, h->d_out, h->d_rep,
+                  h->d_rep_of_atom, h->d_rep_of_cell, h->d_rep_of_block, h->d_lam};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (int k = 0; k < 3; ++k)
     if (h->bank_on[k]) h->banks[k].c.destroy();
   if (h->h_obs) cudaFreeHost(h->h_obs);
+  if (h->h_st) cudaFreeHost(h->h_st);
   if (h->h_err) cudaFreeHost(h->h_err);
+  if (h->h_lam) cudaFreeHost(h->h_lam);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   delete h;
 }
 
-int init_impl(md_handle *h, const md_params *p, const md_system *s) {
+// Device time of `reps` runs of fn on the handle's stream (ms per run).
+template <typename Fn>
+float time_runs(md_handle *h, int reps, Fn fn) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  fn();  // warm
+  cudaEventRecord(a, h->stream);
+  for (int k = 0; k < reps; ++k) fn();
+  cudaEventRecord(b, h->stream);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms / reps;
+}
+
+// Autotuner: times the pair kernel at 64 / 128 / 256 threads per CTA and
+// the list build at 2 / 4 / 8 warps per CTA on the system itself (forces
+// and lists are recomputed from the unchanged state, so the trajectory is
+// not touched) and keeps the fastest of each.
+template <typename TF>
+int autotune(md_handle *h) {
+  if (h->prm.pair_mode != MD_PAIR_VERLET) return MD_OK;
+  const int one = 1;
+  float best = 1e30f;
+  int best_t = h->pair_threads;
+  for (int t : {64, 128, 256}) {
+    h->pair_threads = t;
+    const float ms = time_runs(h, 5, [&] { launch_pair<TF>(h, h->stream); });
+    if (ms < best) best = ms, best_t = t;
+  }
+  h->pair_threads = best_t;
+  best = 1e30f;
+  int best_w = h->build_warps;
+  for (int w : {2, 4, 8}) {
+    h->build_warps = w;
+    const float ms = time_runs(h, 3, [&] {
+      cudaMemcpyAsync(h->d.rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream);
+      launch_build<TF>(h, h->stream);
+    });
+    if (ms < best) best = ms, best_w = w;
+  }
+  h->build_warps = best_w;
+  OTF_CUDA(cudaMemsetAsync(h->d.rebuild, 0, sizeof(int), h->stream));
+  // rebuild the lists once more with the chosen shape, then the forces
+  OTF_CUDA(cudaMemcpyAsync(h->d.rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  launch_build<TF>(h, h->stream);
+  OTF_LAUNCH_CHECK();
+  if (int rc = launch_pair<TF>(h, h->stream)) return rc;
+  OTF_CUDA(cudaMemsetAsync(h->d.rebuild, 0, sizeof(int), h->stream));
+  OTF_CUDA(cudaStreamSynchronize(h->stream));
+  return MD_OK;
+}
+
+int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int count, int mem) {
   h->prm = *p;
   h->fp64 = p->precision == MD_PREC_FP64;
+  h->nrep = count;
   Sys &d = h->d;
-  const int64_t n = p->n;
   const double rl = p->rc + (p->pair_mode == MD_PAIR_VERLET ? p->skin : 0.0);
+  // replica table: atoms, cells and reduction CTAs laid end to end
+  h->reps.resize(count);
+  int64_t n = 0, ncell = 0, blocks = 0;
+  double rho_max = 0.0;
+  for (int k = 0; k < count; ++k) {
+    Rep &R = h->reps[k];
+    R.nc = (int)std::floor(reps[k].box / rl);
+    R.L = reps[k].box;
+    R.edge = R.L / R.nc;
+    const dfloat ef = df_from_double(R.edge);
+    R.edge_h = ef.h;
+    R.edge_l = ef.l;
+    R.atom0 = n;
+    R.atom1 = n + reps[k].n;
+    R.cell0 = ncell;
+    R.block0 = blocks;
+    R.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxRedBlocks, (reps[k].n + 4095) / 4096));
+    n += reps[k].n;
+    ncell += (int64_t)R.nc * R.nc * R.nc;
+    blocks += R.nblk;
+    rho_max = std::max(rho_max, reps[k].n / (R.L * R.L * R.L));
+  }
   d.n = n;
-  d.nc = (int)std::floor(p->box / rl);
-  d.ncell = (int64_t)d.nc * d.nc * d.nc;
-  d.L = p->box;
-  d.edge = p->box / d.nc;
+  d.ncell = ncell;
+  d.nrep = count;
+  h->red_blocks = (int)blocks;
   d.dt = p->dt;
   const double half_skin = 0.5 * (p->pair_mode == MD_PAIR_VERLET ? p->skin : 0.0);
   d.lim2 = half_skin * half_skin;
@@ -1155,30 +1350,26 @@ int init_impl(md_handle *h, const md_params *p, const md_system *s) {
     d.mass[t] = t < p->ntypes ? p->mass[t] : 1.0;
     d.invm[t] = 1.0 / d.mass[t];
   }
-  const double rho = (double)n / (p->box * p->box * p->box);
   int maxnb = p->max_neighbors;
   if (maxnb <= 0) {
-    const double mean = rho * 4.18879020478639 * rl * rl * rl;
+    const double mean = rho_max * 4.18879020478639 * rl * rl * rl;
     maxnb = ((int)(1.35 * mean + 24.0) + 7) / 8 * 8;
   }
   d.maxnb = maxnb;
   d.vacf_u = p->vacf.u;
   d.maxchunks = (n + 31) / 32;  // 32-atom chunks of the neighbour lists
   for (int t = 0; t < 8; ++t) {
-    const dfloat h = df_from_double(0.5 * p->dt * d.invm[t]);
-    d.hdtm_h[t] = h.h;
-    d.hdtm_l[t] = h.l;
+    const dfloat hh = df_from_double(0.5 * p->dt * d.invm[t]);
+    d.hdtm_h[t] = hh.h;
+    d.hdtm_l[t] = hh.l;
   }
   {
-    const dfloat dtf = df_from_double(p->dt), ef = df_from_double(d.edge);
+    const dfloat dtf = df_from_double(p->dt);
     d.dt_h = dtf.h;
     d.dt_l = dtf.l;
-    d.edge_h = ef.h;
-    d.edge_l = ef.l;
   }
   const size_t tf = h->fp64 ? sizeof(double) : sizeof(float);
   const size_t v4 = h->fp64 ? sizeof(dvec4) : sizeof(float4);
-  h->red_blocks = grid_for(n, kThreads, kMaxRedBlocks);
   OTF_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   if (h->fp64) {
     OTF_CUDA(cudaMalloc(&d.r, 3 * n * sizeof(double)));
@@ -1204,35 +1395,71 @@ int init_impl(md_handle *h, const md_params *p, const md_system *s) {
   OTF_CUDA(cudaMalloc(&d.cellB, n * sizeof(int)));
   OTF_CUDA(cudaMalloc(&d.slot, n * sizeof(int)));
   OTF_CUDA(cudaMalloc(&d.perm, n * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&d.cellcount, d.ncell * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&d.cellstart, (d.ncell + 1) * sizeof(int)));
+  OTF_CUDA(cudaMalloc(&d.cellcount, ncell * sizeof(int)));
+  OTF_CUDA(cudaMalloc(&d.cellstart, (ncell + 1) * sizeof(int)));
   if (p->pair_mode == MD_PAIR_VERLET)
     OTF_CUDA(cudaMalloc(&d.nbr, (size_t)d.maxchunks * maxnb * 32 * sizeof(uint32_t)));
   OTF_CUDA(cudaMalloc(&d.nnb, n * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&d.partials, (size_t)h->red_blocks * kNRed * sizeof(double)));
-  OTF_CUDA(cudaMalloc(&d.counter, sizeof(unsigned)));
-  OTF_CUDA(cudaMalloc(&d.obs, sizeof(ObsDev)));
+  OTF_CUDA(cudaMalloc(&d.partials, (size_t)blocks * kNRed * sizeof(double)));
+  OTF_CUDA(cudaMalloc(&d.counter, count * sizeof(unsigned)));
+  OTF_CUDA(cudaMalloc(&d.obs, count * sizeof(ObsDev)));
+  OTF_CUDA(cudaMalloc(&d.st, sizeof(StepDev)));
   OTF_CUDA(cudaMalloc(&d.rebuild, sizeof(int)));
   OTF_CUDA(cudaMalloc(&d.err, sizeof(unsigned)));
-  OTF_CUDA(cudaMallocHost(&h->h_obs, sizeof(ObsDev)));
+  OTF_CUDA(cudaMalloc(&h->d_rep, count * sizeof(Rep)));
+  OTF_CUDA(cudaMalloc(&h->d_rep_of_atom, n * sizeof(int)));
+  OTF_CUDA(cudaMalloc(&h->d_rep_of_cell, ncell * sizeof(int)));
+  OTF_CUDA(cudaMalloc(&h->d_rep_of_block, blocks * sizeof(int)));
+  OTF_CUDA(cudaMalloc(&h->d_lam, count * sizeof(double)));
+  OTF_CUDA(cudaMallocHost(&h->h_obs, count * sizeof(ObsDev)));
+  OTF_CUDA(cudaMallocHost(&h->h_st, sizeof(StepDev)));
   OTF_CUDA(cudaMallocHost(&h->h_err, sizeof(unsigned)));
+  OTF_CUDA(cudaMallocHost(&h->h_lam, count * sizeof(double)));
+  d.rep = h->d_rep;
+  d.rep_of_atom = h->d_rep_of_atom;
+  d.rep_of_cell = h->d_rep_of_cell;
+  d.rep_of_block = h->d_rep_of_block;
+  d.lam = h->d_lam;
   cudaStream_t st = h->stream;
-  OTF_CUDA(cudaMemsetAsync(d.counter, 0, sizeof(unsigned), st));
-  OTF_CUDA(cudaMemsetAsync(d.obs, 0, sizeof(ObsDev), st));
+  {
+    // replica lookup tables (set-up only)
+    std::vector<int> roa(n), roc(ncell), rob(blocks);
+    for (int k = 0; k < count; ++k) {
+      const Rep &R = h->reps[k];
+      std::fill(roa.begin() + R.atom0, roa.begin() + R.atom1, k);
+      std::fill(roc.begin() + R.cell0, roc.begin() + R.cell0 + (int64_t)R.nc * R.nc * R.nc, k);
+      std::fill(rob.begin() + R.block0, rob.begin() + R.block0 + R.nblk, k);
+    }
+    OTF_CUDA(cudaMemcpy(h->d_rep, h->reps.data(), count * sizeof(Rep), cudaMemcpyHostToDevice));
+    OTF_CUDA(cudaMemcpy(h->d_rep_of_atom, roa.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+    OTF_CUDA(cudaMemcpy(h->d_rep_of_cell, roc.data(), ncell * sizeof(int), cudaMemcpyHostToDevice));
+    OTF_CUDA(cudaMemcpy(h->d_rep_of_block, rob.data(), blocks * sizeof(int), cudaMemcpyHostToDevice));
+  }
+  OTF_CUDA(cudaMemsetAsync(d.counter, 0, count * sizeof(unsigned), st));
+  OTF_CUDA(cudaMemsetAsync(d.obs, 0, count * sizeof(ObsDev), st));
+  OTF_CUDA(cudaMemsetAsync(d.st, 0, sizeof(StepDev), st));
   OTF_CUDA(cudaMemsetAsync(d.err, 0, sizeof(unsigned), st));
   OTF_CUDA(cudaMemsetAsync(d.F, 0, 3 * n * tf, st));
   OTF_CUDA(cudaMemsetAsync(d.vbuf, 0, 3 * n * tf, st));
   const int one = 1;
   OTF_CUDA(cudaMemcpyAsync(d.rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, st));
-  const cudaMemcpyKind kind = s->mem == MD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  // FP64 form: straight into the state; mixed form: through the scratch,
+  // inputs, replica after replica, component-major within the whole system:
+  // FP64 form straight into the state; mixed form through the scratch,
   // converted to cell + double-float offset by k_init_df below
-  OTF_CUDA(cudaMemcpyAsync(h->fp64 ? d.r : d.rB, s->r, 3 * n * sizeof(double), kind, st));
-  OTF_CUDA(cudaMemcpyAsync(h->fp64 ? d.v : d.vB, s->v, 3 * n * sizeof(double), kind, st));
-  if (s->type)
-    OTF_CUDA(cudaMemcpyAsync(d.type, s->type, n * sizeof(int), kind, st));
-  else
-    OTF_CUDA(cudaMemsetAsync(d.type, 0, n * sizeof(int), st));
+  const cudaMemcpyKind kind = mem == MD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  double *rdst = h->fp64 ? d.r : d.rB, *vdst = h->fp64 ? d.v : d.vB;
+  for (int k = 0; k < count; ++k) {
+    const Rep &R = h->reps[k];
+    const int64_t nk = reps[k].n;
+    for (int a = 0; a < 3; ++a) {
+      OTF_CUDA(cudaMemcpyAsync(rdst + a * n + R.atom0, reps[k].r + a * nk, nk * sizeof(double), kind, st));
+      OTF_CUDA(cudaMemcpyAsync(vdst + a * n + R.atom0, reps[k].v + a * nk, nk * sizeof(double), kind, st));
+    }
+    if (reps[k].type)
+      OTF_CUDA(cudaMemcpyAsync(d.type + R.atom0, reps[k].type, nk * sizeof(int), kind, st));
+    else
+      OTF_CUDA(cudaMemsetAsync(d.type + R.atom0, 0, nk * sizeof(int), st));
+  }
   k_iota<<<grid_for(n, kThreads), kThreads, 0, st>>>(d.id, n);
   OTF_LAUNCH_CHECK();
   if (!h->fp64) {
@@ -1241,11 +1468,12 @@ int init_impl(md_handle *h, const md_params *p, const md_system *s) {
   }
   // host-side copies of the inputs must be done before returning
   OTF_CUDA(cudaStreamSynchronize(st));
-  // correlators
+  // correlators: stress and heat flux have 3 series per replica, the
+  // velocity correlator 3n series in 3 groups (single system)
   const corr_spec *specs[3] = {&p->stress, &p->heatflux, &p->vacf};
   for (int k = 0; k < 3; ++k) {
     if (specs[k]->u <= 0) continue;
-    corr_params cp{specs[k]->b, specs[k]->p, specs[k]->m, 0, k == 2 ? 3 * n : 3, k == 2 ? n : 1,
+    corr_params cp{specs[k]->b, specs[k]->p, specs[k]->m, 0, k == 2 ? 3 * n : 3 * (int64_t)count, k == 2 ? n : 1,
                    k == 2 ? p->precision : MD_PREC_FP64, specs[k]->u * p->dt};
     Correlator &c = h->banks[k].c;
     h->bank_on[k] = true;
@@ -1262,7 +1490,64 @@ int init_impl(md_handle *h, const md_params *p, const md_system *s) {
   rc = h->fp64 ? launch_pair<double>(h, st) : launch_pair<float>(h, st);
   if (rc) return rc;
   if ((rc = refresh_obs(h))) return rc;
-  return check_device(h);
+  if ((rc = check_device(h))) return rc;
+  if (p->autotune) {
+    rc = h->fp64 ? autotune<double>(h) : autotune<float>(h);
+    if (rc) return rc;
+    if ((rc = refresh_obs(h))) return rc;
+    return check_device(h);
+  }
+  return MD_OK;
+}
+
+void fill_obs(const md_handle *h, int r, md_obs *out) {
+  const ObsDev &o = h->h_obs[r];
+  out->step = h->h_st->step;
+  out->U = o.U;
+  out->K = o.K;
+  out->T = o.T;
+  for (int a = 0; a < 6; ++a) out->sigma[a] = o.sigma[a];
+  for (int a = 0; a < 3; ++a) out->q[a] = o.q[a];
+  out->T_mean = o.Tn > 0 ? o.Tsum / (double)o.Tn : o.T;
+  out->rebuilds = h->h_st->rebuilds;
+}
+
+int fetch_obs(md_handle *h) {
+  OTF_CUDA(cudaMemcpyAsync(h->h_obs, h->d.obs, h->nrep * sizeof(ObsDev), cudaMemcpyDeviceToHost, h->stream));
+  OTF_CUDA(cudaMemcpyAsync(h->h_st, h->d.st, sizeof(StepDev), cudaMemcpyDeviceToHost, h->stream));
+  OTF_CUDA(cudaStreamSynchronize(h->stream));
+  return MD_OK;
+}
+
+int scale_impl(md_handle *h) {
+  OTF_CUDA(cudaMemcpyAsync(h->d_lam, h->h_lam, h->nrep * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  if (h->fp64)
+    k_scale_v<double><<<grid_for(3 * h->d.n, kThreads), kThreads, 0, h->stream>>>(h->d);
+  else
+    k_scale_v<float><<<grid_for(3 * h->d.n, kThreads), kThreads, 0, h->stream>>>(h->d);
+  OTF_LAUNCH_CHECK();
+  int rc = refresh_obs(h);
+  if (rc) return rc;
+  OTF_CUDA(cudaStreamSynchronize(h->stream));
+  return MD_OK;
+}
+
+int create_handle(const md_params *p, const md_replica *reps, int count, int mem, void *cuda_stream,
+                  md_handle **out) {
+  *out = nullptr;
+  int rc = validate_params(p);
+  if (!rc) rc = validate_replicas(p, reps, count, mem);
+  if (rc) return rc;
+  md_handle *h = new (std::nothrow) md_handle;
+  if (!h) return MD_ENOMEM;
+  h->stream = (cudaStream_t)cuda_stream;
+  rc = init_impl(h, p, reps, count, mem);
+  if (rc) {
+    release(h);
+    return rc;
+  }
+  *out = h;
+  return MD_OK;
 }
 
 }  // namespace
@@ -1271,23 +1556,31 @@ extern "C" {
 
 int md_init(const md_params *p, const md_system *s, void *cuda_stream, md_handle **out) {
   clear_error();
-  if (!out) {
-    set_error("md_init: null output handle");
+  if (!out || !p || !s) {
+    set_error("md_init: null argument");
     return MD_EINVAL;
   }
   *out = nullptr;
-  int rc = validate(p, s);
-  if (rc) return rc;
-  md_handle *h = new (std::nothrow) md_handle;
-  if (!h) return MD_ENOMEM;
-  h->stream = (cudaStream_t)cuda_stream;
-  rc = init_impl(h, p, s);
-  if (rc) {
-    release(h);
-    return rc;
+  if (p->n < 2 || p->n >= (1 << 27) || !(p->box > 0)) {
+    set_error("md_init: n must be in [2, 2^27) and box positive");
+    return MD_EINVAL;
   }
-  *out = h;
-  return MD_OK;
+  if (!s->r || !s->v) {
+    set_error("md_init: system needs r, v and a valid mem flag");
+    return MD_EINVAL;
+  }
+  const md_replica one{p->n, p->box, s->r, s->v, s->type};
+  return create_handle(p, &one, 1, s->mem, cuda_stream, out);
+}
+
+int md_init_replicas(const md_params *p, const md_replica *reps, int32_t count, int32_t mem, void *cuda_stream,
+                     md_handle **out) {
+  clear_error();
+  if (!out) {
+    set_error("md_init_replicas: null output handle");
+    return MD_EINVAL;
+  }
+  return create_handle(p, reps, count, mem, cuda_stream, out);
 }
 
 int md_step(md_handle *h, int64_t nsteps) {
@@ -1327,23 +1620,17 @@ int md_step(md_handle *h, int64_t nsteps) {
   return rc;
 }
 
-int md_observables(md_handle *h, md_obs *out) {
+int md_observables(md_handle *h, md_obs *out) { return md_replica_observables(h, 0, out); }
+
+int md_replica_observables(md_handle *h, int32_t r, md_obs *out) {
   clear_error();
-  if (!h || !out) {
-    set_error("md_observables: null argument");
+  if (!h || !out || r < 0 || r >= h->nrep) {
+    set_error("md_replica_observables: bad argument");
     return MD_EINVAL;
   }
-  OTF_CUDA(cudaMemcpyAsync(h->h_obs, h->d.obs, sizeof(ObsDev), cudaMemcpyDeviceToHost, h->stream));
-  OTF_CUDA(cudaStreamSynchronize(h->stream));
-  const ObsDev &o = *h->h_obs;
-  out->step = o.step;
-  out->U = o.U;
-  out->K = o.K;
-  out->T = o.T;
-  for (int a = 0; a < 6; ++a) out->sigma[a] = o.sigma[a];
-  for (int a = 0; a < 3; ++a) out->q[a] = o.q[a];
-  out->T_mean = o.Tn > 0 ? o.Tsum / (double)o.Tn : o.T;
-  out->rebuilds = o.rebuilds;
+  int rc = fetch_obs(h);
+  if (rc) return rc;
+  fill_obs(h, r, out);
   return MD_OK;
 }
 
@@ -1388,15 +1675,24 @@ int md_scale_velocities(md_handle *h, double lambda) {
     set_error("md_scale_velocities: bad argument");
     return MD_EINVAL;
   }
-  if (h->fp64)
-    k_scale_v<double><<<grid_for(3 * h->d.n, kThreads), kThreads, 0, h->stream>>>(h->d, lambda);
-  else
-    k_scale_v<float><<<grid_for(3 * h->d.n, kThreads), kThreads, 0, h->stream>>>(h->d, lambda);
-  OTF_LAUNCH_CHECK();
-  int rc = refresh_obs(h);
-  if (rc) return rc;
-  OTF_CUDA(cudaStreamSynchronize(h->stream));
-  return MD_OK;
+  for (int k = 0; k < h->nrep; ++k) h->h_lam[k] = lambda;
+  return scale_impl(h);
+}
+
+int md_replica_scale_velocities(md_handle *h, const double *lambda) {
+  clear_error();
+  if (!h || !lambda) {
+    set_error("md_replica_scale_velocities: null argument");
+    return MD_EINVAL;
+  }
+  for (int k = 0; k < h->nrep; ++k) {
+    if (!std::isfinite(lambda[k])) {
+      set_error("md_replica_scale_velocities: non-finite factor for replica %d", k);
+      return MD_EINVAL;
+    }
+    h->h_lam[k] = lambda[k];
+  }
+  return scale_impl(h);
 }
 
 int md_reset_correlators(md_handle *h) {
@@ -1407,13 +1703,16 @@ int md_reset_correlators(md_handle *h) {
       int rc = h->banks[k].c.reset();
       if (rc) return rc;
     }
-  // correlator base := current step; temperature mean restarts
-  OTF_CUDA(cudaMemcpyAsync(h->h_obs, h->d.obs, sizeof(ObsDev), cudaMemcpyDeviceToHost, h->stream));
-  OTF_CUDA(cudaStreamSynchronize(h->stream));
-  h->h_obs->corr_base = h->h_obs->step;
-  h->h_obs->Tsum = 0.0;
-  h->h_obs->Tn = 0;
-  OTF_CUDA(cudaMemcpyAsync(h->d.obs, h->h_obs, sizeof(ObsDev), cudaMemcpyHostToDevice, h->stream));
+  // correlator base := current step; temperature means restart
+  int rc = fetch_obs(h);
+  if (rc) return rc;
+  h->h_st->corr_base = h->h_st->step;
+  for (int k = 0; k < h->nrep; ++k) {
+    h->h_obs[k].Tsum = 0.0;
+    h->h_obs[k].Tn = 0;
+  }
+  OTF_CUDA(cudaMemcpyAsync(h->d.st, h->h_st, sizeof(StepDev), cudaMemcpyHostToDevice, h->stream));
+  OTF_CUDA(cudaMemcpyAsync(h->d.obs, h->h_obs, h->nrep * sizeof(ObsDev), cudaMemcpyHostToDevice, h->stream));
   OTF_CUDA(cudaStreamSynchronize(h->stream));
   h->corr_base = h->steps_done;
   return MD_OK;
@@ -1430,6 +1729,21 @@ int md_corr(md_handle *h, int32_t which, corr_handle **out) {
     return MD_EINVAL;
   }
   *out = &h->banks[which];
+  return MD_OK;
+}
+
+int md_get_config(md_handle *h, md_config *out) {
+  clear_error();
+  if (!h || !out) {
+    set_error("md_get_config: null argument");
+    return MD_EINVAL;
+  }
+  out->replicas = h->nrep;
+  out->atoms = h->d.n;
+  out->cells = h->d.ncell;
+  out->max_neighbors = h->d.maxnb;
+  out->pair_threads = h->pair_threads;
+  out->build_warps = h->build_warps;
   return MD_OK;
 }
 
