@@ -106,7 +106,7 @@ struct Sys {
   unsigned *counter;         // [nrep] finished CTAs per replica
   ObsDev *obs;               // [nrep]
   StepDev *st;
-  int *rebuild;
+  int *rebuild;              // [1 + nrep]: any replica, then each replica
   unsigned *err;
 };
 
@@ -123,17 +123,33 @@ __device__ __forceinline__ void unpack_cell(int c, int &x, int &y, int &z) {
 }
 __device__ __forceinline__ int type_of(const Sys &d, int64_t i) { return min(max(d.type[i], 0), 7); }
 __device__ __forceinline__ const Rep &rep_of(const Sys &d, int64_t i) { return d.rep[d.rep_of_atom[i]]; }
+// Rebuild flags: a replica is re-sorted and gets new lists only when one of
+// its own atoms has moved half the skin, so each replica follows exactly the
+// schedule it would follow alone.
+__device__ __forceinline__ bool any_rebuild(const Sys &d) { return d.rebuild[0] != 0; }
+__device__ __forceinline__ bool rebuilds(const Sys &d, int r) { return d.rebuild[1 + r] != 0; }
+__device__ __forceinline__ void request_rebuild(const Sys &d, int r) {
+  d.rebuild[1 + r] = 1;
+  d.rebuild[0] = 1;
+}
 
 // ------------------------------------------------------------ integrate
 
 // FP64 form: first half kick and drift (velocity Verlet), new
 // cell-relative coordinates, and the skin test that decides the next
 // rebuild.
+// Link-cell mode (or no skin): every replica is re-sorted every step.
+__device__ __forceinline__ void request_all(const Sys &d) {
+  if (d.always_rebuild && blockIdx.x == 0)
+    for (int k = threadIdx.x; k <= d.nrep; k += blockDim.x) d.rebuild[k] = 1;
+}
+
 __global__ void __launch_bounds__(kThreads) k_kick_drift64(Sys d, double hdt) {
+  request_all(d);
   const double *F = static_cast<const double *>(d.F);
   dvec4 *rel = static_cast<dvec4 *>(d.rel);
   const dvec4 *relb = static_cast<const dvec4 *>(d.relb);
-  bool over = false, bad = false;
+  bool bad = false;
   const int64_t n = d.n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -155,10 +171,9 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift64(Sys d, double hdt) {
     Vec4<double>::store(rel + i, px, py, pz);
     const dvec4 b = Vec4<double>::load(relb + i);
     const double dx = px - b.x, dy = py - b.y, dz = pz - b.z;
-    over |= (dx * dx + dy * dy + dz * dz) > d.lim2;
+    if ((dx * dx + dy * dy + dz * dz) > d.lim2) request_rebuild(d, d.rep_of_atom[i]);
     bad |= !(isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]));
   }
-  if (__any_sync(0xffffffffu, over || d.always_rebuild) && (threadIdx.x & 31) == 0) *d.rebuild = 1;
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(d.err, ERR_NONFINITE);
 }
 
@@ -167,12 +182,13 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift64(Sys d, double hdt) {
 // per atom).  The offset's high words are the FP32 coordinates of the pair
 // kernel.
 __global__ void __launch_bounds__(kThreads) k_kick_drift_df(Sys d) {
+  request_all(d);
   const float *F = static_cast<const float *>(d.F);
   float4 *rel = static_cast<float4 *>(d.rel);
   const float4 *relb = static_cast<const float4 *>(d.relb);
   const dfloat dt{d.dt_h, d.dt_l};
   const float lim2 = (float)d.lim2;
-  bool over = false, bad = false;
+  bool bad = false;
   const int64_t n = d.n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -194,20 +210,19 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift_df(Sys d) {
     rel[i] = make_float4(oh[0], oh[1], oh[2], 0.f);
     const float4 b = relb[i];
     const float dx = oh[0] - b.x, dy = oh[1] - b.y, dz = oh[2] - b.z;
-    over |= (dx * dx + dy * dy + dz * dz) > lim2;
+    if ((dx * dx + dy * dy + dz * dz) > lim2) request_rebuild(d, d.rep_of_atom[i]);
     bad |= !(isfinite(oh[0]) && isfinite(oh[1]) && isfinite(oh[2]));
   }
-  if (__any_sync(0xffffffffu, over || d.always_rebuild) && (threadIdx.x & 31) == 0) *d.rebuild = 1;
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(d.err, ERR_NONFINITE);
 }
 
 // ---------------------------------------------------------------- sort
 
 __global__ void k_rb_zero(Sys d) {
-  if (!*d.rebuild) return;
+  if (!any_rebuild(d)) return;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < d.ncell;
        c += (int64_t)gridDim.x * blockDim.x)
-    d.cellcount[c] = 0;
+    if (rebuilds(d, d.rep_of_cell[c])) d.cellcount[c] = 0;
 }
 
 // Takes a provisional slot in cell c for atom i: lanes binning into the
@@ -226,10 +241,11 @@ __device__ __forceinline__ void bin_atom(const Sys &d, int64_t i, int c) {
 // FP64 form: wraps positions into the box, bins every atom into its cell
 // and copies the state aside for the gather.
 __global__ void __launch_bounds__(kThreads) k_rb_assign64(Sys d) {
-  if (!*d.rebuild) return;
+  if (!any_rebuild(d)) return;
   const int64_t n = d.n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    if (!rebuilds(d, d.rep_of_atom[i])) continue;
     const Rep &R = rep_of(d, i);
     const int nc = R.nc;
     int ci[3];
@@ -257,13 +273,14 @@ __global__ void __launch_bounds__(kThreads) k_rb_assign64(Sys d) {
 // multiple of the edge, in double-float.  Scratch layout: rB = offset high
 // then low words, vB = velocity high then low words (float [3][n] each).
 __global__ void __launch_bounds__(kThreads) k_rb_assign_df(Sys d) {
-  if (!*d.rebuild) return;
+  if (!any_rebuild(d)) return;
   const int64_t n = d.n;
   const float4 *rel = static_cast<const float4 *>(d.rel);
   float *oB = reinterpret_cast<float *>(d.rB);
   float *wB = reinterpret_cast<float *>(d.vB);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    if (!rebuilds(d, d.rep_of_atom[i])) continue;
     const Rep &R = rep_of(d, i);
     const int nc = R.nc;
     const dfloat edge{R.edge_h, R.edge_l};
@@ -299,7 +316,7 @@ __global__ void __launch_bounds__(kThreads) k_rb_assign_df(Sys d) {
 // segments, warp 0 scans the 32 sums, pass 2 scans each row with shuffles
 // and a running carry.
 __global__ void __launch_bounds__(1024) k_rb_scan(Sys d) {
-  if (!*d.rebuild) return;
+  if (!any_rebuild(d)) return;
   __shared__ int wsum[32];
   const int64_t nc3 = d.ncell;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -341,10 +358,10 @@ __global__ void __launch_bounds__(1024) k_rb_scan(Sys d) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_rb_place(Sys d) {
-  if (!*d.rebuild) return;
+  if (!any_rebuild(d)) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.n;
        i += (int64_t)gridDim.x * blockDim.x)
-    d.perm[d.cellstart[d.cellB[i]] + d.slot[i]] = (int)i;
+    if (rebuilds(d, d.rep_of_atom[i])) d.perm[d.cellstart[d.cellB[i]] + d.slot[i]] = (int)i;
 }
 
 // One warp per cell: orders the cell's atoms by id (deterministic layout
@@ -352,12 +369,13 @@ __global__ void __launch_bounds__(kThreads) k_rb_place(Sys d) {
 // cell-relative coordinates.
 template <typename TF>
 __global__ void __launch_bounds__(kCellWarps * 32) k_rb_rank(Sys d) {
-  if (!*d.rebuild) return;
+  if (!any_rebuild(d)) return;
   const int lane = threadIdx.x & 31;
   const int64_t n = d.n;
   const int64_t wglobal = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t c = wglobal; c < d.ncell; c += nwarps) {
+    if (!rebuilds(d, d.rep_of_cell[c])) continue;
     const int s0 = d.cellstart[c], cnt = d.cellstart[c + 1] - s0;
     const Rep &R = d.rep[d.rep_of_cell[c]];
     const int64_t lc = c - R.cell0;
@@ -533,7 +551,7 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
 template <typename TF, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_build(Sys d, LJ<TF> lj) {
   using V4 = typename Vec4<TF>::type;
-  if (!*d.rebuild) return;
+  if (!any_rebuild(d)) return;
   __shared__ V4 spi[WARPS][32];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int64_t n = d.n;
@@ -556,6 +574,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_build(Sys d, LJ<TF> lj) {
       int cx, cy, cz;
       unpack_cell(d.cpk[s], cx, cy, cz);
       const int e = min(d.cellstart[R.cell0 + (cz * nc + cy) * nc + cx + 1], a1);
+      if (!rebuilds(d, d.rep_of_atom[s])) {  // this replica keeps its lists
+        s = e;
+        continue;
+      }
       for (int row = 0; row < 9; ++row) {
         const int oy = row % 3 - 1, oz = row / 3 - 1;
         const int jy = (cy + oy + nc) % nc, jz = (cz + oz + nc) % nc;
@@ -608,7 +630,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_build(Sys d, LJ<TF> lj) {
       }
       s = e;
     }
-    if (a0 + lane < a1) {
+    if (a0 + lane < a1 && rebuilds(d, d.rep_of_atom[a0 + lane])) {
       d.nnb[a0 + lane] = min(cnt, d.maxnb);
       if (cnt > d.maxnb) atomicOr(d.err, ERR_NBR_OVERFLOW);
     }
@@ -821,13 +843,17 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   // the last replica to finish closes the step
+  __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    if (atomicAdd(&d.st->reps_done, 1u) == (unsigned)d.nrep - 1) {
-      d.st->reps_done = 0u;
-      if (KICK) d.st->step = step_now;
-      *d.rebuild = 0;
-    }
+    last = atomicAdd(&d.st->reps_done, 1u) == (unsigned)d.nrep - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  for (int k = threadIdx.x; k <= d.nrep; k += blockDim.x) d.rebuild[k] = 0;
+  if (threadIdx.x == 0) {
+    d.st->reps_done = 0u;
+    if (KICK) d.st->step = step_now;
   }
 }
 
@@ -1278,7 +1304,6 @@ float time_runs(md_handle *h, int reps, Fn fn) {
 template <typename TF>
 int autotune(md_handle *h) {
   if (h->prm.pair_mode != MD_PAIR_VERLET) return MD_OK;
-  const int one = 1;
   float best = 1e30f;
   int best_t = h->pair_threads;
   for (int t : {64, 128, 256}) {
@@ -1292,19 +1317,18 @@ int autotune(md_handle *h) {
   for (int w : {2, 4, 8}) {
     h->build_warps = w;
     const float ms = time_runs(h, 3, [&] {
-      cudaMemcpyAsync(h->d.rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream);
+      cudaMemsetAsync(h->d.rebuild, 1, (h->nrep + 1) * sizeof(int), h->stream);
       launch_build<TF>(h, h->stream);
     });
     if (ms < best) best = ms, best_w = w;
   }
   h->build_warps = best_w;
-  OTF_CUDA(cudaMemsetAsync(h->d.rebuild, 0, sizeof(int), h->stream));
   // rebuild the lists once more with the chosen shape, then the forces
-  OTF_CUDA(cudaMemcpyAsync(h->d.rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  OTF_CUDA(cudaMemsetAsync(h->d.rebuild, 1, (h->nrep + 1) * sizeof(int), h->stream));
   launch_build<TF>(h, h->stream);
   OTF_LAUNCH_CHECK();
   if (int rc = launch_pair<TF>(h, h->stream)) return rc;
-  OTF_CUDA(cudaMemsetAsync(h->d.rebuild, 0, sizeof(int), h->stream));
+  OTF_CUDA(cudaMemsetAsync(h->d.rebuild, 0, (h->nrep + 1) * sizeof(int), h->stream));
   OTF_CUDA(cudaStreamSynchronize(h->stream));
   return MD_OK;
 }
@@ -1404,7 +1428,7 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   OTF_CUDA(cudaMalloc(&d.counter, count * sizeof(unsigned)));
   OTF_CUDA(cudaMalloc(&d.obs, count * sizeof(ObsDev)));
   OTF_CUDA(cudaMalloc(&d.st, sizeof(StepDev)));
-  OTF_CUDA(cudaMalloc(&d.rebuild, sizeof(int)));
+  OTF_CUDA(cudaMalloc(&d.rebuild, (count + 1) * sizeof(int)));
   OTF_CUDA(cudaMalloc(&d.err, sizeof(unsigned)));
   OTF_CUDA(cudaMalloc(&h->d_rep, count * sizeof(Rep)));
   OTF_CUDA(cudaMalloc(&h->d_rep_of_atom, n * sizeof(int)));
@@ -1441,8 +1465,7 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   OTF_CUDA(cudaMemsetAsync(d.err, 0, sizeof(unsigned), st));
   OTF_CUDA(cudaMemsetAsync(d.F, 0, 3 * n * tf, st));
   OTF_CUDA(cudaMemsetAsync(d.vbuf, 0, 3 * n * tf, st));
-  const int one = 1;
-  OTF_CUDA(cudaMemcpyAsync(d.rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+  OTF_CUDA(cudaMemsetAsync(d.rebuild, 1, (count + 1) * sizeof(int), st));  // every flag set (nonzero)
   // inputs, replica after replica, component-major within the whole system:
   // FP64 form straight into the state; mixed form through the scratch,
   // converted to cell + double-float offset by k_init_df below
