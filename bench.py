@@ -314,11 +314,129 @@ def run_ours(args):
         "fp64_gpu": {"ms_per_step": ms64, "value": world * n / (ms64 / 1e3), "steps": k64,
                      "speedup_mixed_over_fp64": ms64 / ms_step},
     }
+    if world == 1 and not args.no_ensemble:
+        out["batched_ensemble"] = run_batched(pkg, synth, 200, torch)
+        out["time_to_viscosity"] = run_time_to_viscosity(pkg, synth, torch)
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(st, s, budget_s=args.cpu_seconds)
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def c4_ensemble(pkg, synth, count=256, seed=11):
+    """The batched-replica workload: count LJ replicas with sizes drawn
+    log-uniformly in [500, 32,000] atoms (fcc k^3 x 4, k in [5, 20]),
+    density uniform in [0.7, 0.9] and T* uniform in [0.7, 2.0]."""
+    u = synth.uniform01(seed, 3 * count).reshape(3, count)
+    reps, temps = [], []
+    for k in range(count):
+        n_target = math.exp(math.log(500) + u[0, k] * (math.log(32000) - math.log(500)))
+        cells = synth.cells_for_atoms(n_target)
+        rho = 0.7 + 0.2 * u[1, k]
+        T = 0.7 + 1.3 * u[2, k]
+        s = synth.lj_system(cells, rho=rho, T=T, seed=seed * 1000 + k)
+        reps.append(dict(r=s["r"], v=s["v"], box=s["L"]))
+        temps.append(T)
+    return reps, np.array(temps)
+
+
+def melt_replicas(g, temps, steps_hot=600, steps_cold=600, every=10):
+    """Velocity rescaling per replica: all to T* = 2.0, then each to its own T*."""
+    nrep = len(temps)
+    for target, steps in ((np.full(nrep, 2.0), steps_hot), (temps, steps_cold)):
+        for _ in range(steps // every):
+            g.step(every)
+            T = np.array([g.replica_observables(k)["T"] for k in range(nrep)])
+            g.replica_scale_velocities(np.sqrt(target / T))
+
+
+def run_batched(pkg, synth, steps, torch):
+    """Throughput of the 256-replica uneven ensemble in one handle (mixed
+    form, autotuned launch shapes, stress and heat-flux correlators)."""
+    reps, temps = c4_ensemble(pkg, synth)
+    p = pkg.make_params(1, 1.0, rc=RC, dt=DT, skin=0.2, precision=pkg.MD_PREC_MIXED, autotune=True,
+                        stress=(12, 16, 2, 1), heatflux=(12, 16, 2, 1), vacf=None)
+    g = pkg.System(p, replicas=reps)
+    melt_replicas(g, temps, 300, 300)
+    g.reset_correlators()
+    g.step(5)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    g.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    cfg = g.config()
+    g.close()
+    return {"workload": "256 LJ replicas, sizes log-uniform in [500, 32000] atoms, rho* uniform in [0.7, 0.9], "
+                        "T* uniform in [0.7, 2.0], rc=2.5, dt=0.005, skin 0.2, mixed form, one handle, one graph "
+                        "launch per step; stress and heat-flux correlators per replica",
+            "atoms": cfg["atoms"], "replicas": cfg["replicas"], "steps": steps, "ms_per_step": ms / steps,
+            "value": cfg["atoms"] * steps / (ms / 1e3), "unit": UNIT,
+            "autotuned": {"pair_threads": cfg["pair_threads"], "build_warps": cfg["build_warps"]}}
+
+
+def eta_of(t, c, V, T, gk):
+    return gk(t, c, t_cut=2.0, prefactor=V / T)[0]
+
+
+def run_time_to_viscosity(pkg, synth, torch, replicas=64, prod=4000):
+    """Time to a Green-Kubo viscosity with <= 2 % relative standard error at
+    the 4,000-atom state point (rho* = 0.8442, T* = 0.722; eta from each
+    replica's stress autocorrelation, mean of xy/xz/yz, integrated to
+    t_cut = 2 tau).  The spread of eta over `replicas` replicas of `prod`
+    production steps gives the replica-steps needed for 2 %; each form's
+    measured cost per replica-step turns that into seconds of production
+    (equilibration excluded)."""
+    reps = []
+    for k in range(replicas):
+        s = synth.lj_system(10, rho=RHO, T=T_STAR, seed=500 + k)
+        reps.append(dict(r=s["r"], v=s["v"], box=s["L"]))
+    V = reps[0]["box"] ** 3
+    p = pkg.make_params(1, 1.0, rc=RC, dt=DT, skin=0.2, precision=pkg.MD_PREC_MIXED,
+                        stress=(12, 16, 2, 1), heatflux=(12, 16, 2, 1), vacf=None)
+    g = pkg.System(p, replicas=reps)
+    melt_replicas(g, np.full(replicas, T_STAR), 2000, 3000)
+    g.reset_correlators()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.step(prod)
+    torch.cuda.synchronize()
+    batch_s = time.perf_counter() - t0
+    c = g.corr(pkg.MD_CORR_STRESS)
+    etas = []
+    for k in range(replicas):
+        Tk = g.replica_observables(k)["T_mean"]
+        curves = [c.read(3 * k + a) for a in range(3)]
+        etas.append(eta_of(curves[0][0], np.mean([cv[1] for cv in curves], axis=0), V, Tk, pkg.gk_integrate))
+    g.close()
+    etas = np.array(etas)
+    mean, se = etas.mean(), etas.std(ddof=1) / math.sqrt(replicas)
+    need = replicas * prod * (se / (0.02 * abs(mean))) ** 2  # replica-steps for 2 %
+    # cost per replica-step of one 4,000-atom system on its own (graph replay)
+    costs = {"mixed_gpu_batched_%d" % replicas: batch_s / (replicas * prod)}
+    s = synth.lj_system(10, rho=RHO, T=T_STAR, seed=1)
+    for name, prec in (("fp64_gpu_single", pkg.MD_PREC_FP64), ("mixed_gpu_single", pkg.MD_PREC_MIXED)):
+        ps = pkg.make_params(s["n"], s["L"], rc=RC, dt=DT, skin=0.3, precision=prec,
+                             stress=(12, 16, 2, 1), heatflux=(12, 16, 2, 1), vacf=(8, 16, 2, 1))
+        gs = pkg.System(ps, s["r"], s["v"])
+        gs.step(50)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gs.step(2000)
+        torch.cuda.synchronize()
+        costs[name] = (time.perf_counter() - t0) / 2000
+        gs.close()
+    return {"definition": "seconds of production MD (correlators included, equilibration excluded) until the "
+                          "ensemble Green-Kubo viscosity has <= 2 % relative standard error; 4,000-atom LJ liquid, "
+                          "rho*=0.8442, T*=0.722, eta to t_cut = 2 tau; replica-steps needed from the spread over "
+                          f"{replicas} replicas x {prod} steps, seconds = needed x measured cost per replica-step",
+            "eta": float(mean), "eta_se": float(se), "replica_steps_needed": float(need),
+            "seconds": {k: v * need for k, v in costs.items()},
+            "cost_per_replica_step_s": costs}
 
 
 def committed_traffic(kernel):
@@ -405,6 +523,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the replica ensemble and time-to-viscosity")
     ap.add_argument("--cells", type=int, default=CELLS, help="fcc cells per side (4 cells^3 atoms)")
     ap.add_argument("--quick", action="store_true", help="short melt, timed region only (for profilers)")
     args = ap.parse_args()
