@@ -97,3 +97,25 @@ def ar1_series(nseries: int, S: int, phi: float, seed: int) -> np.ndarray:
     for t in range(1, S):
         x[t] = phi * x[t - 1] + c * e[t]
     return x
+
+
+def mlp_init(seed: int, dims, bias_scale: float = 0.0):
+    """Weights of a fully connected network with layer widths dims
+    (n_in, hidden..., n_out): Glorot-uniform matrices W [out, in] with
+    limit sqrt(6 / (in + out)) (Glorot and Bengio, 2010) and biases uniform
+    in [-bias_scale, bias_scale].  Returns [(W, b)] per layer."""
+    out = []
+    for l in range(len(dims) - 1):
+        fi, fo = dims[l], dims[l + 1]
+        lim = math.sqrt(6.0 / (fi + fo))
+        W = (2.0 * uniform01(seed * 1000 + 2 * l, fo * fi) - 1.0).reshape(fo, fi) * lim
+        b = (2.0 * uniform01(seed * 1000 + 2 * l + 1, fo) - 1.0) * bias_scale
+        out.append((W, b))
+    return out
+
+
+def permutations(seed: int, count: int, n: int) -> np.ndarray:
+    """count independent uniform permutations of range(n), shape [count, n],
+    by sorting SplitMix64 keys (ties broken by index)."""
+    keys = splitmix64(seed, count * n).reshape(count, n)
+    return np.argsort(keys, axis=1, kind="stable").astype(np.int64)
