@@ -2,9 +2,11 @@
 
 Lennard-Jones MD on one GPU with the system stress tensor, heat flux and
 multiple-tau correlators (stress, heat flux, per-atom velocity) computed
-while the simulation runs, plus Green-Kubo integrals.  The compute lives in
-``libotfmd.so`` (C ABI in ``include/otf_md.h``); this package only marshals
-arguments.
+while the simulation runs, plus Green-Kubo integrals, and a learned
+Green-Kubo tail (a tensor-core network that predicts converged transport
+coefficients from a short run).  The compute lives in ``libotfmd.so`` (C ABI
+in ``include/otf_md.h`` and ``include/gk_tail.h``); this package only
+marshals arguments.
 """
 from ._lib import (  # noqa: F401
     EXPORTS,
@@ -18,10 +20,12 @@ from ._lib import (  # noqa: F401
     MD_PAIR_VERLET,
     MD_PREC_FP64,
     MD_PREC_MIXED,
+    MLP,
     Corr,
     MdError,
     System,
     gk_integrate,
+    gk_tail_features,
     lib,
     make_params,
     observables_noalloc,

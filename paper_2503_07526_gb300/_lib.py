@@ -69,6 +69,12 @@ class corr_params(C.Structure):
                 ("dt_unit", C.c_double)]
 
 
+class mlp_params(C.Structure):
+    _fields_ = [("n_in", C.c_int32), ("width", C.c_int32), ("depth", C.c_int32), ("n_out", C.c_int32),
+                ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float), ("weight_decay", C.c_float), ("seed", C.c_uint64)]
+
+
 _lib = None
 
 
@@ -105,6 +111,18 @@ def lib(build: bool = False):
         "corr_reset": [vp],
         "gk_integrate": [dp, dp, i64, C.c_double, C.c_double, dp, dp],
         "md_observables_noalloc": [i64, C.c_double, vp, vp, vp, vp, vp, vp],
+        "mlp_create": [C.POINTER(mlp_params), vp, C.POINTER(vp)],
+        "mlp_param_count": [vp, C.POINTER(C.c_int64)],
+        "mlp_get_params": [vp, vp, i64, i32],
+        "mlp_set_params": [vp, vp, i64, i32],
+        "mlp_set_scaler": [vp, vp, vp, vp, vp],
+        "mlp_fit_scaler": [vp, vp, vp, i64],
+        "mlp_forward": [vp, vp, i64, vp, i32],
+        "mlp_loss_grad": [vp, vp, vp, i64, dp, vp, i32],
+        "mlp_adam_step": [vp, vp, i32],
+        "mlp_train": [vp, vp, vp, i64, i32, vp, C.c_uint64, dp, i32],
+        "gk_tail_features": [dp, dp, i64, i64, dp, dp, dp, vp],
+        "corr_read_rows": [vp, i64, i64, i64, dp, dp, i64, C.POINTER(C.c_int64)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -114,6 +132,8 @@ def lib(build: bool = False):
     L.md_free.restype = None
     L.corr_free.argtypes = [vp]
     L.corr_free.restype = None
+    L.mlp_free.argtypes = [vp]
+    L.mlp_free.restype = None
     L.md_last_error.argtypes = []
     L.md_last_error.restype = C.c_char_p
     _lib = L
@@ -124,7 +144,9 @@ EXPORTS = ("md_init", "md_step", "md_observables", "md_get_particles", "md_scale
            "md_reset_correlators", "md_corr", "md_set_timing", "md_kernel_times", "md_free", "corr_create",
            "corr_push", "corr_read", "corr_raw", "corr_pushes", "corr_reset", "corr_free", "gk_integrate",
            "md_last_error", "md_observables_noalloc", "md_init_replicas", "md_replica_observables",
-           "md_replica_scale_velocities", "md_get_config")
+           "md_replica_scale_velocities", "md_get_config", "mlp_create", "mlp_param_count", "mlp_get_params",
+           "mlp_set_params", "mlp_set_scaler", "mlp_fit_scaler", "mlp_forward", "mlp_loss_grad", "mlp_adam_step",
+           "mlp_train", "mlp_free", "gk_tail_features", "corr_read_rows")
 
 
 def _check(rc):
@@ -165,6 +187,7 @@ def _ptr(a, dtype, mem_hint=None):
 
 
 F64 = {"np": np.float64, "torch": None}
+F32 = {"np": np.float32, "torch": None}
 I32 = {"np": np.int32, "torch": None}
 
 
@@ -173,6 +196,7 @@ def _init_dtypes():
         import torch
 
         F64["torch"] = torch.float64
+        F32["torch"] = torch.float32
         I32["torch"] = torch.int32
     except ImportError:
         pass
@@ -230,6 +254,18 @@ class Corr:
         dp = C.POINTER(C.c_double)
         _check(lib().corr_read(self._h, group, t.ctypes.data_as(dp), v.ctypes.data_as(dp), cap, C.byref(n)))
         return t[: n.value].copy(), v[: n.value].copy()
+
+    def read_rows(self, g0, rows, avg=1):
+        """(times [n], values [rows, n]): row i is the mean of groups
+        g0 + i*avg ... g0 + i*avg + avg - 1 on the readout grid."""
+        cap = self.b * self.p
+        t = np.zeros(cap)
+        v = np.zeros((rows, cap))
+        n = C.c_int64(0)
+        dp = C.POINTER(C.c_double)
+        _check(lib().corr_read_rows(self._h, int(g0), int(rows), int(avg), t.ctypes.data_as(dp),
+                                    v.ctypes.data_as(dp), cap, C.byref(n)))
+        return t[: n.value].copy(), v[:, : n.value].copy()
 
     def raw(self):
         vals = np.zeros((self.ngroups, self.b, self.p))
@@ -391,3 +427,133 @@ def observables_noalloc(volume, v, epot, W, mass_of, obs, stream=None):
     n = v.shape[1]
     _check(lib().md_observables_noalloc(n, float(volume), v.data_ptr(), epot.data_ptr(), W.data_ptr(),
                                         mass_of.data_ptr(), obs.data_ptr(), _stream_ptr(stream)))
+
+
+class MLP:
+    """The learned-tail network behind mlp_create / mlp_free (tensor-core
+    bfloat16 products, FP32 master weights, Adam)."""
+
+    def __init__(self, n_in, n_out=2, *, width=128, depth=3, batch=256, lr=1e-3, beta1=0.9, beta2=0.999,
+                 eps=1e-8, weight_decay=0.0, seed=1, stream=None):
+        self.p = mlp_params(n_in, width, depth, n_out, batch, lr, beta1, beta2, eps, weight_decay, seed)
+        self.n_in, self.n_out, self.batch = n_in, n_out, batch
+        h = C.c_void_p()
+        _check(lib().mlp_create(C.byref(self.p), _stream_ptr(stream), C.byref(h)))
+        self._h = h
+        n = C.c_int64(0)
+        _check(lib().mlp_param_count(self._h, C.byref(n)))
+        self.nparams = n.value
+        self.dims = (n_in,) + (width,) * depth + (n_out,)
+
+    # flat parameter order: per layer W [out, in] then b [out]
+    def get_flat(self):
+        f = np.zeros(self.nparams, dtype=np.float32)
+        _check(lib().mlp_get_params(self._h, f.ctypes.data, self.nparams, MD_MEM_HOST))
+        return f
+
+    def set_flat(self, flat):
+        f = np.ascontiguousarray(flat, dtype=np.float32)
+        if f.size != self.nparams:
+            raise ValueError(f"expected {self.nparams} parameters, got {f.size}")
+        _check(lib().mlp_set_params(self._h, f.ctypes.data, self.nparams, MD_MEM_HOST))
+
+    def unflatten(self, flat):
+        out, k = [], 0
+        for fi, fo in zip(self.dims[:-1], self.dims[1:]):
+            W = np.asarray(flat[k:k + fo * fi], dtype=np.float64).reshape(fo, fi)
+            k += fo * fi
+            b = np.asarray(flat[k:k + fo], dtype=np.float64)
+            k += fo
+            out.append((W, b))
+        return out
+
+    @staticmethod
+    def flatten(params):
+        return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in params]).astype(np.float32)
+
+    def get_params(self):
+        return self.unflatten(self.get_flat())
+
+    def set_params(self, params):
+        self.set_flat(self.flatten(params))
+
+    def set_scaler(self, x_mean, x_std, y_mean, y_std):
+        a = [np.ascontiguousarray(v, dtype=np.float32) for v in (x_mean, x_std, y_mean, y_std)]
+        _check(lib().mlp_set_scaler(self._h, *[v.ctypes.data for v in a]))
+
+    def fit_scaler(self, X, T):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        _check(lib().mlp_fit_scaler(self._h, X.ctypes.data, T.ctypes.data, X.shape[0]))
+
+    def forward(self, X):
+        px, mem, kx = _ptr(X, F32)
+        rows = X.shape[0]
+        if mem == MD_MEM_HOST:
+            Y = np.zeros((rows, self.n_out), dtype=np.float32)
+            py = Y.ctypes.data
+        else:
+            import torch
+
+            Y = torch.zeros((rows, self.n_out), dtype=torch.float32, device=X.device)
+            py = Y.data_ptr()
+        _check(lib().mlp_forward(self._h, px, rows, py, mem))
+        return Y
+
+    def loss_grad(self, X, T):
+        px, mem, kx = _ptr(X, F32)
+        pt, memt, kt = _ptr(T, F32)
+        g = np.zeros(self.nparams, dtype=np.float32)
+        loss = C.c_double(0.0)
+        if mem != MD_MEM_HOST:
+            raise ValueError("loss_grad takes host arrays")
+        _check(lib().mlp_loss_grad(self._h, px, pt, X.shape[0], C.byref(loss), g.ctypes.data, mem))
+        return loss.value, g
+
+    def adam_step(self, grad=None):
+        if grad is None:
+            _check(lib().mlp_adam_step(self._h, None, MD_MEM_HOST))
+        else:
+            g = np.ascontiguousarray(grad, dtype=np.float32)
+            _check(lib().mlp_adam_step(self._h, g.ctypes.data, MD_MEM_HOST))
+
+    def train(self, X, T, epochs, order=None, shuffle_seed=1):
+        px, mem, kx = _ptr(X, F32)
+        pt, memt, kt = _ptr(T, F32)
+        if mem != memt:
+            raise ValueError("X and T must live in the same memory")
+        rows = X.shape[0]
+        po, ko = None, None
+        if order is not None:
+            ko = np.ascontiguousarray(order, dtype=np.int64)
+            if ko.shape != (epochs, rows):
+                raise ValueError("order must be [epochs, rows]")
+            po = ko.ctypes.data
+        hist = np.zeros(max(epochs, 1))
+        _check(lib().mlp_train(self._h, px, pt, rows, int(epochs), po, int(shuffle_seed),
+                               hist.ctypes.data_as(C.POINTER(C.c_double)), mem))
+        return hist[:epochs]
+
+    def close(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h and _lib is not None:
+            _lib.mlp_free(h)
+
+    __del__ = close
+
+
+def gk_tail_features(c_sigma, c_q, volume, temperature, density):
+    """Features [nruns, 132] of the learned tail from per-run readouts
+    c_sigma, c_q [nruns, >= 64] (float32)."""
+    cs = np.ascontiguousarray(np.atleast_2d(c_sigma), dtype=np.float64)
+    cq = np.ascontiguousarray(np.atleast_2d(c_q), dtype=np.float64)
+    if cs.shape != cq.shape:
+        raise ValueError("c_sigma and c_q must have the same shape")
+    nr = cs.shape[0]
+    V, T, rho = (np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), (nr,)))
+                 for a in (volume, temperature, density))
+    out = np.zeros((nr, 132), dtype=np.float32)
+    dp = C.POINTER(C.c_double)
+    _check(lib().gk_tail_features(cs.ctypes.data_as(dp), cq.ctypes.data_as(dp), cs.shape[1], nr,
+                                  V.ctypes.data_as(dp), T.ctypes.data_as(dp), rho.ctypes.data_as(dp), out.ctypes.data))
+    return out

@@ -1,7 +1,8 @@
 """Builds the CUDA library ``libotfmd.so`` in-tree with nvcc for sm_103a.
 
 The translation units are compiled in parallel, then linked into one shared
-library whose exported symbols are the C ABI of ``include/otf_md.h``.
+library whose exported symbols are the C ABI of ``include/otf_md.h`` and
+``include/gk_tail.h``.
 """
 from __future__ import annotations
 
@@ -15,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libotfmd.so")
-SOURCES = ["capi.cu", "corr.cu", "md.cu", "obs_noalloc.cu"]
+SOURCES = ["capi.cu", "corr.cu", "md.cu", "obs_noalloc.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "-I" + INCLUDE, "-I" + CSRC, "--expt-relaxed-constexpr"]
@@ -32,7 +33,8 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "otf_md.h"), __file__]
+    deps = ([os.path.join(CSRC, f) for f in os.listdir(CSRC)] +
+            [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)] + [__file__])
     return any(os.path.getmtime(p) > t for p in deps)
 
 

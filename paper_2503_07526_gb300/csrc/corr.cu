@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "corr.cuh"
+#include "gk_tail.h"
 
 namespace otf {
 
@@ -504,6 +505,55 @@ int corr_read(corr_handle *h, int64_t g, double *times, double *values, int64_t 
   *n = npts;
   if (npts > cap) {
     set_error("corr_read: %lld points need a larger buffer", (long long)npts);
+    return MD_ECAP;
+  }
+  return MD_OK;
+}
+
+int corr_read_rows(corr_handle *h, int64_t g0, int64_t rows, int64_t avg, double *times, double *values,
+                   int64_t cap, int64_t *n) {
+  otf::clear_error();
+  if (!h || !n || rows < 1 || avg < 1) {
+    set_error("corr_read_rows: null argument or rows / avg < 1");
+    return MD_EINVAL;
+  }
+  Correlator &c = h->c;
+  const corr_params &p = c.prm;
+  const int64_t ng = c.dev.ng;
+  if (g0 < 0 || g0 + rows * avg > ng) {
+    set_error("corr_read_rows: groups %lld..%lld out of range (%lld groups)", (long long)g0,
+              (long long)(g0 + rows * avg - 1), (long long)ng);
+    return MD_EINVAL;
+  }
+  std::vector<double> v((size_t)ng * p.b * p.p);
+  int rc = c.fetch(v.data());
+  if (rc) return rc;
+  std::vector<int64_t> cnt;
+  int used = 0;
+  counts_from_pushes(p, c.push_count(), cnt, &used);
+  // the Algorithm 2 grid, as in corr_read, for every row at once
+  int64_t npts = 0;
+  double scale = 1.0;
+  for (int k = 0; k < used; ++k) {
+    if (k > 0) scale *= p.m;
+    const int lo = (k == 0) ? 0 : p.p / p.m;
+    for (int lag = lo; lag < p.p; ++lag) {
+      const int64_t ct = cnt[(size_t)k * p.p + lag];
+      if (ct <= 0) continue;
+      if (npts < cap && times && values) {
+        times[npts] = lag * scale * p.dt_unit;
+        for (int64_t r = 0; r < rows; ++r) {
+          double sum = 0.0;
+          for (int64_t a = 0; a < avg; ++a) sum += v[((size_t)(g0 + r * avg + a) * p.b + k) * p.p + lag];
+          values[r * cap + npts] = sum / (double)avg / ((double)ct * (double)p.group_size);
+        }
+      }
+      ++npts;
+    }
+  }
+  *n = npts;
+  if (npts > cap) {
+    set_error("corr_read_rows: %lld points need a larger buffer", (long long)npts);
     return MD_ECAP;
   }
   return MD_OK;

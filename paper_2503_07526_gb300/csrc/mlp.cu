@@ -1,0 +1,1249 @@
+// Learned Green-Kubo tail: a fully connected network trained and evaluated
+// on the tensor cores (tcgen05.mma with TMEM accumulators, operands staged in
+// shared memory by TMA), with FP32 master weights and Adam.
+//
+// Every product of the forward and backward pass is one launch of k_gemm_tc:
+// D [M x N] = A [M x K] * B [N x K]^T with bfloat16 A and B read K-major
+// (K contiguous) through 128-byte-swizzled TMA tiles, FP32 accumulation in
+// tensor memory, and a fused epilogue (bias, tanh, tanh' from a stored
+// activation, output scaling, bfloat16 and FP32 stores, straight or
+// transposed).  The transposed stores give the K-major copies that the
+// weight-gradient products read (their K is the batch), so no transpose
+// kernel runs.
+//
+// The paper (arXiv 2503.07526) has no learned part; the network, features and
+// training are defined in include/gk_tail.h.  Inputs come from the
+// multiple-tau readout (Sec. 2.2, Appendix D Algorithm 2); targets are the
+// Green-Kubo integrals of Sec. 2.3.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "gk_tail.h"
+
+namespace otf {
+namespace tc {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kBM = 128;     // rows of a CTA tile = MMA M (one TMEM lane per row)
+constexpr int kBK = 64;      // K panel: 64 bfloat16 = one 128-byte swizzle row
+constexpr int kStages = 2;   // TMA panels in flight
+constexpr int kThreads = 128;
+constexpr int kOutPad = 16;  // outputs padded to the smallest MMA N
+constexpr int kMaxLayers = 8;
+constexpr uint64_t kWaitNs = 2000000000ull;  // bounded waits: 2 s of wall time
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t global_timer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase with the given parity to complete; gives up (false)
+// after kWaitNs.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_test(bar, parity)) return true;
+  const uint64_t t0 = global_timer();
+  for (;;) {
+    if (mbar_test(bar, parity)) return true;
+    if (global_timer() - t0 > kWaitNs) return false;
+    __nanosleep(64);
+  }
+}
+// 2-D tiled TMA load of box {64 columns, rows} at (x = column, y = row).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols) : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major operand tile written by TMA
+// with 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart
+// (the stride field); the leading field is unused for this layout.  Bits:
+// start address >> 4 at [0,14), leading offset >> 4 at [16,30), stride
+// offset >> 4 at [32,46), descriptor version 1 at [46,48), swizzle mode
+// (2 = 128 B) at [61,64).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1),
+// bfloat16 A and B (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0),
+// N >> 3 at [17,23), M >> 4 at [24,29).
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// Arrives on the barrier once every MMA this thread issued has completed.
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Fused epilogue of one product.  x = acc; x += bias[n]; x *= 1 - h^2 with
+// h = dact[m][n]; x = tanh(x); x = x * post_scale[n] + post_shift[n]; then
+// every non-null output gets x (bfloat16 outputs round to nearest even).
+struct Epi {
+  const float *bias = nullptr;
+  const bf16 *dact = nullptr;
+  int64_t ld_dact = 0;
+  int act_tanh = 0;
+  const float *post_scale = nullptr, *post_shift = nullptr;
+  int n_store = 0;     // columns written
+  int64_t m_rows = 0;  // rows written
+  bf16 *out_b = nullptr;
+  int64_t ld_b = 0;
+  bf16 *out_bt = nullptr;  // out_bt[n * ld_bt + m]
+  int64_t ld_bt = 0;
+  float *out_f = nullptr;
+  int64_t ld_f = 0;
+  float *out_ft = nullptr;  // out_ft[n * ld_ft + m]
+  int64_t ld_ft = 0;
+};
+
+__host__ __device__ constexpr uint32_t tmem_cols(int N) { return N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256; }
+__host__ __device__ constexpr size_t gemm_smem_need(int N) {
+  return 1024 + (size_t)kStages * ((size_t)kBM * 128 + (size_t)N * 128) + 64;
+}
+
+// One CTA per 128-row tile of D.  Thread 0 issues the TMA loads and the MMAs
+// (two panels in flight); all four warps then read their 32 TMEM lanes and
+// run the epilogue.  K must be a multiple of 16, N a multiple of 16 in
+// [16, 256]; rows and columns of A / B past the tensors' ends read as zero.
+__global__ void __launch_bounds__(kThreads) k_gemm_tc(const __grid_constant__ CUtensorMap ta,
+                                                      const __grid_constant__ CUtensorMap tb, int K, int N,
+                                                      int a_row0, int a_k0, int b_row0, int b_k0, Epi e,
+                                                      unsigned *err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const uint32_t a_bytes = kBM * 128, b_bytes = (uint32_t)N * 128;
+  uint8_t *sa = smem;
+  uint8_t *sb = smem + kStages * a_bytes;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sb + kStages * b_bytes);  // full[S], empty[S], done
+  uint32_t *slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 1);
+  int *flag = reinterpret_cast<int *>(slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t ncols = tmem_cols(N);
+  const uint32_t done_bar = smem_u32(&bars[2 * kStages]);
+
+  if (tid == 0) {
+    for (int s = 0; s < 2 * kStages + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    *flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(smem_u32(slot), ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  const int m0 = blockIdx.x * kBM;
+
+  if (tid == 0) {
+    const int np = (K + kBK - 1) / kBK;
+    const uint32_t idesc = idesc_bf16(kBM, N);
+    int issued = 0, consumed = 0;
+    bool ok = true;
+    auto load = [&](int p, int s) {
+      const uint32_t fb = smem_u32(&bars[s]);
+      mbar_expect_tx(fb, a_bytes + b_bytes);
+      tma_load_2d(smem_u32(sa + s * a_bytes), &ta, a_k0 + p * kBK, a_row0 + m0, fb);
+      tma_load_2d(smem_u32(sb + s * b_bytes), &tb, b_k0 + p * kBK, b_row0, fb);
+      ++issued;
+    };
+    for (int p = 0; p < np && p < kStages; ++p) load(p, p);
+    for (int p = 0; p < np; ++p) {
+      const int s = p % kStages;
+      const uint32_t ph = (uint32_t)(p / kStages) & 1u;
+      if (!mbar_wait(smem_u32(&bars[s]), ph)) {
+        ok = false;
+        break;
+      }
+      ++consumed;
+      tc_fence_after();
+      const int nk = min(kBK, K - p * kBK) / 16;
+      const uint32_t a0 = smem_u32(sa + s * a_bytes), b0 = smem_u32(sb + s * b_bytes);
+      for (int j = 0; j < nk; ++j)
+        mma_bf16(tmem, sw128_desc(a0 + 32u * j), sw128_desc(b0 + 32u * j), idesc, (p | j) != 0);
+      mma_commit(smem_u32(&bars[kStages + s]));
+      if (p + kStages < np) {
+        if (!mbar_wait(smem_u32(&bars[kStages + s]), ph)) {
+          ok = false;
+          break;
+        }
+        load(p + kStages, s);
+      }
+    }
+    mma_commit(done_bar);
+    if (!ok) {
+      // let the copies already issued land before the CTA exits
+      for (int p = consumed; p < issued; ++p) mbar_wait(smem_u32(&bars[p % kStages]), (uint32_t)(p / kStages) & 1u);
+      *flag = 1;
+    }
+  }
+  const bool done_ok = mbar_wait(done_bar, 0);
+  tc_fence_after();
+  __syncthreads();
+  const bool run = done_ok && *flag == 0;
+  if (!run && tid == 0) atomicOr(err, 1u);
+
+  if (run) {
+    const int row = warp * 32 + lane;
+    const int64_t m = (int64_t)m0 + row;
+    const bool live = m < e.m_rows;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      float v[16];
+      tmem_ld16(trow + (uint32_t)c0, v);  // warp-collective: every lane loads
+      if (!live) continue;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int n = c0 + i;
+        if (n >= e.n_store) break;
+        float x = v[i];
+        if (e.bias) x += e.bias[n];
+        if (e.dact) {
+          const float h = __bfloat162float(e.dact[m * e.ld_dact + n]);
+          x *= 1.0f - h * h;
+        }
+        if (e.act_tanh) x = tanhf(x);
+        if (e.post_scale) x = fmaf(x, e.post_scale[n], e.post_shift[n]);
+        if (e.out_f) e.out_f[m * e.ld_f + n] = x;
+        if (e.out_ft) e.out_ft[(int64_t)n * e.ld_ft + m] = x;
+        const bf16 xb = __float2bfloat16_rn(x);
+        if (e.out_b) e.out_b[m * e.ld_b + n] = xb;
+        if (e.out_bt) e.out_bt[(int64_t)n * e.ld_bt + m] = xb;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+// Standardised, bfloat16-rounded inputs: out [rows_pad][k] row-major and
+// (optional) out_t [k][ld_t]; pad columns and rows past `rows` are zero.
+__global__ void k_prep_x(const float *__restrict__ X, int64_t rows, int n_in, const float *__restrict__ mean,
+                         const float *__restrict__ stdv, bf16 *__restrict__ out, int64_t rows_pad, int k,
+                         bf16 *__restrict__ out_t, int64_t ld_t) {
+  const int64_t total = rows_pad * k;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = i / k;
+    const int c = (int)(i % k);
+    float x = 0.f;
+    if (m < rows && c < n_in) x = (X[m * n_in + c] - mean[c]) / stdv[c];
+    const bf16 xb = __float2bfloat16_rn(x);
+    out[i] = xb;
+    if (out_t) out_t[(int64_t)c * ld_t + m] = xb;
+  }
+}
+
+// Standardised targets.
+__global__ void k_prep_t(const float *__restrict__ T, int64_t rows, int n_out, const float *__restrict__ mean,
+                         const float *__restrict__ stdv, float *__restrict__ out) {
+  const int64_t total = rows * n_out;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % n_out);
+    out[i] = (T[i] - mean[c]) / stdv[c];
+  }
+}
+
+// One epoch's sample order: rows of the prepared inputs and targets gathered
+// into X [n][k], its transpose [k][n], and T [n][n_out].
+__global__ void k_gather(const bf16 *__restrict__ Xall, const float *__restrict__ Tall, const int64_t *__restrict__ perm,
+                         int64_t n, int k, int n_out, bf16 *__restrict__ Xs, bf16 *__restrict__ Xst,
+                         float *__restrict__ Ts) {
+  const int64_t total = n * k;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = i / k;
+    const int c = (int)(i % k);
+    const int64_t src = perm[m];
+    const bf16 x = Xall[src * k + c];
+    Xs[i] = x;
+    Xst[(int64_t)c * n + m] = x;
+    if (c < n_out) Ts[m * n_out + c] = Tall[src * n_out + c];
+  }
+}
+
+// Loss of one batch and the output gradient dY = 2 (y - t) / (rows n_out),
+// bfloat16, into dY [rows][64] and dYt [16][ld_t] (pads stay zero).  One
+// block; the sum runs in a fixed order, so the loss is reproducible.
+// loss_acc[0] += loss * acc_scale; loss_acc[1] = loss.
+__global__ void k_loss_dy(const float *__restrict__ Y, const float *__restrict__ T, int64_t rows, int n_out,
+                          bf16 *__restrict__ dY, bf16 *__restrict__ dYt, int64_t ld_t, double *loss_acc,
+                          double acc_scale) {
+  __shared__ double part[256];
+  const double inv = 1.0 / ((double)rows * n_out);
+  const float g = (float)(2.0 * inv);
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < rows * n_out; i += blockDim.x) {
+    const int64_t m = i / n_out;
+    const int c = (int)(i % n_out);
+    const float d = Y[m * kOutPad + c] - T[i];
+    acc += (double)d * d;
+    const bf16 db = __float2bfloat16_rn(g * d);
+    dY[m * 64 + c] = db;
+    dYt[(int64_t)c * ld_t + m] = db;
+  }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double L = part[0] * inv;
+    loss_acc[0] += L * acc_scale;
+    loss_acc[1] = L;
+  }
+}
+
+// Bias gradients: dst_l[n] = sum over m < rows of src_l[n][m] (bfloat16 dZ^T
+// rows), one warp per (layer, n), fixed summation order.
+struct BiasJob {
+  const bf16 *src;
+  int64_t ld;
+  float *dst;
+  int count;
+};
+struct BiasJobs {
+  BiasJob j[kMaxLayers];
+  int n;
+};
+__global__ void k_bias_grad(BiasJobs jobs, int64_t rows) {
+  const BiasJob &J = jobs.j[blockIdx.y];
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= J.count) return;
+  const bf16 *s = J.src + (int64_t)w * J.ld;
+  float acc = 0.f;
+  for (int64_t m = lane; m < rows; m += 32) acc += __bfloat162float(s[m]);
+  acc = warp_sum(acc);
+  if (lane == 0) J.dst[w] = acc;
+}
+
+// Adam with bias correction (c1 = 1 - beta1^t, c2 = 1 - beta2^t) and
+// decoupled weight decay on weight matrices, over the padded parameter
+// vector; refreshes the bfloat16 copies W [out_p][in_k] and (when present)
+// W^T [in_k][ld_t].
+struct AdamLayer {
+  int64_t w_off, b_off;
+  int out_p, in_k;
+  bf16 *wb, *wtb;
+  int ld_t;
+};
+struct AdamTable {
+  AdamLayer l[kMaxLayers];
+  int n;
+};
+__global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m1,
+                       float *__restrict__ m2, int64_t count, AdamTable tab, float lr, float beta1, float beta2,
+                       float eps, float wd, float c1, float c2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    int L = 0;
+    bool is_w = false;
+    for (int l = 0; l < tab.n; ++l) {
+      const AdamLayer &A = tab.l[l];
+      if (i >= A.w_off && i < A.w_off + (int64_t)A.out_p * A.in_k) {
+        L = l;
+        is_w = true;
+      }
+      if (i >= A.b_off && i < A.b_off + A.out_p) L = l;
+    }
+    const float gi = g[i];
+    const float a = beta1 * m1[i] + (1.f - beta1) * gi;
+    const float b = beta2 * m2[i] + (1.f - beta2) * gi * gi;
+    m1[i] = a;
+    m2[i] = b;
+    float step = (a / c1) / (sqrtf(b / c2) + eps);
+    if (is_w) step += wd * w[i];
+    const float wn = w[i] - lr * step;
+    w[i] = wn;
+    if (is_w) {
+      const AdamLayer &A = tab.l[L];
+      const int64_t j = i - A.w_off;
+      const int o = (int)(j / A.in_k), c = (int)(j % A.in_k);
+      const bf16 wbv = __float2bfloat16_rn(wn);
+      A.wb[j] = wbv;
+      if (A.wtb) A.wtb[(int64_t)c * A.ld_t + o] = wbv;
+    }
+  }
+}
+
+// bfloat16 copies of the master weights (after set / init).
+__global__ void k_cast_weights(const float *__restrict__ w, AdamTable tab) {
+  const AdamLayer &A = tab.l[blockIdx.y];
+  const int64_t n = (int64_t)A.out_p * A.in_k;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int o = (int)(j / A.in_k), c = (int)(j % A.in_k);
+    const bf16 v = __float2bfloat16_rn(w[A.w_off + j]);
+    A.wb[j] = v;
+    if (A.wtb) A.wtb[(int64_t)c * A.ld_t + o] = v;
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Tensor map of a row-major bfloat16 matrix [outer][inner], read in boxes of
+// 64 columns x box_rows rows with 128-byte swizzle.
+int make_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer, uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return MD_ECUDA;
+  }
+  if (inner % 8 || inner < 64 || box_rows < 1 || box_rows > 256) {
+    set_error("tensor map: inner extent %llu / box rows %u not supported", (unsigned long long)inner, box_rows);
+    return MD_EINVAL;
+  }
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * sizeof(bf16)};
+  cuuint32_t box[2] = {(cuuint32_t)kBK, box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return MD_ECUDA;
+  }
+  return MD_OK;
+}
+
+struct Mat {  // a bfloat16 device matrix with its tensor map
+  bf16 *p = nullptr;
+  int64_t rows = 0, cols = 0;
+  CUtensorMap map;  // the type carries the alignment the driver needs
+};
+
+int mat_alloc(Mat &M, int64_t rows, int64_t cols, uint32_t box_rows) {
+  M.rows = rows;
+  M.cols = cols;
+  OTF_CUDA(cudaMalloc(&M.p, sizeof(bf16) * rows * cols));
+  OTF_CUDA(cudaMemset(M.p, 0, sizeof(bf16) * rows * cols));
+  return make_map(&M.map, M.p, (uint64_t)cols, (uint64_t)rows, box_rows);
+}
+void mat_free(Mat &M) {
+  if (M.p) cudaFree(M.p);
+  M.p = nullptr;
+}
+
+int launch_gemm(cudaStream_t st, const Mat &A, int a_row0, int a_k0, const Mat &B, int b_row0, int b_k0, int64_t M,
+                int N, int K, const Epi &e, unsigned *err) {
+  if (N % 16 || N < 16 || N > 256 || K % 16 || K < 16) {
+    set_error("k_gemm_tc: N = %d, K = %d not supported", N, K);
+    return MD_EINVAL;
+  }
+  size_t smem = gemm_smem_need(N);
+  // at most two CTAs of 256 TMEM columns per SM (512 columns in all)
+  if (tmem_cols(N) == 256) smem = std::max<size_t>(smem, 80 * 1024);
+  static std::once_flag once;
+  static cudaError_t attr_rc = cudaSuccess;
+  std::call_once(once, [] {
+    attr_rc = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  });
+  OTF_CUDA(attr_rc);
+  const int grid = ceil_div(M, kBM);
+  k_gemm_tc<<<grid, kThreads, smem, st>>>(A.map, B.map, K, N, a_row0, a_k0, b_row0, b_k0, e, err);
+  OTF_LAUNCH_CHECK();
+  return MD_OK;
+}
+
+// SplitMix64 (Steele, Lea and Flood 2014): output k (k >= 1) of the stream
+// with the given seed, and a uniform double in [0, 1) from its top 53 bits.
+uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + k * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+double uniform01_at(uint64_t seed, uint64_t k) { return (double)(splitmix64_at(seed, k) >> 11) * (1.0 / 9007199254740992.0); }
+
+}  // namespace tc
+}  // namespace otf
+
+using namespace otf;
+using namespace otf::tc;
+
+struct mlp_handle_s {
+  cudaStream_t st = nullptr;
+  mlp_params p{};
+  int L = 0;          // layers = depth + 1
+  int k_in = 0;       // padded input width
+  int cap = 0;        // training batch rows
+  struct Layer {
+    int in = 0, out = 0, in_k = 0, out_p = 0;
+    int64_t w_off = 0, b_off = 0;  // into the padded parameter vector
+    Mat wb, wtb;                   // bfloat16 W [out_p][in_k], W^T [in_k][out_p or 64]
+  };
+  std::vector<Layer> lay;
+  int64_t np_pad = 0, np_flat = 0;
+  float *w = nullptr, *g = nullptr, *m1 = nullptr, *m2 = nullptr;
+  int64_t t = 0;  // Adam steps taken
+  float *xmean = nullptr, *xstd = nullptr, *ymean = nullptr, *ystd = nullptr;  // device scaler
+  std::vector<float> h_xmean, h_xstd, h_ymean, h_ystd;
+  // training batch state
+  Mat xb, xbt;              // [cap][k_in], [k_in][cap]
+  std::vector<Mat> H, Ht;   // per hidden layer: [cap][width], [width][cap]
+  std::vector<Mat> dZ, dZt; // per hidden layer
+  Mat dY, dYt;              // [cap][64], [16][cap]
+  float *Y = nullptr;       // [cap][16]
+  float *T = nullptr;       // [cap][n_out]
+  double *loss = nullptr;   // [2]
+  unsigned *err = nullptr;
+  // inference state (grown on demand)
+  int64_t icap = 0;
+  Mat xi;
+  Mat hi[2];
+  float *Yi = nullptr;
+  AdamTable table{};
+};
+
+namespace {
+
+int check_err(mlp_handle *h) {
+  unsigned e = 0;
+  OTF_CUDA(cudaMemcpyAsync(&e, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
+  OTF_CUDA(cudaStreamSynchronize(h->st));
+  if (e) {
+    cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->st);
+    set_error("a bounded tensor-core pipeline wait gave up");
+    return MD_ETIMEOUT;
+  }
+  return MD_OK;
+}
+
+int upload_scaler(mlp_handle *h) {
+  std::vector<float> ym(kOutPad, 0.f), ys(kOutPad, 1.f);
+  std::copy(h->h_ymean.begin(), h->h_ymean.end(), ym.begin());
+  std::copy(h->h_ystd.begin(), h->h_ystd.end(), ys.begin());
+  OTF_CUDA(cudaMemcpyAsync(h->xmean, h->h_xmean.data(), sizeof(float) * h->p.n_in, cudaMemcpyHostToDevice, h->st));
+  OTF_CUDA(cudaMemcpyAsync(h->xstd, h->h_xstd.data(), sizeof(float) * h->p.n_in, cudaMemcpyHostToDevice, h->st));
+  OTF_CUDA(cudaMemcpyAsync(h->ymean, ym.data(), sizeof(float) * kOutPad, cudaMemcpyHostToDevice, h->st));
+  OTF_CUDA(cudaMemcpyAsync(h->ystd, ys.data(), sizeof(float) * kOutPad, cudaMemcpyHostToDevice, h->st));
+  OTF_CUDA(cudaStreamSynchronize(h->st));
+  return MD_OK;
+}
+
+int cast_weights(mlp_handle *h) {
+  dim3 grid(64, h->L);
+  k_cast_weights<<<grid, 256, 0, h->st>>>(h->w, h->table);
+  OTF_LAUNCH_CHECK();
+  return MD_OK;
+}
+
+// flat (unpadded, API order) <-> padded device layout, on the host
+void flat_to_pad(const mlp_handle *h, const float *flat, std::vector<float> &pad) {
+  pad.assign((size_t)h->np_pad, 0.f);
+  int64_t f = 0;
+  for (const auto &Ly : h->lay) {
+    for (int o = 0; o < Ly.out; ++o)
+      for (int i = 0; i < Ly.in; ++i) pad[(size_t)(Ly.w_off + (int64_t)o * Ly.in_k + i)] = flat[f++];
+    for (int o = 0; o < Ly.out; ++o) pad[(size_t)(Ly.b_off + o)] = flat[f++];
+  }
+}
+void pad_to_flat(const mlp_handle *h, const std::vector<float> &pad, float *flat) {
+  int64_t f = 0;
+  for (const auto &Ly : h->lay) {
+    for (int o = 0; o < Ly.out; ++o)
+      for (int i = 0; i < Ly.in; ++i) flat[f++] = pad[(size_t)(Ly.w_off + (int64_t)o * Ly.in_k + i)];
+    for (int o = 0; o < Ly.out; ++o) flat[f++] = pad[(size_t)(Ly.b_off + o)];
+  }
+}
+
+int reset_adam(mlp_handle *h) {
+  OTF_CUDA(cudaMemsetAsync(h->m1, 0, sizeof(float) * h->np_pad, h->st));
+  OTF_CUDA(cudaMemsetAsync(h->m2, 0, sizeof(float) * h->np_pad, h->st));
+  h->t = 0;
+  return MD_OK;
+}
+
+// Forward pass of `rows` rows whose prepared inputs are rows [row0, row0+rows)
+// of X.  Hidden activations go to Hs (ping-pong when Hs has 2 entries and no
+// transposes are kept), the output to Y [.][16].
+int forward(mlp_handle *h, const Mat &X, int row0, int64_t rows, Mat *Hs, int nH, Mat *Hts, float *Y,
+            bool unscale) {
+  const int L = h->L;
+  for (int l = 0; l < L; ++l) {
+    const auto &Ly = h->lay[l];
+    const Mat &A = (l == 0) ? X : Hs[(l - 1) % nH];
+    Epi e;
+    e.bias = h->w + Ly.b_off;
+    e.m_rows = rows;
+    if (l < L - 1) {
+      Mat &out = Hs[l % nH];
+      e.act_tanh = 1;
+      e.n_store = Ly.out_p;
+      e.out_b = out.p;
+      e.ld_b = out.cols;
+      if (Hts) {
+        e.out_bt = Hts[l].p;
+        e.ld_bt = Hts[l].cols;
+      }
+    } else {
+      e.n_store = kOutPad;
+      e.out_f = Y;
+      e.ld_f = kOutPad;
+      if (unscale) {
+        e.post_scale = h->ystd;
+        e.post_shift = h->ymean;
+      }
+    }
+    int rc = launch_gemm(h->st, A, l == 0 ? row0 : 0, 0, Ly.wb, 0, 0, rows, Ly.out_p, Ly.in_k, e, h->err);
+    if (rc) return rc;
+  }
+  return MD_OK;
+}
+
+// Forward + backward on one batch: inputs rows [row0, row0+cap) of X (with
+// its transpose Xt, K offset row0), standardised targets Tb [cap][n_out].
+// Gradients land in h->g (padded layout).
+int train_step(mlp_handle *h, const Mat &X, const Mat &Xt, int row0, const float *Tb, double acc_scale) {
+  const int L = h->L, cap = h->cap;
+  int rc = forward(h, X, row0, cap, h->H.data(), (int)h->H.size(), h->Ht.data(), h->Y, false);
+  if (rc) return rc;
+  k_loss_dy<<<1, 256, 0, h->st>>>(h->Y, Tb, cap, h->p.n_out, h->dY.p, h->dYt.p, cap, h->loss, acc_scale);
+  OTF_LAUNCH_CHECK();
+  BiasJobs jobs{};
+  jobs.n = L;
+  // output layer: dW^T [in][16] = H^T dY (M = width), stored transposed as dW
+  {
+    const auto &Ly = h->lay[L - 1];
+    Epi e;
+    e.n_store = kOutPad;
+    e.m_rows = Ly.in;
+    e.out_ft = h->g + Ly.w_off;
+    e.ld_ft = Ly.in_k;
+    rc = launch_gemm(h->st, h->Ht[L - 2], 0, 0, h->dYt, 0, 0, Ly.in, kOutPad, cap, e, h->err);
+    if (rc) return rc;
+    jobs.j[L - 1] = BiasJob{h->dYt.p, cap, h->g + Ly.b_off, kOutPad};
+    // dH = dY W, then dZ = dH (1 - H^2) of the last hidden layer
+    Epi d;
+    d.dact = h->H[L - 2].p;
+    d.ld_dact = h->H[L - 2].cols;
+    d.n_store = Ly.in;
+    d.m_rows = cap;
+    d.out_b = h->dZ[L - 2].p;
+    d.ld_b = h->dZ[L - 2].cols;
+    d.out_bt = h->dZt[L - 2].p;
+    d.ld_bt = h->dZt[L - 2].cols;
+    rc = launch_gemm(h->st, h->dY, 0, 0, Ly.wtb, 0, 0, cap, Ly.in, kOutPad, d, h->err);
+    if (rc) return rc;
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    const auto &Ly = h->lay[l];
+    // dW [out][in_k] = dZ^T X_in: A = dZ^T [out][cap], B = X_in^T [in_k][cap]
+    Epi e;
+    e.n_store = Ly.in_k;
+    e.m_rows = Ly.out;
+    e.out_f = h->g + Ly.w_off;
+    e.ld_f = Ly.in_k;
+    const Mat &Bm = (l == 0) ? Xt : h->Ht[l - 1];
+    rc = launch_gemm(h->st, h->dZt[l], 0, 0, Bm, 0, l == 0 ? row0 : 0, Ly.out, Ly.in_k, cap, e, h->err);
+    if (rc) return rc;
+    jobs.j[l] = BiasJob{h->dZt[l].p, cap, h->g + Ly.b_off, Ly.out};
+    if (l > 0) {
+      Epi d;
+      d.dact = h->H[l - 1].p;
+      d.ld_dact = h->H[l - 1].cols;
+      d.n_store = Ly.in;
+      d.m_rows = cap;
+      d.out_b = h->dZ[l - 1].p;
+      d.ld_b = h->dZ[l - 1].cols;
+      d.out_bt = h->dZt[l - 1].p;
+      d.ld_bt = h->dZt[l - 1].cols;
+      rc = launch_gemm(h->st, h->dZ[l], 0, 0, Ly.wtb, 0, 0, cap, Ly.in, Ly.out, d, h->err);
+      if (rc) return rc;
+    }
+  }
+  dim3 grid(ceil_div((int64_t)std::max(h->p.width, kOutPad) * 32, 256), L);
+  k_bias_grad<<<grid, 256, 0, h->st>>>(jobs, cap);
+  OTF_LAUNCH_CHECK();
+  return MD_OK;
+}
+
+int adam_step(mlp_handle *h) {
+  h->t += 1;
+  const double c1 = 1.0 - std::pow((double)h->p.beta1, (double)h->t);
+  const double c2 = 1.0 - std::pow((double)h->p.beta2, (double)h->t);
+  k_adam<<<ceil_div(h->np_pad, 256), 256, 0, h->st>>>(h->w, h->g, h->m1, h->m2, h->np_pad, h->table, h->p.lr,
+                                                       h->p.beta1, h->p.beta2, h->p.eps, h->p.weight_decay,
+                                                       (float)c1, (float)c2);
+  OTF_LAUNCH_CHECK();
+  return MD_OK;
+}
+
+// Copies caller rows (host or device) into a device buffer of `count` floats.
+int to_device(mlp_handle *h, const float *src, int64_t count, int32_t mem, float **dst_owned, const float **dst) {
+  if (mem == MD_MEM_DEVICE) {
+    *dst = src;
+    *dst_owned = nullptr;
+    return MD_OK;
+  }
+  if (mem != MD_MEM_HOST) {
+    set_error("mem must be MD_MEM_HOST or MD_MEM_DEVICE");
+    return MD_EINVAL;
+  }
+  OTF_CUDA(cudaMalloc(dst_owned, sizeof(float) * std::max<int64_t>(count, 1)));
+  OTF_CUDA(cudaMemcpyAsync(*dst_owned, src, sizeof(float) * count, cudaMemcpyHostToDevice, h->st));
+  *dst = *dst_owned;
+  return MD_OK;
+}
+
+int grow_inference(mlp_handle *h, int64_t rows) {
+  const int64_t need = ((rows + kBM - 1) / kBM) * kBM;
+  if (need <= h->icap) return MD_OK;
+  mat_free(h->xi);
+  mat_free(h->hi[0]);
+  mat_free(h->hi[1]);
+  if (h->Yi) cudaFree(h->Yi);
+  h->Yi = nullptr;
+  h->icap = 0;
+  int rc = mat_alloc(h->xi, need, h->k_in, kBM);
+  if (!rc) rc = mat_alloc(h->hi[0], need, h->p.width, kBM);
+  if (!rc) rc = mat_alloc(h->hi[1], need, h->p.width, kBM);
+  if (rc) return rc;
+  OTF_CUDA(cudaMalloc(&h->Yi, sizeof(float) * need * kOutPad));
+  h->icap = need;
+  return MD_OK;
+}
+
+void destroy(mlp_handle *h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  for (auto &Ly : h->lay) {
+    mat_free(Ly.wb);
+    mat_free(Ly.wtb);
+  }
+  for (auto *v : {&h->H, &h->Ht, &h->dZ, &h->dZt})
+    for (auto &M : *v) mat_free(M);
+  mat_free(h->xb);
+  mat_free(h->xbt);
+  mat_free(h->dY);
+  mat_free(h->dYt);
+  mat_free(h->xi);
+  mat_free(h->hi[0]);
+  mat_free(h->hi[1]);
+  for (void *q : {(void *)h->w, (void *)h->g, (void *)h->m1, (void *)h->m2, (void *)h->xmean, (void *)h->xstd,
+                  (void *)h->ymean, (void *)h->ystd, (void *)h->Y, (void *)h->T, (void *)h->loss, (void *)h->err,
+                  (void *)h->Yi})
+    if (q) cudaFree(q);
+  delete h;
+}
+
+int create_impl(mlp_handle *h) {
+  const mlp_params &p = h->p;
+  h->L = p.depth + 1;
+  h->k_in = std::max(64, (p.n_in + 15) / 16 * 16);
+  h->cap = p.batch;
+  h->lay.resize(h->L);
+  int64_t off = 0, flat = 0;
+  for (int l = 0; l < h->L; ++l) {
+    auto &Ly = h->lay[l];
+    Ly.in = l == 0 ? p.n_in : p.width;
+    Ly.in_k = l == 0 ? h->k_in : p.width;
+    Ly.out = l == h->L - 1 ? p.n_out : p.width;
+    Ly.out_p = l == h->L - 1 ? kOutPad : p.width;
+    Ly.w_off = off;
+    off += (int64_t)Ly.out_p * Ly.in_k;
+    Ly.b_off = off;
+    off += Ly.out_p;
+    flat += (int64_t)Ly.out * Ly.in + Ly.out;
+    int rc = mat_alloc(Ly.wb, Ly.out_p, Ly.in_k, (uint32_t)Ly.out_p);
+    if (rc) return rc;
+    if (l > 0) {  // W^T feeds dH = dZ W; the output layer's is padded to 64 columns
+      rc = mat_alloc(Ly.wtb, Ly.in_k, l == h->L - 1 ? 64 : Ly.out_p, (uint32_t)Ly.in_k);
+      if (rc) return rc;
+    }
+    h->table.l[l] = AdamLayer{Ly.w_off, Ly.b_off, Ly.out_p, Ly.in_k, Ly.wb.p, Ly.wtb.p, (int)Ly.wtb.cols};
+  }
+  h->table.n = h->L;
+  h->np_pad = off;
+  h->np_flat = flat;
+  for (float **q : {&h->w, &h->g, &h->m1, &h->m2}) {
+    OTF_CUDA(cudaMalloc(q, sizeof(float) * off));
+    OTF_CUDA(cudaMemset(*q, 0, sizeof(float) * off));
+  }
+  OTF_CUDA(cudaMalloc(&h->xmean, sizeof(float) * p.n_in));
+  OTF_CUDA(cudaMalloc(&h->xstd, sizeof(float) * p.n_in));
+  OTF_CUDA(cudaMalloc(&h->ymean, sizeof(float) * kOutPad));
+  OTF_CUDA(cudaMalloc(&h->ystd, sizeof(float) * kOutPad));
+  h->h_xmean.assign(p.n_in, 0.f);
+  h->h_xstd.assign(p.n_in, 1.f);
+  h->h_ymean.assign(p.n_out, 0.f);
+  h->h_ystd.assign(p.n_out, 1.f);
+  int rc = upload_scaler(h);
+  if (rc) return rc;
+  // Glorot-uniform weights from SplitMix64: layer l draws stream seed*1000 + 2l
+  std::vector<float> flatv((size_t)flat);
+  int64_t f = 0;
+  for (int l = 0; l < h->L; ++l) {
+    const auto &Ly = h->lay[l];
+    const double lim = std::sqrt(6.0 / (Ly.in + Ly.out));
+    const uint64_t s = p.seed * 1000ull + 2ull * l;
+    for (int64_t k = 0; k < (int64_t)Ly.out * Ly.in; ++k)
+      flatv[(size_t)f++] = (float)((2.0 * uniform01_at(s, (uint64_t)k + 1) - 1.0) * lim);
+    for (int o = 0; o < Ly.out; ++o) flatv[(size_t)f++] = 0.f;
+  }
+  std::vector<float> pad;
+  flat_to_pad(h, flatv.data(), pad);
+  OTF_CUDA(cudaMemcpyAsync(h->w, pad.data(), sizeof(float) * off, cudaMemcpyHostToDevice, h->st));
+  OTF_CUDA(cudaStreamSynchronize(h->st));
+  rc = cast_weights(h);
+  if (rc) return rc;
+  // training batch buffers
+  const int cap = h->cap, nh = p.depth;
+  rc = mat_alloc(h->xb, cap, h->k_in, kBM);
+  if (!rc) rc = mat_alloc(h->xbt, h->k_in, cap, (uint32_t)h->k_in);
+  if (rc) return rc;
+  h->H.resize(nh);
+  h->Ht.resize(nh);
+  h->dZ.resize(nh);
+  h->dZt.resize(nh);
+  for (int l = 0; l < nh; ++l) {
+    rc = mat_alloc(h->H[l], cap, p.width, kBM);
+    if (!rc) rc = mat_alloc(h->Ht[l], p.width, cap, (uint32_t)p.width);  // A of dW_out (box 128) / B of dW
+    if (!rc) rc = mat_alloc(h->dZ[l], cap, p.width, kBM);
+    if (!rc) rc = mat_alloc(h->dZt[l], p.width, cap, kBM);
+    if (rc) return rc;
+  }
+  rc = mat_alloc(h->dY, cap, 64, kBM);
+  if (!rc) rc = mat_alloc(h->dYt, kOutPad, cap, kOutPad);
+  if (rc) return rc;
+  OTF_CUDA(cudaMalloc(&h->Y, sizeof(float) * cap * kOutPad));
+  OTF_CUDA(cudaMalloc(&h->T, sizeof(float) * cap * p.n_out));
+  OTF_CUDA(cudaMalloc(&h->loss, sizeof(double) * 2));
+  OTF_CUDA(cudaMemset(h->loss, 0, sizeof(double) * 2));
+  OTF_CUDA(cudaMalloc(&h->err, sizeof(unsigned)));
+  OTF_CUDA(cudaMemset(h->err, 0, sizeof(unsigned)));
+  OTF_CUDA(cudaDeviceSynchronize());
+  return MD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mlp_create(const mlp_params *p, void *cuda_stream, mlp_handle **out) {
+  clear_error();
+  if (!p || !out) {
+    set_error("mlp_create: null argument");
+    return MD_EINVAL;
+  }
+  *out = nullptr;
+  if (p->n_in < 1 || p->n_in > 240 || p->width != 128 || p->depth < 1 || p->depth > kMaxLayers - 2 ||
+      p->n_out < 1 || p->n_out > kOutPad || p->batch < kBM || p->batch % kBM || p->batch > 4096) {
+    set_error("mlp_create: need 1 <= n_in <= 240, width = 128, 1 <= depth <= 6, 1 <= n_out <= 16 and a batch "
+              "that is a multiple of 128 up to 4096");
+    return MD_EINVAL;
+  }
+  if (!(p->lr > 0) || !(p->beta1 >= 0 && p->beta1 < 1) || !(p->beta2 >= 0 && p->beta2 < 1) || !(p->eps > 0) ||
+      !(p->weight_decay >= 0)) {
+    set_error("mlp_create: Adam needs lr > 0, 0 <= beta < 1, eps > 0, weight_decay >= 0");
+    return MD_EINVAL;
+  }
+  mlp_handle *h = new (std::nothrow) mlp_handle_s;
+  if (!h) return MD_ENOMEM;
+  h->p = *p;
+  h->st = (cudaStream_t)cuda_stream;
+  int rc = create_impl(h);
+  if (rc) {
+    destroy(h);
+    return rc;
+  }
+  *out = h;
+  return MD_OK;
+}
+
+int mlp_param_count(const mlp_handle *h, int64_t *count) {
+  if (!h || !count) return MD_EINVAL;
+  *count = h->np_flat;
+  return MD_OK;
+}
+
+int mlp_get_params(mlp_handle *h, float *flat, int64_t count, int32_t mem) {
+  clear_error();
+  if (!h || !flat || count != h->np_flat) {
+    set_error("mlp_get_params: null argument or count != %lld", h ? (long long)h->np_flat : 0LL);
+    return MD_EINVAL;
+  }
+  std::vector<float> pad((size_t)h->np_pad), f((size_t)count);
+  OTF_CUDA(cudaMemcpyAsync(pad.data(), h->w, sizeof(float) * h->np_pad, cudaMemcpyDeviceToHost, h->st));
+  OTF_CUDA(cudaStreamSynchronize(h->st));
+  pad_to_flat(h, pad, f.data());
+  if (mem == MD_MEM_HOST) {
+    std::memcpy(flat, f.data(), sizeof(float) * count);
+  } else {
+    OTF_CUDA(cudaMemcpyAsync(flat, f.data(), sizeof(float) * count, cudaMemcpyHostToDevice, h->st));
+    OTF_CUDA(cudaStreamSynchronize(h->st));
+  }
+  return MD_OK;
+}
+
+int mlp_set_params(mlp_handle *h, const float *flat, int64_t count, int32_t mem) {
+  clear_error();
+  if (!h || !flat || count != h->np_flat) {
+    set_error("mlp_set_params: null argument or count != %lld", h ? (long long)h->np_flat : 0LL);
+    return MD_EINVAL;
+  }
+  std::vector<float> f((size_t)count), pad;
+  if (mem == MD_MEM_HOST) {
+    std::memcpy(f.data(), flat, sizeof(float) * count);
+  } else {
+    OTF_CUDA(cudaMemcpyAsync(f.data(), flat, sizeof(float) * count, cudaMemcpyDeviceToHost, h->st));
+    OTF_CUDA(cudaStreamSynchronize(h->st));
+  }
+  flat_to_pad(h, f.data(), pad);
+  OTF_CUDA(cudaMemcpyAsync(h->w, pad.data(), sizeof(float) * h->np_pad, cudaMemcpyHostToDevice, h->st));
+  OTF_CUDA(cudaStreamSynchronize(h->st));
+  int rc = reset_adam(h);
+  if (!rc) rc = cast_weights(h);
+  if (!rc) {
+    OTF_CUDA(cudaStreamSynchronize(h->st));
+  }
+  return rc;
+}
+
+int mlp_set_scaler(mlp_handle *h, const float *x_mean, const float *x_std, const float *y_mean, const float *y_std) {
+  clear_error();
+  if (!h || !x_mean || !x_std || !y_mean || !y_std) {
+    set_error("mlp_set_scaler: null argument");
+    return MD_EINVAL;
+  }
+  for (int i = 0; i < h->p.n_in; ++i)
+    if (!(x_std[i] > 0)) {
+      set_error("mlp_set_scaler: x_std[%d] is not positive", i);
+      return MD_EINVAL;
+    }
+  for (int i = 0; i < h->p.n_out; ++i)
+    if (!(y_std[i] > 0)) {
+      set_error("mlp_set_scaler: y_std[%d] is not positive", i);
+      return MD_EINVAL;
+    }
+  h->h_xmean.assign(x_mean, x_mean + h->p.n_in);
+  h->h_xstd.assign(x_std, x_std + h->p.n_in);
+  h->h_ymean.assign(y_mean, y_mean + h->p.n_out);
+  h->h_ystd.assign(y_std, y_std + h->p.n_out);
+  return upload_scaler(h);
+}
+
+int mlp_fit_scaler(mlp_handle *h, const float *X, const float *T, int64_t rows) {
+  clear_error();
+  if (!h || !X || !T || rows < 1) {
+    set_error("mlp_fit_scaler: null argument or rows < 1");
+    return MD_EINVAL;
+  }
+  auto stats = [&](const float *A, int cols, std::vector<float> &mean, std::vector<float> &sd) {
+    mean.assign(cols, 0.f);
+    sd.assign(cols, 1.f);
+    for (int c = 0; c < cols; ++c) {
+      double s = 0.0, s2 = 0.0;
+      for (int64_t r = 0; r < rows; ++r) s += A[r * cols + c];
+      const double mu = s / rows;
+      for (int64_t r = 0; r < rows; ++r) {
+        const double d = A[r * cols + c] - mu;
+        s2 += d * d;
+      }
+      const double v = std::sqrt(s2 / rows);
+      mean[c] = (float)mu;
+      sd[c] = v > 0 ? (float)v : 1.f;
+    }
+  };
+  stats(X, h->p.n_in, h->h_xmean, h->h_xstd);
+  stats(T, h->p.n_out, h->h_ymean, h->h_ystd);
+  return upload_scaler(h);
+}
+
+int mlp_forward(mlp_handle *h, const float *X, int64_t rows, float *Y, int32_t mem) {
+  clear_error();
+  if (!h || !X || !Y || rows < 1) {
+    set_error("mlp_forward: null argument or rows < 1");
+    return MD_EINVAL;
+  }
+  const int64_t chunk = 4096;
+  int rc = grow_inference(h, std::min(rows, chunk));
+  if (rc) return rc;
+  float *own = nullptr;
+  const float *dX = nullptr;
+  rc = to_device(h, X, rows * h->p.n_in, mem, &own, &dX);
+  if (rc) return rc;
+  for (int64_t r0 = 0; r0 < rows && !rc; r0 += chunk) {
+    const int64_t n = std::min(chunk, rows - r0);
+    const int64_t npad = (n + kBM - 1) / kBM * kBM;
+    k_prep_x<<<std::min<int64_t>(1024, ceil_div(npad * h->k_in, 256)), 256, 0, h->st>>>(
+        dX + r0 * h->p.n_in, n, h->p.n_in, h->xmean, h->xstd, h->xi.p, npad, h->k_in, nullptr, 0);
+    if (cudaGetLastError() != cudaSuccess) {
+      rc = MD_ECUDA;
+      set_error("k_prep_x launch failed");
+      break;
+    }
+    rc = forward(h, h->xi, 0, n, h->hi, 2, nullptr, h->Yi, true);
+    if (rc) break;
+    const cudaMemcpyKind kind = mem == MD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (cudaMemcpy2DAsync(Y + r0 * h->p.n_out, sizeof(float) * h->p.n_out, h->Yi, sizeof(float) * kOutPad,
+                          sizeof(float) * h->p.n_out, n, kind, h->st) != cudaSuccess) {
+      rc = MD_ECUDA;
+      set_error("mlp_forward: output copy failed");
+    }
+  }
+  if (!rc) rc = check_err(h);
+  cudaStreamSynchronize(h->st);
+  if (own) cudaFree(own);
+  return rc;
+}
+
+int mlp_loss_grad(mlp_handle *h, const float *X, const float *T, int64_t rows, double *loss, float *grad,
+                  int32_t mem) {
+  clear_error();
+  if (!h || !X || !T || rows != h->cap) {
+    set_error("mlp_loss_grad: null argument or rows != batch (%d)", h ? h->cap : 0);
+    return MD_EINVAL;
+  }
+  float *ox = nullptr, *ot = nullptr;
+  const float *dX = nullptr, *dT = nullptr;
+  int rc = to_device(h, X, rows * h->p.n_in, mem, &ox, &dX);
+  if (!rc) rc = to_device(h, T, rows * h->p.n_out, mem, &ot, &dT);
+  if (!rc) {
+    k_prep_x<<<std::min<int64_t>(1024, ceil_div(rows * h->k_in, 256)), 256, 0, h->st>>>(
+        dX, rows, h->p.n_in, h->xmean, h->xstd, h->xb.p, rows, h->k_in, h->xbt.p, h->xbt.cols);
+    k_prep_t<<<ceil_div(rows * h->p.n_out, 256), 256, 0, h->st>>>(dT, rows, h->p.n_out, h->ymean, h->ystd, h->T);
+    if (cudaGetLastError() != cudaSuccess) {
+      set_error("input preparation launch failed");
+      rc = MD_ECUDA;
+    }
+  }
+  if (!rc) rc = train_step(h, h->xb, h->xbt, 0, h->T, 0.0);
+  double lv[2] = {0, 0};
+  if (!rc && cudaMemcpyAsync(lv, h->loss, sizeof(lv), cudaMemcpyDeviceToHost, h->st) != cudaSuccess) rc = MD_ECUDA;
+  if (!rc) rc = check_err(h);
+  if (!rc && loss) *loss = lv[1];
+  if (!rc && grad) {
+    std::vector<float> pad((size_t)h->np_pad), f((size_t)h->np_flat);
+    if (cudaMemcpyAsync(pad.data(), h->g, sizeof(float) * h->np_pad, cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
+        cudaStreamSynchronize(h->st) != cudaSuccess) {
+      rc = MD_ECUDA;
+    } else {
+      pad_to_flat(h, pad, f.data());
+      if (mem == MD_MEM_HOST)
+        std::memcpy(grad, f.data(), sizeof(float) * h->np_flat);
+      else if (cudaMemcpy(grad, f.data(), sizeof(float) * h->np_flat, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = MD_ECUDA;
+    }
+  }
+  cudaStreamSynchronize(h->st);
+  if (ox) cudaFree(ox);
+  if (ot) cudaFree(ot);
+  if (rc == MD_ECUDA && !md_last_error()[0]) set_error("mlp_loss_grad: CUDA call failed");
+  return rc;
+}
+
+int mlp_adam_step(mlp_handle *h, const float *grad, int32_t mem) {
+  clear_error();
+  if (!h) return MD_EINVAL;
+  if (grad) {
+    std::vector<float> f((size_t)h->np_flat), pad;
+    if (mem == MD_MEM_HOST) {
+      std::memcpy(f.data(), grad, sizeof(float) * h->np_flat);
+    } else {
+      OTF_CUDA(cudaMemcpyAsync(f.data(), grad, sizeof(float) * h->np_flat, cudaMemcpyDeviceToHost, h->st));
+      OTF_CUDA(cudaStreamSynchronize(h->st));
+    }
+    flat_to_pad(h, f.data(), pad);
+    OTF_CUDA(cudaMemcpyAsync(h->g, pad.data(), sizeof(float) * h->np_pad, cudaMemcpyHostToDevice, h->st));
+  }
+  int rc = adam_step(h);
+  if (!rc) {
+    OTF_CUDA(cudaStreamSynchronize(h->st));
+  }
+  return rc;
+}
+
+int mlp_train(mlp_handle *h, const float *X, const float *T, int64_t rows, int32_t epochs, const int64_t *order,
+              uint64_t shuffle_seed, double *loss_per_epoch, int32_t mem) {
+  clear_error();
+  if (!h || !X || !T || epochs < 0) {
+    set_error("mlp_train: null argument or epochs < 0");
+    return MD_EINVAL;
+  }
+  const int cap = h->cap;
+  const int64_t nb = rows / cap;  // batches per epoch
+  if (nb < 1) {
+    set_error("mlp_train: %lld rows hold no full batch of %d", (long long)rows, cap);
+    return MD_EINVAL;
+  }
+  if (rows > ((int64_t)1 << 30) / h->k_in) {
+    set_error("mlp_train: too many rows");
+    return MD_EINVAL;
+  }
+  const int64_t nused = nb * cap;
+  Mat Xall, Xs, Xst;
+  float *Tall = nullptr, *Ts = nullptr, *ox = nullptr, *ot = nullptr;
+  int64_t *dperm = nullptr;
+  double *dloss = nullptr;
+  const float *dX = nullptr, *dT = nullptr;
+  std::vector<double> hist((size_t)epochs, 0.0);
+  int rc = to_device(h, X, rows * h->p.n_in, mem, &ox, &dX);
+  if (!rc) rc = to_device(h, T, rows * h->p.n_out, mem, &ot, &dT);
+  if (!rc) rc = mat_alloc(Xall, rows, h->k_in, kBM);
+  if (!rc) rc = mat_alloc(Xs, nused, h->k_in, kBM);
+  if (!rc) rc = mat_alloc(Xst, h->k_in, nused, (uint32_t)h->k_in);
+  auto cuda_ok = [&](cudaError_t e) {
+    if (e != cudaSuccess && !rc) {
+      set_error("mlp_train: %s", cudaGetErrorString(e));
+      rc = e == cudaErrorMemoryAllocation ? MD_ENOMEM : MD_ECUDA;
+    }
+    return rc == MD_OK;
+  };
+  if (!rc) cuda_ok(cudaMalloc(&Tall, sizeof(float) * rows * h->p.n_out));
+  if (!rc) cuda_ok(cudaMalloc(&Ts, sizeof(float) * nused * h->p.n_out));
+  if (!rc) cuda_ok(cudaMalloc(&dperm, sizeof(int64_t) * rows));
+  if (!rc) cuda_ok(cudaMalloc(&dloss, sizeof(double) * std::max(epochs, 1)));
+  if (!rc) cuda_ok(cudaMemsetAsync(dloss, 0, sizeof(double) * std::max(epochs, 1), h->st));
+  if (!rc) {
+    k_prep_x<<<1024, 256, 0, h->st>>>(dX, rows, h->p.n_in, h->xmean, h->xstd, Xall.p, rows, h->k_in, nullptr, 0);
+    k_prep_t<<<256, 256, 0, h->st>>>(dT, rows, h->p.n_out, h->ymean, h->ystd, Tall);
+    cuda_ok(cudaGetLastError());
+  }
+  if (!rc) cuda_ok(cudaMemsetAsync(h->loss, 0, sizeof(double), h->st));
+  std::vector<int64_t> perm((size_t)rows);
+  std::vector<uint64_t> keys((size_t)rows);
+  for (int e = 0; e < epochs && !rc; ++e) {
+    if (order) {
+      std::memcpy(perm.data(), order + (int64_t)e * rows, sizeof(int64_t) * rows);
+      for (int64_t i = 0; i < rows; ++i)
+        if (perm[(size_t)i] < 0 || perm[(size_t)i] >= rows) {
+          set_error("mlp_train: order[%d][%lld] out of range", e, (long long)i);
+          rc = MD_EINVAL;
+          break;
+        }
+      if (rc) break;
+    } else {  // sort SplitMix64 keys of stream shuffle_seed + e (ties by index)
+      for (int64_t i = 0; i < rows; ++i) {
+        keys[(size_t)i] = splitmix64_at(shuffle_seed + (uint64_t)e, (uint64_t)i + 1);
+        perm[(size_t)i] = i;
+      }
+      std::stable_sort(perm.begin(), perm.end(),
+                       [&](int64_t a, int64_t b) { return keys[(size_t)a] < keys[(size_t)b]; });
+    }
+    if (!cuda_ok(cudaMemcpyAsync(dperm, perm.data(), sizeof(int64_t) * rows, cudaMemcpyHostToDevice, h->st))) break;
+    k_gather<<<1024, 256, 0, h->st>>>(Xall.p, Tall, dperm, nused, h->k_in, h->p.n_out, Xs.p, Xst.p, Ts);
+    if (!cuda_ok(cudaGetLastError())) break;
+    for (int64_t b = 0; b < nb && !rc; ++b) {
+      // the loss kernel adds loss / nb to the epoch's slot via h->loss[0]
+      rc = train_step(h, Xs, Xst, (int)(b * cap), Ts + b * cap * h->p.n_out, 1.0 / (double)nb);
+      if (!rc) rc = adam_step(h);
+    }
+    if (!rc) cuda_ok(cudaMemcpyAsync(dloss + e, h->loss, sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    if (!rc) cuda_ok(cudaMemsetAsync(h->loss, 0, sizeof(double), h->st));
+    if (!rc) cuda_ok(cudaStreamSynchronize(h->st));  // the host permutation buffer is reused next epoch
+  }
+  if (!rc && epochs > 0)
+    cuda_ok(cudaMemcpyAsync(hist.data(), dloss, sizeof(double) * epochs, cudaMemcpyDeviceToHost, h->st));
+  if (!rc) rc = check_err(h);
+  cudaStreamSynchronize(h->st);
+  if (!rc && loss_per_epoch) std::memcpy(loss_per_epoch, hist.data(), sizeof(double) * epochs);
+  mat_free(Xall);
+  mat_free(Xs);
+  mat_free(Xst);
+  for (void *q : {(void *)Tall, (void *)Ts, (void *)ox, (void *)ot, (void *)dperm, (void *)dloss})
+    if (q) cudaFree(q);
+  return rc;
+}
+
+void mlp_free(mlp_handle *h) { destroy(h); }
+
+int gk_tail_features(const double *c_sigma, const double *c_q, int64_t ld, int64_t nruns, const double *volume,
+                     const double *temperature, const double *density, float *out) {
+  clear_error();
+  constexpr int kPts = 64;
+  if (!c_sigma || !c_q || !volume || !temperature || !density || !out || ld < kPts || nruns < 0) {
+    set_error("gk_tail_features: null argument or fewer than 64 readout points");
+    return MD_EINVAL;
+  }
+  for (int64_t r = 0; r < nruns; ++r) {
+    const double *cs = c_sigma + r * ld, *cq = c_q + r * ld;
+    const double V = volume[r], T = temperature[r];
+    if (!(cs[0] > 0) || !(cq[0] > 0) || !(V > 0) || !(T > 0)) {
+      set_error("gk_tail_features: run %lld has a non-positive C(0), volume or temperature", (long long)r);
+      return MD_EINVAL;
+    }
+    float *o = out + r * (2 * kPts + 4);
+    for (int i = 0; i < kPts; ++i) o[i] = (float)(cs[i] / cs[0]);
+    o[kPts] = (float)std::log(V * cs[0] / T);
+    for (int i = 0; i < kPts; ++i) o[kPts + 1 + i] = (float)(cq[i] / cq[0]);
+    o[2 * kPts + 1] = (float)std::log(V * cq[0] / (T * T));
+    o[2 * kPts + 2] = (float)T;
+    o[2 * kPts + 3] = (float)density[r];
+  }
+  return MD_OK;
+}
+
+}  // extern "C"
