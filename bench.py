@@ -316,7 +316,9 @@ def run_ours(args):
     }
     if world == 1 and not args.no_ensemble:
         out["batched_ensemble"] = run_batched(pkg, synth, 200, torch)
-        out["time_to_viscosity"] = run_time_to_viscosity(pkg, synth, torch)
+        tail, out["learned_tail"] = run_learned_tail(pkg, torch)
+        out["time_to_viscosity"] = run_time_to_viscosity(pkg, synth, torch, tail=tail)
+        tail.net.close()
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(st, s, budget_s=args.cpu_seconds)
     print(json.dumps(out), flush=True)
@@ -343,12 +345,9 @@ def c4_ensemble(pkg, synth, count=256, seed=11):
 
 def melt_replicas(g, temps, steps_hot=600, steps_cold=600, every=10):
     """Velocity rescaling per replica: all to T* = 2.0, then each to its own T*."""
-    nrep = len(temps)
-    for target, steps in ((np.full(nrep, 2.0), steps_hot), (temps, steps_cold)):
-        for _ in range(steps // every):
-            g.step(every)
-            T = np.array([g.replica_observables(k)["T"] for k in range(nrep)])
-            g.replica_scale_velocities(np.sqrt(target / T))
+    from paper_2503_07526_gb300 import learned_tail as lt
+
+    lt.melt(g, temps, steps_hot, steps_cold, every)
 
 
 def run_batched(pkg, synth, steps, torch):
@@ -379,23 +378,147 @@ def run_batched(pkg, synth, steps, torch):
             "autotuned": {"pair_threads": cfg["pair_threads"], "build_warps": cfg["build_warps"]}}
 
 
-def eta_of(t, c, V, T, gk):
-    return gk(t, c, t_cut=2.0, prefactor=V / T)[0]
+def run_learned_tail(pkg, torch):
+    """Train the learned Green-Kubo tail on a replica ensemble (features from
+    2,000-step runs, targets from the same replicas at 20,000 steps) and
+    judge it on held-out replicas against the short-run integral."""
+    from paper_2503_07526_gb300 import learned_tail as lt
+
+    specs = lt.ensemble_specs(512, seed=5, n_range=(500, 4000))
+    sync = torch.cuda.synchronize
+    t0 = time.perf_counter()
+    d = lt.generate(specs, 2000, 20000, sync=sync)
+    gen_s = time.perf_counter() - t0
+    tr, va, te = (lt.split(d, slice(a, b)) for a, b in ((0, 256), (256, 384), (384, 512)))
+    tail = lt.LearnedTail(lr=1e-3, weight_decay=1e-3, seed=1)
+    sync()
+    t0 = time.perf_counter()
+    hist = tail.fit(tr, va, epochs=30)
+    sync()
+    train_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    eta, kappa, ue, uk = tail.predict(te["X"], te["eta_short"], te["kappa_short"], te["atoms"], te["steps_short"])
+    infer_s = time.perf_counter() - t0
+
+    def rms_rel(a, b):
+        return float(np.sqrt(np.mean(((a - b) / b) ** 2)))
+
+    return tail, {
+        "workload": "512 LJ replicas, sizes log-uniform in [500, 4000] atoms, rho* uniform in [0.7, 0.9], T* uniform "
+                    "in [0.7, 2.0]; features after 2,000 steps, targets (eta, kappa to t_cut = 2 tau) after 20,000 "
+                    "steps; trained on 256, validated on 128, judged on 128 held-out replicas",
+        "network": "132 -> 3 x 128 tanh -> 2, bfloat16 tcgen05 products, FP32 master weights, Adam, 30 epochs",
+        "rms_rel_error_vs_long_run": {"eta_learned_tail": rms_rel(eta, te["eta_long"]),
+                                      "eta_short_run_integral": rms_rel(te["eta_short"], te["eta_long"]),
+                                      "kappa_learned_tail": rms_rel(kappa, te["kappa_long"]),
+                                      "kappa_short_run_integral": rms_rel(te["kappa_short"], te["kappa_long"])},
+        "network_used_fraction": {"eta": float(ue.mean()), "kappa": float(uk.mean())},
+        "validation_error": list(tail.val_error), "short_run_error_coefficients": list(tail.short_coeff),
+        "loss_first_last": [float(hist[0]), float(hist[-1])],
+        "seconds": {"generate": gen_s, "train": train_s, "inference_128": infer_s},
+        "ensemble_atom_steps_per_s": float(d["atoms"].sum() * 20000 / (d["seconds_short"] + d["seconds_long"])),
+    }
 
 
-def run_time_to_viscosity(pkg, synth, torch, replicas=64, prod=4000):
+def run_learned_tail_full(args):
+    """The full learned-tail workload: the network trained on 4,096 replica
+    runs of the batched-ensemble distribution (sizes log-uniform in
+    [500, 32,000] atoms; features after 5,000 steps, targets after 50,000),
+    then applied to a 16,384,000-atom box (160^3 fcc cells x 4) run for 5,000
+    steps and judged against the same box's 100,000-step integral.  Opt-in
+    (about half an hour on one GB300); prints one JSON line."""
+    import torch
+
+    import paper_2503_07526_gb300 as pkg
+    from paper_2503_07526_gb300 import learned_tail as lt
+    from paper_2503_07526_gb300 import synth
+
+    pkg.lib()
+    sync = torch.cuda.synchronize
+    nrep, short, long = args.lt_replicas, 5000, 50000
+    t0 = time.perf_counter()
+    d = lt.generate(lt.ensemble_specs(nrep, seed=7), short, long, sync=sync)
+    gen_s = time.perf_counter() - t0
+    if args.save_dataset:
+        np.savez(args.save_dataset, **{k: v for k, v in d.items()})
+    a, b = int(nrep * 0.75), int(nrep * 0.875)
+    tr, va, te = (lt.split(d, slice(x, y)) for x, y in ((0, a), (a, b), (b, nrep)))
+    tail = lt.LearnedTail(lr=1e-3, weight_decay=1e-3, seed=1)
+    sync()
+    t0 = time.perf_counter()
+    hist = tail.fit(tr, va, epochs=30)
+    sync()
+    train_s = time.perf_counter() - t0
+    eta, kappa, ue, uk = tail.predict(te["X"], te["eta_short"], te["kappa_short"], te["atoms"], te["steps_short"])
+
+    def rms_rel(x, y):
+        return float(np.sqrt(np.mean(((x - y) / y) ** 2)))
+
+    held_out = {"eta_learned_tail": rms_rel(eta, te["eta_long"]),
+                "eta_short_run_integral": rms_rel(te["eta_short"], te["eta_long"]),
+                "kappa_learned_tail": rms_rel(kappa, te["kappa_long"]),
+                "kappa_short_run_integral": rms_rel(te["kappa_short"], te["kappa_long"]),
+                "network_used": [float(ue.mean()), float(uk.mean())]}
+    # the judge: one large box, short run then the full-length integral
+    jc, js, jl = args.lt_judge_cells, 5000, 100000
+    s = synth.lj_system(jc, rho=RHO, T=T_STAR, seed=3)
+    n, L = s["n"], s["L"]
+    V = L ** 3
+    p = pkg.make_params(n, L, rc=RC, dt=DT, skin=SKIN, precision=pkg.MD_PREC_MIXED, stress=(12, 16, 2, 1),
+                        heatflux=(12, 16, 2, 1), vacf=None)
+    g = pkg.System(p, s["r"], s["v"])
+    melt(g, 2.0, 600)
+    melt(g, T_STAR, 600)
+    g.reset_correlators()
+    sync()
+    t0 = time.perf_counter()
+    g.step(js)
+    sync()
+    short_s = time.perf_counter() - t0
+    ra = lt.transport(g, [V])
+    X = pkg.gk_tail_features(ra["Cs"][:, :64], ra["Cq"][:, :64], [V], ra["T"], [n / V])
+    je, jk, jue, juk = tail.predict(X, ra["eta"], ra["kappa"], [n], [js])
+    nete, netk = tail._net(X)
+    t0 = time.perf_counter()
+    g.step(jl - js)
+    sync()
+    long_s = time.perf_counter() - t0
+    rb = lt.transport(g, [V])
+    g.close()
+    out = {"workload": f"learned Green-Kubo tail: {nrep} replicas x {long} steps (features at {short}), judged on "
+                       f"a {n}-atom LJ box (rho*={RHO}, T*={T_STAR}) at {js} against {jl} steps",
+           "training": {"seconds_generate": gen_s, "seconds_train": train_s, "atoms": int(d["atoms"].sum()),
+                        "loss_first_last": [float(hist[0]), float(hist[-1])],
+                        "validation_error": list(tail.val_error), "short_run_error_coefficients": list(tail.short_coeff)},
+           "held_out_rms_rel_error_vs_long_run": held_out,
+           "judge": {"atoms": n, "eta_full_integral": float(rb["eta"][0]), "kappa_full_integral": float(rb["kappa"][0]),
+                     "eta_short_integral": float(ra["eta"][0]), "kappa_short_integral": float(ra["kappa"][0]),
+                     "eta_network": float(nete[0]), "kappa_network": float(netk[0]),
+                     "eta_returned": float(je[0]), "kappa_returned": float(jk[0]),
+                     "network_used": [bool(jue[0]), bool(juk[0])],
+                     "seconds_short": short_s, "seconds_long": long_s,
+                     "atom_steps_per_s": n * jl / (short_s + long_s)}}
+    print(json.dumps(out), flush=True)
+
+
+def run_time_to_viscosity(pkg, synth, torch, replicas=64, prod=4000, tail=None, tail_steps=2000):
     """Time to a Green-Kubo viscosity with <= 2 % relative standard error at
     the 4,000-atom state point (rho* = 0.8442, T* = 0.722; eta from each
     replica's stress autocorrelation, mean of xy/xz/yz, integrated to
     t_cut = 2 tau).  The spread of eta over `replicas` replicas of `prod`
     production steps gives the replica-steps needed for 2 %; each form's
     measured cost per replica-step turns that into seconds of production
-    (equilibration excluded)."""
+    (equilibration excluded).  With a trained learned tail, the same batch
+    is also read after `tail_steps` steps and the spread of the network's
+    predictions gives the learned form's replica-steps."""
+    from paper_2503_07526_gb300 import learned_tail as lt
+
     reps = []
     for k in range(replicas):
         s = synth.lj_system(10, rho=RHO, T=T_STAR, seed=500 + k)
         reps.append(dict(r=s["r"], v=s["v"], box=s["L"]))
     V = reps[0]["box"] ** 3
+    n_atoms = reps[0]["r"].shape[1]
     p = pkg.make_params(1, 1.0, rc=RC, dt=DT, skin=0.2, precision=pkg.MD_PREC_MIXED,
                         stress=(12, 16, 2, 1), heatflux=(12, 16, 2, 1), vacf=None)
     g = pkg.System(p, replicas=reps)
@@ -403,17 +526,26 @@ def run_time_to_viscosity(pkg, synth, torch, replicas=64, prod=4000):
     g.reset_correlators()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    g.step(prod)
+    learned = None
+    if tail is not None:
+        g.step(tail_steps)
+        torch.cuda.synchronize()
+        t_short = time.perf_counter() - t0
+        a = lt.transport(g, np.full(replicas, V))
+        X = pkg.gk_tail_features(a["Cs"][:, :64], a["Cq"][:, :64], np.full(replicas, V), a["T"],
+                                 np.full(replicas, n_atoms / V))
+        ti = time.perf_counter()
+        eta_l, _, used, _ = tail.predict(X, a["eta"], a["kappa"], np.full(replicas, n_atoms),
+                                         np.full(replicas, tail_steps))
+        infer_s = time.perf_counter() - ti
+        learned = (eta_l, used, t_short, infer_s)
+        g.step(prod - tail_steps)
+    else:
+        g.step(prod)
     torch.cuda.synchronize()
     batch_s = time.perf_counter() - t0
-    c = g.corr(pkg.MD_CORR_STRESS)
-    etas = []
-    for k in range(replicas):
-        Tk = g.replica_observables(k)["T_mean"]
-        curves = [c.read(3 * k + a) for a in range(3)]
-        etas.append(eta_of(curves[0][0], np.mean([cv[1] for cv in curves], axis=0), V, Tk, pkg.gk_integrate))
+    etas = lt.transport(g, np.full(replicas, V))["eta"]
     g.close()
-    etas = np.array(etas)
     mean, se = etas.mean(), etas.std(ddof=1) / math.sqrt(replicas)
     need = replicas * prod * (se / (0.02 * abs(mean))) ** 2  # replica-steps for 2 %
     # cost per replica-step of one 4,000-atom system on its own (graph replay)
@@ -430,13 +562,27 @@ def run_time_to_viscosity(pkg, synth, torch, replicas=64, prod=4000):
         torch.cuda.synchronize()
         costs[name] = (time.perf_counter() - t0) / 2000
         gs.close()
-    return {"definition": "seconds of production MD (correlators included, equilibration excluded) until the "
-                          "ensemble Green-Kubo viscosity has <= 2 % relative standard error; 4,000-atom LJ liquid, "
-                          "rho*=0.8442, T*=0.722, eta to t_cut = 2 tau; replica-steps needed from the spread over "
-                          f"{replicas} replicas x {prod} steps, seconds = needed x measured cost per replica-step",
-            "eta": float(mean), "eta_se": float(se), "replica_steps_needed": float(need),
-            "seconds": {k: v * need for k, v in costs.items()},
-            "cost_per_replica_step_s": costs}
+    out = {"definition": "seconds of production MD (correlators included, equilibration excluded) until the "
+                         "ensemble Green-Kubo viscosity has <= 2 % relative standard error; 4,000-atom LJ liquid, "
+                         "rho*=0.8442, T*=0.722, eta to t_cut = 2 tau; replica-steps needed from the spread over "
+                         f"{replicas} replicas x {prod} steps, seconds = needed x measured cost per replica-step",
+           "eta": float(mean), "eta_se": float(se), "replica_steps_needed": float(need),
+           "seconds": {k: v * need for k, v in costs.items()},
+           "cost_per_replica_step_s": costs}
+    if learned is not None:
+        eta_l, used, t_short, infer_s = learned
+        lm, lse = float(eta_l.mean()), float(eta_l.std(ddof=1) / math.sqrt(replicas))
+        need_l = replicas * tail_steps * (lse / (0.02 * abs(lm))) ** 2
+        out["learned_tail"] = {
+            "what": f"network prediction from each replica's first {tail_steps} steps; replica-steps for a 2 % "
+                    "standard error of the mean prediction, at the batched cost, plus inference",
+            "eta_mean": lm, "eta_se": lse, "network_used_fraction": float(used.mean()),
+            "deviation_from_ensemble_eta_in_se": (lm - float(mean)) / float(se),
+            "replica_steps_needed": float(max(need_l, tail_steps)),  # at least one short run
+            "seconds": float(max(need_l, tail_steps) * costs["mixed_gpu_batched_%d" % replicas] + infer_s),
+            "note": "the 2 % criterion bounds the scatter of the prediction; its bias against the ensemble "
+                    "integral is reported beside it in standard errors of that integral"}
+    return out
 
 
 def committed_traffic(kernel):
@@ -526,10 +672,17 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the replica ensemble and time-to-viscosity")
     ap.add_argument("--cells", type=int, default=CELLS, help="fcc cells per side (4 cells^3 atoms)")
     ap.add_argument("--quick", action="store_true", help="short melt, timed region only (for profilers)")
+    ap.add_argument("--learned-tail-full", action="store_true",
+                    help="run only the full learned-tail workload (4,096 replicas, 16.4M-atom judge)")
+    ap.add_argument("--lt-replicas", type=int, default=4096)
+    ap.add_argument("--lt-judge-cells", type=int, default=160)
+    ap.add_argument("--save-dataset", default=None, help="npz path for the learned-tail training set")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.learned_tail_full:
+        run_learned_tail_full(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -176,6 +176,9 @@ OTF_API int md_observables(md_handle *h, md_obs *out);
 
 /* Observables of replica r of a batch (synchronises). */
 OTF_API int md_replica_observables(md_handle *h, int32_t r, md_obs *out);
+/* The observables of every replica at once: out [count], count = the number
+ * of replicas (MD_EINVAL otherwise).  One device read; synchronises. */
+OTF_API int md_replica_observables_all(md_handle *h, md_obs *out, int32_t count);
 
 /* Per-particle state in the caller's atom order: positions (wrapped into
  * [0, box)), velocities, forces, potential energies [n] and virials [6][n]

@@ -93,6 +93,7 @@ def lib(build: bool = False):
         "md_init": [C.POINTER(md_params), C.POINTER(md_system), vp, C.POINTER(vp)],
         "md_init_replicas": [C.POINTER(md_params), C.POINTER(md_replica), i32, i32, vp, C.POINTER(vp)],
         "md_replica_observables": [vp, i32, C.POINTER(md_obs)],
+        "md_replica_observables_all": [vp, vp, i32],
         "md_replica_scale_velocities": [vp, dp],
         "md_get_config": [vp, C.POINTER(md_config)],
         "md_step": [vp, i64],
@@ -144,7 +145,7 @@ EXPORTS = ("md_init", "md_step", "md_observables", "md_get_particles", "md_scale
            "md_reset_correlators", "md_corr", "md_set_timing", "md_kernel_times", "md_free", "corr_create",
            "corr_push", "corr_read", "corr_raw", "corr_pushes", "corr_reset", "corr_free", "gk_integrate",
            "md_last_error", "md_observables_noalloc", "md_init_replicas", "md_replica_observables",
-           "md_replica_scale_velocities", "md_get_config", "mlp_create", "mlp_param_count", "mlp_get_params",
+           "md_replica_scale_velocities", "md_get_config", "md_replica_observables_all", "mlp_create", "mlp_param_count", "mlp_get_params",
            "mlp_set_params", "mlp_set_scaler", "mlp_fit_scaler", "mlp_forward", "mlp_loss_grad", "mlp_adam_step",
            "mlp_train", "mlp_free", "gk_tail_features", "corr_read_rows")
 
@@ -346,6 +347,16 @@ class System:
         _check(lib().md_replica_observables(self._h, int(r), C.byref(o)))
         return dict(step=o.step, U=o.U, K=o.K, T=o.T, sigma=np.array(o.sigma[:]), q=np.array(o.q[:]),
                     T_mean=o.T_mean, rebuilds=o.rebuilds)
+
+    def replica_observables_all(self):
+        """Every replica's observables in one device read: dict of arrays
+        (step and rebuilds are scalars)."""
+        arr = (md_obs * self.nrep)()
+        _check(lib().md_replica_observables_all(self._h, arr, self.nrep))
+        return dict(step=arr[0].step, rebuilds=arr[0].rebuilds,
+                    U=np.array([o.U for o in arr]), K=np.array([o.K for o in arr]), T=np.array([o.T for o in arr]),
+                    sigma=np.array([o.sigma[:] for o in arr]), q=np.array([o.q[:] for o in arr]),
+                    T_mean=np.array([o.T_mean for o in arr]))
 
     def replica_scale_velocities(self, lams):
         lam = np.ascontiguousarray(lams, dtype=np.float64)

@@ -1657,6 +1657,18 @@ int md_replica_observables(md_handle *h, int32_t r, md_obs *out) {
   return MD_OK;
 }
 
+int md_replica_observables_all(md_handle *h, md_obs *out, int32_t count) {
+  clear_error();
+  if (!h || !out || count != h->nrep) {
+    set_error("md_replica_observables_all: null argument or count != %d replicas", h ? h->nrep : 0);
+    return MD_EINVAL;
+  }
+  int rc = fetch_obs(h);
+  if (rc) return rc;
+  for (int r = 0; r < count; ++r) fill_obs(h, r, out + r);
+  return MD_OK;
+}
+
 int md_get_particles(md_handle *h, double *r, double *v, double *F, double *epot, double *W, int32_t mem) {
   clear_error();
   if (!h || (mem != MD_MEM_HOST && mem != MD_MEM_DEVICE)) {
