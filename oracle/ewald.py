@@ -159,10 +159,19 @@ def bspline_moduli(K, n):
     return 1.0 / den
 
 
-def spme_reciprocal(r, q, L, *, alpha, K, order, ke=KE):
+def spme_reciprocal(r, q, L, *, alpha, K, order, ke=KE, virial="derivative"):
     """Smooth particle-mesh Ewald on a K^3 mesh with order-n splines
     (K >= order) in a cubic box of side L.  Returns (F [3, n], E [n],
-    W [6, n], E_rec, W_rec [6]) like ewald_reciprocal."""
+    W [6, n], E_rec, W_rec [6]) like ewald_reciprocal.
+
+    The per-particle virial: with virial="derivative" (Appendix B's form),
+    W_ab,j = delta_ab E_j minus the m_a m_b term, whose factor m_a m_b is
+    carried by two derivatives of the particle's spline weights,
+    m_a m_b exp(2 pi i m.r) ~ (K/(2 pi i L))^2 b(m) sum_k d_a d_b W_j(k) ...,
+    applied to one more convolved mesh psi (kernel B C h with
+    h = 2 (1 + pi^2 m^2/alpha^2)/m^2).  With virial="tensor", six meshes
+    convolved with the full tensor kernel are read with the plain weights.
+    Both tend to the k-space sum's per-particle virial."""
     L = float(L)
     if K < order:
         raise ValueError("the mesh must have at least `order` points per side")
@@ -174,10 +183,12 @@ def spme_reciprocal(r, q, L, *, alpha, K, order, ke=KE):
     t = np.arange(order)
     w = np.zeros((3, n_at, order))
     dw = np.zeros((3, n_at, order))
+    d2w = np.zeros((3, n_at, order))
     for a in range(3):
         x = (u[a] - base[a])[:, None] + t[None, :]  # argument u - k
         w[a] = bspline(x, order)
         dw[a] = bspline(x, order - 1) - bspline(x - 1.0, order - 1)
+        d2w[a] = bspline(x, order - 2) - 2.0 * bspline(x - 1.0, order - 2) + bspline(x - 2.0, order - 2)
     idx = np.mod(base[:, :, None] - t[None, None, :], K)  # [3, n, order]
     # charge mesh Q(k)
     Q = np.zeros((K, K, K))
@@ -202,7 +213,15 @@ def spme_reciprocal(r, q, L, *, alpha, K, order, ke=KE):
     Wrec = 0.5 * ke * (T * (BC * np.abs(FQ) ** 2)[None]).sum(axis=(1, 2, 3))
     # convolved meshes: theta * Q = IFFT(B C FFT(Q)) (times K^3 for numpy's IFFT scaling)
     phi = np.fft.ifftn(BC * FQ).real * K ** 3
-    phiW = [np.fft.ifftn(BC * T[c] * FQ).real * K ** 3 for c in range(6)]
+    if virial == "tensor":
+        phiW = [np.fft.ifftn(BC * T[c] * FQ).real * K ** 3 for c in range(6)]
+    elif virial == "derivative":
+        hk = 2.0 * (1.0 + math.pi ** 2 * m2 / alpha ** 2) / m2
+        psi = np.fft.ifftn(BC * hk * FQ).real * K ** 3
+    else:
+        raise ValueError("virial must be 'derivative' or 'tensor'")
+    pairs = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))
+    cw = ke * (K / L) ** 2 / (8.0 * math.pi ** 2)
     F = np.zeros((3, n_at))
     E = np.zeros(n_at)
     W = np.zeros((6, n_at))
@@ -211,8 +230,19 @@ def spme_reciprocal(r, q, L, *, alpha, K, order, ke=KE):
         P = phi[sub]
         wj = np.einsum("a,b,c->abc", w[0, j], w[1, j], w[2, j])
         E[j] = 0.5 * ke * q[j] * float((wj * P).sum())
-        for c in range(6):
-            W[c, j] = 0.5 * ke * q[j] * float((wj * phiW[c][sub]).sum())
+        if virial == "tensor":
+            for c in range(6):
+                W[c, j] = 0.5 * ke * q[j] * float((wj * phiW[c][sub]).sum())
+        else:
+            Psi = psi[sub]
+            for c, (a, b) in enumerate(pairs):
+                f = [w[0, j], w[1, j], w[2, j]]
+                if a == b:
+                    f[a] = d2w[a, j]
+                else:
+                    f[a], f[b] = dw[a, j], dw[b, j]
+                S = float((np.einsum("a,b,c->abc", *f) * Psi).sum())
+                W[c, j] = (E[j] if a == b else 0.0) + cw * q[j] * S
         g0 = np.einsum("a,b,c->abc", dw[0, j], w[1, j], w[2, j])
         g1 = np.einsum("a,b,c->abc", w[0, j], dw[1, j], w[2, j])
         g2 = np.einsum("a,b,c->abc", w[0, j], w[1, j], dw[2, j])

@@ -124,23 +124,28 @@ def test_spme_converges_to_the_kspace_sum():
     L, alpha = 12.0, 0.5
     r, q = melt_config(24, L, 11)
     Fd, Ed, Wd, Erd, Wrd = ewald.ewald_reciprocal(r, q, L, alpha=alpha, nmax=12)
+    assert Ed.sum() == pytest.approx(Erd, rel=1e-12)
+    assert np.allclose(Wd.sum(axis=1), Wrd, rtol=1e-11, atol=1e-12 * np.abs(Wrd).max())
+    assert np.abs(Fd.sum(axis=1)).max() <= 1e-10 * np.abs(Fd).max()
     errs = []
     for K, order in ((16, 4), (32, 8)):
         F, E, W, Er, Wr = ewald.spme_reciprocal(r, q, L, alpha=alpha, K=K, order=order)
-        errs.append(abs(Er - Erd) / abs(Erd))
+        Wt = ewald.spme_reciprocal(r, q, L, alpha=alpha, K=K, order=order, virial="tensor")[2]
+        errs.append((abs(Er - Erd) / abs(Erd), np.abs(W - Wd).max() / np.abs(Wd).max()))
+        # the energies and the tensor-form virials sum exactly to the mesh totals
+        assert E.sum() == pytest.approx(Er, rel=1e-12)
+        assert np.allclose(Wt.sum(axis=1), Wr, rtol=1e-11, atol=1e-12 * np.abs(Wr).max())
         if K == 32:
             assert Er == pytest.approx(Erd, rel=1e-7)
             assert np.abs(Wr - Wrd).max() <= 1e-6 * np.abs(Wrd).max()
             assert np.abs(F - Fd).max() <= 1e-5 * np.abs(Fd).max()
             assert np.abs(E - Ed).max() <= 1e-5 * np.abs(Ed).max()
+            # Appendix B's derivative form and the tensor form both reach the
+            # k-space sum's per-particle virial
             assert np.abs(W - Wd).max() <= 1e-5 * np.abs(Wd).max()
-        # per-particle sums equal the totals
-        assert E.sum() == pytest.approx(Er, rel=1e-12)
-        assert np.allclose(W.sum(axis=1), Wr, rtol=1e-11, atol=1e-12 * np.abs(Wr).max())
-    assert errs[1] < 0.01 * errs[0]
-    assert Ed.sum() == pytest.approx(Erd, rel=1e-12)
-    assert np.allclose(Wd.sum(axis=1), Wrd, rtol=1e-11, atol=1e-12 * np.abs(Wrd).max())
-    assert np.abs(Fd.sum(axis=1)).max() <= 1e-10 * np.abs(Fd).max()
+            assert np.abs(Wt - Wd).max() <= 1e-5 * np.abs(Wd).max()
+            assert np.abs(W.sum(axis=1) - Wrd).max() <= 1e-5 * np.abs(Wrd).max()
+    assert errs[1][0] < 0.01 * errs[0][0] and errs[1][1] < 0.01 * errs[0][1]
 
 
 def test_buckingham_dimer_closed_form():
