@@ -316,6 +316,7 @@ def run_ours(args):
     }
     if world == 1 and not args.no_ensemble:
         out["batched_ensemble"] = run_batched(pkg, synth, 200, torch)
+        out["ionic_melt"] = run_ionic(pkg, synth, torch)
         tail, out["learned_tail"] = run_learned_tail(pkg, torch)
         out["time_to_viscosity"] = run_time_to_viscosity(pkg, synth, torch, tail=tail)
         tail.net.close()
@@ -378,6 +379,55 @@ def run_batched(pkg, synth, steps, torch):
             "autotuned": {"pair_threads": cfg["pair_threads"], "build_warps": cfg["build_warps"]}}
 
 
+IONIC = dict(cells=40, rho=0.031, T_K=1300.0, masses=(22.99, 35.45), A=1200.0, brho=0.32, C=10.0, rc=10.0,
+             skin=1.0, alpha=0.3, mesh=128, order=8, dt_fs=1.0)
+KB_EV = 8.617333262e-5           # eV / K
+FS_PER_UNIT = 10.1805055         # fs per (A sqrt(amu / eV))
+
+
+def run_ionic(pkg, synth, torch, steps=100, fp64_steps=10, cells=None):
+    """Throughput of the ionic melt (rock salt 40^3 x 8 = 512,000 ions at
+    0.031 ions/A^3, +-1 e, Na/Cl masses, Buckingham A=1200 eV, rho=0.32 A,
+    C=10 eV A^6, rc=10 A, SPME alpha=0.3/A on a 128^3 mesh, order 8,
+    dt = 1 fs, started from the lattice at 1300 K) in the mixed form and in
+    plain FP64, with the per-kernel-class split."""
+    c = IONIC
+    cells = cells or c["cells"]
+    s = synth.ionic_system(cells, c["rho"], KB_EV * c["T_K"], seed=9, masses=c["masses"], jitter=0.2)
+    n, L = s["n"], s["L"]
+    out = {"workload": f"binary ionic melt, {n} ions (rock salt {cells}^3 x 8), L = {L:.1f} A, Buckingham + SPME "
+                       f"Ewald ({c['mesh']}^3 mesh, order {c['order']}, alpha {c['alpha']}/A, rc {c['rc']} A), "
+                       "dt 1 fs, stress and heat-flux correlators with per-particle reciprocal energy and virial",
+           "n_ions": n}
+    for name, prec, k in (("mixed", pkg.MD_PREC_MIXED, steps), ("fp64_gpu", pkg.MD_PREC_FP64, fp64_steps)):
+        p = pkg.make_params(n, L, rc=c["rc"], dt=c["dt_fs"] / FS_PER_UNIT, skin=c["skin"], precision=prec,
+                            masses=c["masses"], potential=pkg.MD_POT_BUCK_EWALD, charges=(1.0, -1.0),
+                            buckingham=(c["A"], c["brho"], c["C"]), ewald_alpha=c["alpha"], mesh=c["mesh"],
+                            order=c["order"], stress=(12, 16, 2, 1), heatflux=(12, 16, 2, 1), vacf=None)
+        g = pkg.System(p, s["r"], s["v"], types=s["types"])
+        g.step(5)
+        g.set_timing(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.step(k)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        kt = g.kernel_times()
+        g.set_timing(False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.step(k)
+        torch.cuda.synchronize()
+        sec_graph = time.perf_counter() - t0
+        o = g.observables()
+        g.close()
+        out[name] = {"atom_steps_per_s": n * k / sec_graph, "ms_per_step": 1e3 * sec_graph / k, "steps": k,
+                     "kernel_ms_per_step": {kk: v[0] / k for kk, v in kt.items()},
+                     "T_K": o["T"] / KB_EV, "rebuilds": o["rebuilds"]}
+    out["speedup_mixed_over_fp64"] = out["mixed"]["atom_steps_per_s"] / out["fp64_gpu"]["atom_steps_per_s"]
+    return out
+
+
 def run_learned_tail(pkg, torch):
     """Train the learned Green-Kubo tail on a replica ensemble (features from
     2,000-step runs, targets from the same replicas at 20,000 steps) and
@@ -397,7 +447,7 @@ def run_learned_tail(pkg, torch):
     sync()
     train_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    eta, kappa, ue, uk = tail.predict(te["X"], te["eta_short"], te["kappa_short"], te["atoms"], te["steps_short"])
+    eta, kappa, ue, uk = tail.predict(te["X"], te["eta_short"], te["kappa_short"], te["steps_short"])
     infer_s = time.perf_counter() - t0
 
     def rms_rel(a, b):
@@ -437,7 +487,11 @@ def run_learned_tail_full(args):
     sync = torch.cuda.synchronize
     nrep, short, long = args.lt_replicas, 5000, 50000
     t0 = time.perf_counter()
-    d = lt.generate(lt.ensemble_specs(nrep, seed=7), short, long, sync=sync)
+    if args.lt_dataset:  # a training set saved by an earlier --save-dataset run
+        d = dict(np.load(args.lt_dataset))
+        nrep = len(d["T"])
+    else:
+        d = lt.generate(lt.ensemble_specs(nrep, seed=7), short, long, sync=sync)
     gen_s = time.perf_counter() - t0
     if args.save_dataset:
         np.savez(args.save_dataset, **{k: v for k, v in d.items()})
@@ -449,7 +503,7 @@ def run_learned_tail_full(args):
     hist = tail.fit(tr, va, epochs=30)
     sync()
     train_s = time.perf_counter() - t0
-    eta, kappa, ue, uk = tail.predict(te["X"], te["eta_short"], te["kappa_short"], te["atoms"], te["steps_short"])
+    eta, kappa, ue, uk = tail.predict(te["X"], te["eta_short"], te["kappa_short"], te["steps_short"])
 
     def rms_rel(x, y):
         return float(np.sqrt(np.mean(((x - y) / y) ** 2)))
@@ -477,7 +531,7 @@ def run_learned_tail_full(args):
     short_s = time.perf_counter() - t0
     ra = lt.transport(g, [V])
     X = pkg.gk_tail_features(ra["Cs"][:, :64], ra["Cq"][:, :64], [V], ra["T"], [n / V])
-    je, jk, jue, juk = tail.predict(X, ra["eta"], ra["kappa"], [n], [js])
+    je, jk, jue, juk = tail.predict(X, ra["eta"], ra["kappa"], [js])
     nete, netk = tail._net(X)
     t0 = time.perf_counter()
     g.step(jl - js)
@@ -535,8 +589,7 @@ def run_time_to_viscosity(pkg, synth, torch, replicas=64, prod=4000, tail=None, 
         X = pkg.gk_tail_features(a["Cs"][:, :64], a["Cq"][:, :64], np.full(replicas, V), a["T"],
                                  np.full(replicas, n_atoms / V))
         ti = time.perf_counter()
-        eta_l, _, used, _ = tail.predict(X, a["eta"], a["kappa"], np.full(replicas, n_atoms),
-                                         np.full(replicas, tail_steps))
+        eta_l, _, used, _ = tail.predict(X, a["eta"], a["kappa"], np.full(replicas, tail_steps))
         infer_s = time.perf_counter() - ti
         learned = (eta_l, used, t_short, infer_s)
         g.step(prod - tail_steps)
@@ -677,6 +730,7 @@ def main():
     ap.add_argument("--lt-replicas", type=int, default=4096)
     ap.add_argument("--lt-judge-cells", type=int, default=160)
     ap.add_argument("--save-dataset", default=None, help="npz path for the learned-tail training set")
+    ap.add_argument("--lt-dataset", default=None, help="train on this saved training set instead of generating it")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

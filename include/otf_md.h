@@ -67,6 +67,13 @@ extern "C" {
 #define MD_CORR_VACF 2     /* 3n series: v_x of every atom, then v_y, then v_z;
                               read out per component, averaged over atoms */
 
+/* Interaction (md_params.potential). */
+#define MD_POT_LJ 0          /* Lennard-Jones (eps, sigma), optionally energy-shifted */
+#define MD_POT_BUCK_EWALD 1  /* Buckingham A exp(-r/rho) - C/r^6 between every pair
+                                plus Coulomb by Ewald: real-space erfc term
+                                within rc, smooth particle-mesh Ewald in
+                                reciprocal space (single systems only) */
+
 /* Pair evaluation. */
 #define MD_PAIR_VERLET 0 /* Verlet neighbour lists built from link cells,
                             rebuilt when an atom has moved skin/2 */
@@ -95,9 +102,23 @@ typedef struct {
   int32_t max_neighbors; /* neighbour-list capacity per atom; 0 = automatic */
   int32_t use_graph;  /* 1: md_step replays a captured CUDA graph of a step */
   int32_t autotune;   /* 1: md_init times the pair kernel (64/128/256 threads
-                         per CTA) and the list build (2/4/8 warps per CTA) on
-                         the system and keeps the fastest (md_get_config) */
+                         per CTA) and the list build (j-parallel at 2/4/8,
+                         i-parallel at 4/8 warps per CTA) on the system and
+                         keeps the fastest (md_get_config) */
   corr_spec stress, heatflux, vacf; /* the three correlators of Sec. 2.3/2.7 */
+  int32_t list_build; /* neighbour-list build when not autotuned: 0 = the
+                         library's default, 1 = j-parallel, 2 = i-parallel
+                         (both give the same lists in the same order) */
+  int32_t potential;  /* MD_POT_LJ or MD_POT_BUCK_EWALD */
+  double charge[8];   /* MD_POT_BUCK_EWALD: charge of each type */
+  double buck_A, buck_rho, buck_C; /* MD_POT_BUCK_EWALD: Buckingham parameters
+                         (one set for every pair of types; no energy shift) */
+  double coulomb;     /* MD_POT_BUCK_EWALD: ke = 1/(4 pi eps0) in the caller's
+                         units (14.399645 eV Angstrom / e^2 for eV, Angstrom, e) */
+  double ewald_alpha; /* MD_POT_BUCK_EWALD: Ewald splitting parameter */
+  int32_t mesh;       /* MD_POT_BUCK_EWALD: SPME mesh points per side (even,
+                         >= order) */
+  int32_t order;      /* MD_POT_BUCK_EWALD: B-spline order: 4, 6 or 8 */
 } md_params;
 
 typedef struct {
@@ -124,6 +145,7 @@ typedef struct {
   int32_t build_warps;    /* warps per CTA of the neighbour-list build */
   int32_t max_neighbors;  /* neighbour-list capacity per atom */
   int64_t atoms, cells;   /* totals over all replicas */
+  int32_t build_kind;     /* 0: j-parallel list build, 1: i-parallel */
 } md_config;
 
 /* Observables of the last completed step (Sec. 2.3). */
@@ -214,7 +236,8 @@ OTF_API int md_corr(md_handle *h, int32_t which, corr_handle **out);
 #define MD_K_REDUCE 3    /* half kick + stress / heat-flux reduction + their
                             correlator samples */
 #define MD_K_VACF 4      /* per-atom velocity correlator sample */
-#define MD_NKCLASS 5
+#define MD_K_SPME 5      /* reciprocal-space Ewald (MD_POT_BUCK_EWALD) */
+#define MD_NKCLASS 6
 
 /* on = 1: the following md_step calls launch every kernel directly (no graph)
  * between CUDA events on the system's stream and add each kernel class's

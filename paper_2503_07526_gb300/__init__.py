@@ -18,6 +18,9 @@ from ._lib import (  # noqa: F401
     MD_MEM_HOST,
     MD_PAIR_CELLS,
     MD_PAIR_VERLET,
+    MD_POT_BUCK_EWALD,
+    MD_POT_LJ,
+    KE_EV_ANGSTROM,
     MD_PREC_FP64,
     MD_PREC_MIXED,
     MLP,

@@ -19,8 +19,10 @@ MD_PREC_FP64, MD_PREC_MIXED = 0, 1
 MD_MEM_HOST, MD_MEM_DEVICE = 0, 1
 MD_CORR_STRESS, MD_CORR_HEATFLUX, MD_CORR_VACF = 0, 1, 2
 MD_PAIR_VERLET, MD_PAIR_CELLS = 0, 1
-MD_K_NAMES = ("integrate", "rebuild", "pair", "reduce", "vacf")
-MD_NKCLASS = 5
+MD_POT_LJ, MD_POT_BUCK_EWALD = 0, 1
+MD_K_NAMES = ("integrate", "rebuild", "pair", "reduce", "vacf", "spme")
+MD_NKCLASS = 6
+KE_EV_ANGSTROM = 14.399645478425668  # e^2 / (4 pi eps0) in eV Angstrom
 
 _ERRNAMES = {MD_EINVAL: "MD_EINVAL", MD_ENOMEM: "MD_ENOMEM", MD_ECUDA: "MD_ECUDA", MD_ESTATE: "MD_ESTATE",
              MD_ETIMEOUT: "MD_ETIMEOUT", MD_ECAP: "MD_ECAP"}
@@ -41,7 +43,10 @@ class md_params(C.Structure):
                 ("rc", C.c_double), ("shift", C.c_int32), ("ntypes", C.c_int32), ("mass", C.c_double * 8),
                 ("dt", C.c_double), ("precision", C.c_int32), ("pair_mode", C.c_int32), ("skin", C.c_double),
                 ("max_neighbors", C.c_int32), ("use_graph", C.c_int32), ("autotune", C.c_int32), ("stress", corr_spec),
-                ("heatflux", corr_spec), ("vacf", corr_spec)]
+                ("heatflux", corr_spec), ("vacf", corr_spec), ("list_build", C.c_int32),
+                ("potential", C.c_int32), ("charge", C.c_double * 8), ("buck_A", C.c_double), ("buck_rho", C.c_double),
+                ("buck_C", C.c_double), ("coulomb", C.c_double), ("ewald_alpha", C.c_double), ("mesh", C.c_int32),
+                ("order", C.c_int32)]
 
 
 class md_system(C.Structure):
@@ -54,7 +59,8 @@ class md_replica(C.Structure):
 
 class md_config(C.Structure):
     _fields_ = [("replicas", C.c_int32), ("pair_threads", C.c_int32), ("build_warps", C.c_int32),
-                ("max_neighbors", C.c_int32), ("atoms", C.c_int64), ("cells", C.c_int64)]
+                ("max_neighbors", C.c_int32), ("atoms", C.c_int64), ("cells", C.c_int64),
+                ("build_kind", C.c_int32)]
 
 
 class md_obs(C.Structure):
@@ -141,11 +147,11 @@ def lib(build: bool = False):
     return L
 
 
-EXPORTS = ("md_init", "md_step", "md_observables", "md_get_particles", "md_scale_velocities",
-           "md_reset_correlators", "md_corr", "md_set_timing", "md_kernel_times", "md_free", "corr_create",
-           "corr_push", "corr_read", "corr_raw", "corr_pushes", "corr_reset", "corr_free", "gk_integrate",
-           "md_last_error", "md_observables_noalloc", "md_init_replicas", "md_replica_observables",
-           "md_replica_scale_velocities", "md_get_config", "md_replica_observables_all", "mlp_create", "mlp_param_count", "mlp_get_params",
+EXPORTS = ("md_init", "md_step", "md_observables", "md_get_particles", "md_scale_velocities", "md_reset_correlators",
+           "md_corr", "md_set_timing", "md_kernel_times", "md_free", "corr_create", "corr_push", "corr_read",
+           "corr_raw", "corr_pushes", "corr_reset", "corr_free", "gk_integrate", "md_last_error",
+           "md_observables_noalloc", "md_init_replicas", "md_replica_observables", "md_replica_scale_velocities",
+           "md_get_config", "md_replica_observables_all", "mlp_create", "mlp_param_count", "mlp_get_params",
            "mlp_set_params", "mlp_set_scaler", "mlp_fit_scaler", "mlp_forward", "mlp_loss_grad", "mlp_adam_step",
            "mlp_train", "mlp_free", "gk_tail_features", "corr_read_rows")
 
@@ -208,7 +214,9 @@ _init_dtypes()
 
 def make_params(n, box, *, eps=1.0, sigma=1.0, rc=2.5, shift=True, masses=(1.0,), dt=0.005,
                 precision=MD_PREC_FP64, pair_mode=MD_PAIR_VERLET, skin=0.3, max_neighbors=0, use_graph=True,
-                autotune=False, stress=(12, 16, 2, 1), heatflux=(12, 16, 2, 1), vacf=(8, 16, 2, 1)):
+                autotune=False, stress=(12, 16, 2, 1), heatflux=(12, 16, 2, 1), vacf=(8, 16, 2, 1), list_build=0,
+                potential=MD_POT_LJ, charges=(), buckingham=(0.0, 1.0, 0.0), coulomb=KE_EV_ANGSTROM, ewald_alpha=0.0,
+                mesh=0, order=8):
     p = md_params()
     p.n, p.box, p.eps, p.sigma, p.rc, p.shift = int(n), float(box), eps, sigma, rc, int(bool(shift))
     p.ntypes = len(masses)
@@ -216,6 +224,12 @@ def make_params(n, box, *, eps=1.0, sigma=1.0, rc=2.5, shift=True, masses=(1.0,)
         p.mass[t] = float(m)
     p.dt, p.precision, p.pair_mode, p.skin = dt, int(precision), int(pair_mode), float(skin)
     p.max_neighbors, p.use_graph, p.autotune = int(max_neighbors), int(bool(use_graph)), int(bool(autotune))
+    p.list_build = int(list_build)
+    p.potential = int(potential)
+    for t, q in enumerate(charges):
+        p.charge[t] = float(q)
+    p.buck_A, p.buck_rho, p.buck_C = (float(x) for x in buckingham)
+    p.coulomb, p.ewald_alpha, p.mesh, p.order = float(coulomb), float(ewald_alpha), int(mesh), int(order)
     for name, spec in (("stress", stress), ("heatflux", heatflux), ("vacf", vacf)):
         cs = getattr(p, name)
         cs.b, cs.p, cs.m, cs.u = spec if spec is not None else (1, 2, 1, 0)
@@ -366,6 +380,7 @@ class System:
         c = md_config()
         _check(lib().md_get_config(self._h, C.byref(c)))
         return dict(replicas=c.replicas, pair_threads=c.pair_threads, build_warps=c.build_warps,
+                    build_kind=c.build_kind,
                     max_neighbors=c.max_neighbors, atoms=c.atoms, cells=c.cells)
 
     def step(self, nsteps):

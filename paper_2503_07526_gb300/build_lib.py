@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libotfmd.so")
-SOURCES = ["capi.cu", "corr.cu", "md.cu", "obs_noalloc.cu", "mlp.cu"]
+SOURCES = ["capi.cu", "corr.cu", "md.cu", "obs_noalloc.cu", "mlp.cu", "spme.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "-I" + INCLUDE, "-I" + CSRC, "--expt-relaxed-constexpr"]
@@ -60,7 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for _, err in results:
             print(err)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart"]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart", "-lcufft"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -59,8 +59,8 @@ template <>
 struct Vec4<float> {
   using type = float4;
   __device__ __forceinline__ static float4 load(const float4 *p) { return __ldg(p); }
-  __device__ __forceinline__ static void store(float4 *p, float x, float y, float z) {
-    *p = make_float4(x, y, z, 0.f);
+  __device__ __forceinline__ static void store(float4 *p, float x, float y, float z, float w = 0.f) {
+    *p = make_float4(x, y, z, w);
   }
 };
 struct alignas(16) dvec4 {
@@ -74,10 +74,10 @@ struct Vec4<double> {
     double2 a = __ldg(q), b = __ldg(q + 1);
     return dvec4{a.x, a.y, b.x, b.y};
   }
-  __device__ __forceinline__ static void store(dvec4 *p, double x, double y, double z) {
+  __device__ __forceinline__ static void store(dvec4 *p, double x, double y, double z, double w = 0.0) {
     double2 *q = reinterpret_cast<double2 *>(p);
     q[0] = make_double2(x, y);
-    q[1] = make_double2(z, 0.0);
+    q[1] = make_double2(z, w);
   }
 };
 

@@ -38,11 +38,13 @@
 #include <vector>
 
 #include "corr.cuh"
+#include "spme.cuh"
 
 namespace otf {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kDefaultBuildKind = 0;  // list build without autotuning: 0 j-parallel, 1 i-parallel
 constexpr int kPairThreads = 128;     // default CTA of the pair kernel (the autotuner may pick 64 or 256)
 constexpr int kMaxPairThreads = 256;
 constexpr int kCellWarps = 4;  // warps (cells) per CTA in the link-cell kernels
@@ -82,6 +84,7 @@ struct Sys {
   int nrep, ntypes, maxnb, always_rebuild, vacf_u;
   double dt, lim2;
   double invm[8], mass[8];
+  double charge[8];            // per type (MD_POT_BUCK_EWALD); the pair records carry it in w
   float hdtm_h[8], hdtm_l[8];  // mixed form: dt / (2 m) per type, double-float
   float dt_h, dt_l;
   const Rep *rep;            // [nrep]
@@ -113,7 +116,10 @@ struct Sys {
 template <typename TF>
 struct LJ {
   TF eps4, eps24, sig2, rc2, ushift, rlist2;
+  // MD_POT_BUCK_EWALD: A exp(-r/rho) - C/r^6 + ke qq erfc(alpha r)/r
+  TF A, inv_rho, C6, alpha, c2, ke;  // c2 = 2 alpha / sqrt(pi)
 };
+constexpr int kPotLJ = 0, kPotBuck = 1;
 
 __device__ __forceinline__ int pack_cell(int x, int y, int z) { return x | (y << 10) | (z << 20); }
 __device__ __forceinline__ void unpack_cell(int c, int &x, int &y, int &z) {
@@ -168,7 +174,7 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift64(Sys d, double hdt) {
     const double px = fma(-(cx + 0.5), edge, x[0]);
     const double py = fma(-(cy + 0.5), edge, x[1]);
     const double pz = fma(-(cz + 0.5), edge, x[2]);
-    Vec4<double>::store(rel + i, px, py, pz);
+    Vec4<double>::store(rel + i, px, py, pz, rel[i].w);
     const dvec4 b = Vec4<double>::load(relb + i);
     const double dx = px - b.x, dy = py - b.y, dz = pz - b.z;
     if ((dx * dx + dy * dy + dz * dz) > d.lim2) request_rebuild(d, d.rep_of_atom[i]);
@@ -207,7 +213,7 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift_df(Sys d) {
       oh[a] = x.h;
       d.offl[a * n + i] = x.l;
     }
-    rel[i] = make_float4(oh[0], oh[1], oh[2], 0.f);
+    rel[i] = make_float4(oh[0], oh[1], oh[2], o.w);
     const float4 b = relb[i];
     const float dx = oh[0] - b.x, dy = oh[1] - b.y, dz = oh[2] - b.z;
     if ((dx * dx + dy * dy + dz * dz) > lim2) request_rebuild(d, d.rep_of_atom[i]);
@@ -405,8 +411,9 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_rb_rank(Sys d) {
           const double px = fma(-(cx + 0.5), R.edge, x[0]);
           const double py = fma(-(cy + 0.5), R.edge, x[1]);
           const double pz = fma(-(cz + 0.5), R.edge, x[2]);
-          Vec4<double>::store(static_cast<dvec4 *>(d.rel) + dst, px, py, pz);
-          Vec4<double>::store(static_cast<dvec4 *>(d.relb) + dst, px, py, pz);
+          const double qc = d.charge[min(max(d.typeB[a], 0), 7)];
+          Vec4<double>::store(static_cast<dvec4 *>(d.rel) + dst, px, py, pz, qc);
+          Vec4<double>::store(static_cast<dvec4 *>(d.relb) + dst, px, py, pz, qc);
         } else {
           const float *oB = reinterpret_cast<const float *>(d.rB);
           const float *wB = reinterpret_cast<const float *>(d.vB);
@@ -418,7 +425,7 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_rb_rank(Sys d) {
             d.vh[q * n + dst] = wB[q * n + a];
             d.vl[q * n + dst] = wB[3 * n + q * n + a];
           }
-          const float4 o = make_float4(oh[0], oh[1], oh[2], 0.f);
+          const float4 o = make_float4(oh[0], oh[1], oh[2], (float)d.charge[min(max(d.typeB[a], 0), 7)]);
           static_cast<float4 *>(d.rel)[dst] = o;
           static_cast<float4 *>(d.relb)[dst] = o;
         }
@@ -432,14 +439,11 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_rb_rank(Sys d) {
 // Shifted LJ pair terms for r2 < rc2 (Sec. 2.3): adds f_ij = fs d to f,
 // U(r) to e and d (x) f_ij to w (the 1/2 of the per-particle split is
 // applied once at the end).
+// Pair force, energy and virial of one pair (r2 < rc2): f += fs d,
+// e += U, w += d (x) (fs d), with fs = -U'(r)/r.  POT selects the
+// interaction; qq is the product of the two charges (unused for LJ).
 template <typename TF>
-__device__ __forceinline__ void lj_accumulate(const LJ<TF> &lj, TF dx, TF dy, TF dz, TF r2, TF f[3],
-                                              TF &e, TF w[6]) {
-  const TF ir2 = pair_rcp(r2);
-  const TF s2 = lj.sig2 * ir2;
-  const TF s6 = s2 * s2 * s2;
-  const TF u = lj.eps4 * s6 * (s6 - TF(1)) - lj.ushift;
-  const TF fs = lj.eps24 * s6 * (s6 + s6 - TF(1)) * ir2;
+__device__ __forceinline__ void pair_add(TF dx, TF dy, TF dz, TF u, TF fs, TF f[3], TF &e, TF w[6]) {
   const TF fx = fs * dx, fy = fs * dy, fz = fs * dz;
   f[0] += fx;
   f[1] += fy;
@@ -451,6 +455,33 @@ __device__ __forceinline__ void lj_accumulate(const LJ<TF> &lj, TF dx, TF dy, TF
   w[3] += dx * fy;
   w[4] += dx * fz;
   w[5] += dy * fz;
+}
+
+template <typename TF, int POT>
+__device__ __forceinline__ void lj_accumulate(const LJ<TF> &lj, TF dx, TF dy, TF dz, TF r2, TF qq, TF f[3],
+                                              TF &e, TF w[6]) {
+  if constexpr (POT == kPotLJ) {
+    const TF ir2 = pair_rcp(r2);
+    const TF s2 = lj.sig2 * ir2;
+    const TF s6 = s2 * s2 * s2;
+    const TF u = lj.eps4 * s6 * (s6 - TF(1)) - lj.ushift;
+    const TF fs = lj.eps24 * s6 * (s6 + s6 - TF(1)) * ir2;
+    pair_add<TF>(dx, dy, dz, u, fs, f, e, w);
+  } else {
+    // Buckingham plus the real-space Ewald term (arXiv 2503.07526 Sec. 5.3;
+    // erfc screening of Essmann et al. 1995)
+    const TF r = sqrt(r2);
+    const TF ir = TF(1) / r;
+    const TF ir2 = ir * ir;
+    const TF ir6 = ir2 * ir2 * ir2;
+    const TF ex = lj.A * exp(-r * lj.inv_rho);
+    const TF ar = lj.alpha * r;
+    const TF ec = erfc(ar);
+    const TF qk = lj.ke * qq;
+    const TF u = ex - lj.C6 * ir6 + qk * ec * ir;
+    const TF mdu = ex * lj.inv_rho - TF(6) * lj.C6 * ir6 * ir + qk * (ec * ir2 + lj.c2 * exp(-ar * ar) * ir);
+    pair_add<TF>(dx, dy, dz, u, mdu * ir, f, e, w);
+  }
 }
 
 template <typename TF>
@@ -477,7 +508,7 @@ __device__ __forceinline__ void image_offset(int code, int &ox, int &oy, int &oz
 // neighbour cells are staged through shared memory 32 atoms at a time,
 // already moved into the i cell's frame; every lane then sweeps the staged
 // atoms (broadcast reads).
-template <typename TF>
+template <typename TF, int POT>
 __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
   using V4 = typename Vec4<TF>::type;
   __shared__ V4 spos[kCellWarps][32];
@@ -512,6 +543,7 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
             t.x = pj.x + offx;
             t.y = pj.y + offy;
             t.z = pj.z + offz;
+            t.w = pj.w;
             spos[wl][lane] = t;
             sidx[wl][lane] = jb + lane;
           }
@@ -526,7 +558,7 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
               const TF dy = pi.y - pj.y;
               const TF dz = pi.z - pj.z;
               const TF r2 = dx * dx + dy * dy + dz * dz;
-              if (r2 < lj.rc2 && sidx[wl][t] != i) lj_accumulate<TF>(lj, dx, dy, dz, r2, f, e, w);
+              if (r2 < lj.rc2 && sidx[wl][t] != i) lj_accumulate<TF, POT>(lj, dx, dy, dz, r2, pi.w * pj.w, f, e, w);
             }
           }
         }
@@ -645,7 +677,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_build(Sys d, LJ<TF> lj) {
 // flight before the arithmetic that needs them.
 constexpr int kUnroll = 4;
 
-template <typename TF>
+template <typename TF, int POT>
 __device__ __forceinline__ void pair_from_entry(const LJ<TF> &lj, const typename Vec4<TF>::type *off,
                                                 uint32_t ent, const typename Vec4<TF>::type &pi,
                                                 const typename Vec4<TF>::type &pj, TF f[3], TF &e, TF w[6]) {
@@ -656,12 +688,12 @@ __device__ __forceinline__ void pair_from_entry(const LJ<TF> &lj, const typename
   const TF dy = pi.y - (pj.y + o.y);
   const TF dz = pi.z - (pj.z + o.z);
   const TF r2 = dx * dx + dy * dy + dz * dz;
-  if (r2 < lj.rc2) lj_accumulate<TF>(lj, dx, dy, dz, r2, f, e, w);
+  if (r2 < lj.rc2) lj_accumulate<TF, POT>(lj, dx, dy, dz, r2, pi.w * pj.w, f, e, w);
 }
 
 // A CTA spans at most two replicas (replicas hold at least kMaxPairThreads
 // atoms), so it keeps the image offsets of both in shared memory.
-template <typename TF>
+template <typename TF, int POT>
 __global__ void __launch_bounds__(kMaxPairThreads) k_pair_list(Sys d, LJ<TF> lj) {
   using V4 = typename Vec4<TF>::type;
   __shared__ V4 offs[2][27];  // image offsets, one vector load per pair
@@ -696,12 +728,12 @@ __global__ void __launch_bounds__(kMaxPairThreads) k_pair_list(Sys d, LJ<TF> lj)
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) pj[u] = Vec4<TF>::load(rel + (ent[u] & 0x07ffffffu));
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) pair_from_entry<TF>(lj, off, ent[u], pi, pj[u], f, e, w);
+    for (int u = 0; u < kUnroll; ++u) pair_from_entry<TF, POT>(lj, off, ent[u], pi, pj[u], f, e, w);
   }
   for (; k < nn; ++k) {
     const uint32_t ent = __ldcs(nb + k * 32);
     const V4 pj = Vec4<TF>::load(rel + (ent & 0x07ffffffu));
-    pair_from_entry<TF>(lj, off, ent, pi, pj, f, e, w);
+    pair_from_entry<TF, POT>(lj, off, ent, pi, pj, f, e, w);
   }
   store_pair_out<TF>(d, i, f, e, w);
 }
@@ -907,7 +939,7 @@ __global__ void k_init_df(Sys d) {
       d.vh[a * n + i] = v.h;
       d.vl[a * n + i] = v.l;
     }
-    rel[i] = make_float4(oh[0], oh[1], oh[2], 0.f);
+    rel[i] = make_float4(oh[0], oh[1], oh[2], (float)d.charge[type_of(d, i)]);
     d.cpk[i] = pack_cell(ci[0], ci[1], ci[2]);
   }
 }
@@ -954,6 +986,86 @@ __global__ void k_unsort(Sys d, double *r, double *v, double *F, double *epot, d
   }
 }
 
+// Verlet-list build, i-parallel: one warp per chunk of 32 consecutive atoms
+// of the cell-sorted order, lane l owning atom a0 + l (the same list layout
+// as k_build).  The chunk's lanes are taken in groups that share a replica
+// and a cell row (y, z) -- one group for most chunks.  A group visits, row by
+// row of its 9 neighbour rows, the x-cells from one left of its leftmost
+// cell to one right of its rightmost (unwrapped, so a cell may come twice
+// when the row is short; the second image is then at least one cell edge
+// away and fails the distance test), every candidate j once for all lanes
+// (one broadcast load), and each lane appends an accepted j to its own list
+// column.  No ballot or shuffle per candidate; the entry order (row, then
+// x-cell, then j) is the order k_build produces.
+template <typename TF, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_build_ip(Sys d, LJ<TF> lj) {
+  using V4 = typename Vec4<TF>::type;
+  if (!any_rebuild(d)) return;
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int64_t n = d.n;
+  const V4 *rel = static_cast<const V4 *>(d.rel);
+  const int64_t nchunks = (n + 31) / 32;
+  for (int64_t q = blockIdx.x * (int64_t)WARPS + wl; q < nchunks; q += (int64_t)gridDim.x * WARPS) {
+    const int64_t i = q * 32 + lane;
+    const bool act = i < n;
+    int r = -1, cx = 0, cy = 0, cz = 0;
+    V4 pi;
+    pi.x = pi.y = pi.z = TF(0);
+    if (act) {
+      r = d.rep_of_atom[i];
+      unpack_cell(d.cpk[i], cx, cy, cz);
+      pi = Vec4<TF>::load(rel + i);
+    }
+    const bool mine = act && rebuilds(d, r);
+    uint32_t *col = d.nbr + q * d.maxnb * 32 + lane;
+    int cnt = 0;
+    unsigned todo = __ballot_sync(0xffffffffu, mine);
+    while (todo) {
+      const int lead = __ffs(todo) - 1;
+      const int gr = __shfl_sync(0xffffffffu, r, lead);
+      const int gy = __shfl_sync(0xffffffffu, cy, lead);
+      const int gz = __shfl_sync(0xffffffffu, cz, lead);
+      const bool in = mine && r == gr && cy == gy && cz == gz;
+      todo &= ~__ballot_sync(0xffffffffu, in);
+      const int xlo = __reduce_min_sync(0xffffffffu, in ? cx : 0x7fffffff) - 1;
+      const int xhi = -__reduce_min_sync(0xffffffffu, in ? -cx : 0x7fffffff) + 1;
+      const Rep &R = d.rep[gr];
+      const int nc = R.nc;
+      const TF edge = (TF)R.edge;
+      for (int row = 0; row < 9; ++row) {
+        const int oy = row % 3 - 1, oz = row / 3 - 1;
+        const int jy = (gy + oy + nc) % nc, jz = (gz + oz + nc) % nc;
+        const int64_t rb = R.cell0 + ((int64_t)jz * nc + jy) * nc;
+        const TF offy = oy * edge, offz = oz * edge;
+        for (int ux = xlo; ux <= xhi; ++ux) {
+          const int jx = (ux + nc) % nc;
+          const int j0 = d.cellstart[rb + jx], j1 = d.cellstart[rb + jx + 1];
+          const int ox = ux - cx;  // this lane's image offset (|ox| <= 1 for an accepted j)
+          const TF offx = ox * edge;
+          const uint32_t code = (uint32_t)((ox + 1) + 3 * row) << 27;
+          for (int j = j0; j < j1; ++j) {
+            const V4 pj = Vec4<TF>::load(rel + j);
+            V4 t;
+            t.x = pj.x + offx;
+            t.y = pj.y + offy;
+            t.z = pj.z + offz;
+            const TF dx = pi.x - t.x, dy = pi.y - t.y, dz = pi.z - t.z;
+            const TF r2 = dx * dx + dy * dy + dz * dz;
+            if (in && r2 < lj.rlist2 && (int64_t)j != i) {
+              if (cnt < d.maxnb) col[(int64_t)cnt * 32] = (uint32_t)j | code;
+              ++cnt;
+            }
+          }
+        }
+      }
+    }
+    if (mine) {
+      d.nnb[i] = min(cnt, d.maxnb);
+      if (cnt > d.maxnb) atomicOr(d.err, ERR_NBR_OVERFLOW);
+    }
+  }
+}
+
 }  // namespace
 }  // namespace otf
 
@@ -970,6 +1082,7 @@ struct md_handle_s {
   int red_blocks = 1;                // reduction CTAs over all replicas
   int pair_threads = kPairThreads;   // launch shapes (autotuned when asked)
   int build_warps = kCellWarps;
+  int build_kind = 0;                // 0: j-parallel k_build, 1: i-parallel k_build_ip
   std::vector<Rep> reps;             // host copy of the descriptor table
   Rep *d_rep = nullptr;
   int *d_rep_of_atom = nullptr, *d_rep_of_cell = nullptr, *d_rep_of_block = nullptr;
@@ -990,6 +1103,7 @@ struct md_handle_s {
   std::vector<int> ev_class;
   double kms[MD_NKCLASS] = {0};
   int64_t klaunch[MD_NKCLASS] = {0};
+  Spme spme;  // reciprocal-space Ewald (MD_POT_BUCK_EWALD)
 };
 
 namespace {
@@ -1010,6 +1124,12 @@ LJ<TF> lj_of(const md_params &p) {
   lj.ushift = (TF)(p.shift ? 4.0 * p.eps * (sr6 * sr6 - sr6) : 0.0);
   const double rl = p.rc + (p.pair_mode == MD_PAIR_VERLET ? p.skin : 0.0);
   lj.rlist2 = (TF)(rl * rl);
+  lj.A = (TF)p.buck_A;
+  lj.inv_rho = (TF)(p.buck_rho > 0 ? 1.0 / p.buck_rho : 0.0);
+  lj.C6 = (TF)p.buck_C;
+  lj.alpha = (TF)p.ewald_alpha;
+  lj.c2 = (TF)(2.0 * p.ewald_alpha / std::sqrt(3.14159265358979323846));
+  lj.ke = (TF)p.coulomb;
   return lj;
 }
 
@@ -1038,6 +1158,13 @@ void launch_build(const md_handle *h, cudaStream_t s) {
   const Sys &d = h->d;
   const int64_t chunks = (d.n + 31) / 32;
   const LJ<TF> lj = lj_of<TF>(h->prm);
+  if (h->build_kind == 1) {
+    if (h->build_warps == 8)
+      k_build_ip<TF, 8><<<std::min(ceil_div(chunks, 8), 152 * 8), 256, 0, s>>>(d, lj);
+    else
+      k_build_ip<TF, 4><<<std::min(ceil_div(chunks, 4), 152 * 16), 128, 0, s>>>(d, lj);
+    return;
+  }
   switch (h->build_warps) {
     case 2:
       k_build<TF, 2><<<std::min(ceil_div(chunks, 2), 152 * 16), 64, 0, s>>>(d, lj);
@@ -1067,16 +1194,41 @@ int launch_rebuild(md_handle *h, cudaStream_t s) {
   return MD_OK;
 }
 
+template <typename TF, int POT>
+void launch_pair_pot(const md_handle *h, cudaStream_t s) {
+  const Sys &d = h->d;
+  if (h->prm.pair_mode == MD_PAIR_VERLET)
+    k_pair_list<TF, POT><<<ceil_div(d.n, h->pair_threads), h->pair_threads, 0, s>>>(d, lj_of<TF>(h->prm));
+  else
+    k_cells<TF, POT><<<std::min(ceil_div(d.ncell, kCellWarps), 152 * 16), kCellWarps * 32, 0, s>>>(
+        d, lj_of<TF>(h->prm));
+}
+
+// Pair forces, then (MD_POT_BUCK_EWALD) the reciprocal-space Ewald terms
+// added on top.
 template <typename TF>
 int launch_pair(md_handle *h, cudaStream_t s) {
   const Sys &d = h->d;
-  KTimer tm(h, s, MD_K_PAIR);
-  if (h->prm.pair_mode == MD_PAIR_VERLET)
-    k_pair_list<TF><<<ceil_div(d.n, h->pair_threads), h->pair_threads, 0, s>>>(d, lj_of<TF>(h->prm));
-  else
-    k_cells<TF><<<std::min(ceil_div(d.ncell, kCellWarps), 152 * 16), kCellWarps * 32, 0, s>>>(
-        d, lj_of<TF>(h->prm));
-  OTF_LAUNCH_CHECK();
+  {
+    KTimer tm(h, s, MD_K_PAIR);
+    if (h->prm.potential == MD_POT_BUCK_EWALD)
+      launch_pair_pot<TF, kPotBuck>(h, s);
+    else
+      launch_pair_pot<TF, kPotLJ>(h, s);
+    OTF_LAUNCH_CHECK();
+  }
+  if (h->spme.on()) {
+    KTimer tm(h, s, MD_K_SPME);
+    SpmeAtoms a;
+    a.n = d.n;
+    a.cpk = d.cpk;
+    a.rel = d.rel;
+    a.offl = d.offl;
+    a.edge = h->reps[0].edge;
+    a.cellstart = d.cellstart;
+    a.nc = h->reps[0].nc;
+    if (int rc = h->spme.run(a, d.F, d.epot, d.W, s)) return rc;
+  }
   return MD_OK;
 }
 
@@ -1182,8 +1334,31 @@ int validate_params(const md_params *p) {
     set_error("md_init: unknown precision");
     return MD_EINVAL;
   }
+  if (p->list_build < 0 || p->list_build > 2) {
+    set_error("md_init: list_build must be 0, 1 or 2");
+    return MD_EINVAL;
+  }
   if (p->pair_mode != MD_PAIR_VERLET && p->pair_mode != MD_PAIR_CELLS) {
     set_error("md_init: unknown pair_mode");
+    return MD_EINVAL;
+  }
+  if (p->potential == MD_POT_BUCK_EWALD) {
+    if (!(p->buck_A >= 0) || !(p->buck_rho > 0) || !(p->buck_C >= 0) || !(p->coulomb > 0) ||
+        !(p->ewald_alpha > 0)) {
+      set_error("md_init: Buckingham-Ewald needs A >= 0, rho > 0, C >= 0, coulomb > 0, ewald_alpha > 0");
+      return MD_EINVAL;
+    }
+    if ((p->order != 4 && p->order != 6 && p->order != 8) || p->mesh < p->order || p->mesh % 2 || p->mesh > 512) {
+      set_error("md_init: SPME needs order 4, 6 or 8 and an even mesh in [order, 512]");
+      return MD_EINVAL;
+    }
+    for (int t = 0; t < p->ntypes; ++t)
+      if (!std::isfinite(p->charge[t])) {
+        set_error("md_init: charge[%d] is not finite", t);
+        return MD_EINVAL;
+      }
+  } else if (p->potential != MD_POT_LJ) {
+    set_error("md_init: unknown potential");
     return MD_EINVAL;
   }
   const corr_spec *cs[3] = {&p->stress, &p->heatflux, &p->vacf};
@@ -1206,6 +1381,14 @@ int validate_replicas(const md_params *p, const md_replica *reps, int count, int
   }
   if (mem != MD_MEM_HOST && mem != MD_MEM_DEVICE) {
     set_error("md_init: mem must be MD_MEM_HOST or MD_MEM_DEVICE");
+    return MD_EINVAL;
+  }
+  if (p->potential == MD_POT_BUCK_EWALD && count > 1) {
+    set_error("md_init: the Buckingham-Ewald potential is for a single system");
+    return MD_EINVAL;
+  }
+  if (p->potential == MD_POT_BUCK_EWALD && !(2.0 * p->rc < reps[0].box)) {
+    set_error("md_init: the real-space cutoff must be below half the box");
     return MD_EINVAL;
   }
   if (count > 1 && p->vacf.u > 0) {
@@ -1269,6 +1452,7 @@ void release(md_handle *h) {
                   h->d_rep_of_atom, h->d_rep_of_cell, h->d_rep_of_block, h->d_lam};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  h->spme.destroy();
   for (int k = 0; k < 3; ++k)
     if (h->bank_on[k]) h->banks[k].c.destroy();
   if (h->h_obs) cudaFreeHost(h->h_obs);
@@ -1298,7 +1482,8 @@ float time_runs(md_handle *h, int reps, Fn fn) {
 }
 
 // Autotuner: times the pair kernel at 64 / 128 / 256 threads per CTA and
-// the list build at 2 / 4 / 8 warps per CTA on the system itself (forces
+// the list build (j-parallel at 2 / 4 / 8 warps per CTA, i-parallel at 4 / 8)
+// on the system itself (forces
 // and lists are recomputed from the unchanged state, so the trajectory is
 // not touched) and keeps the fastest of each.
 template <typename TF>
@@ -1313,16 +1498,19 @@ int autotune(md_handle *h) {
   }
   h->pair_threads = best_t;
   best = 1e30f;
-  int best_w = h->build_warps;
-  for (int w : {2, 4, 8}) {
-    h->build_warps = w;
+  int best_w = h->build_warps, best_k = h->build_kind;
+  const int shapes[5][2] = {{0, 2}, {0, 4}, {0, 8}, {1, 4}, {1, 8}};
+  for (const auto &kw : shapes) {
+    h->build_kind = kw[0];
+    h->build_warps = kw[1];
     const float ms = time_runs(h, 3, [&] {
       cudaMemsetAsync(h->d.rebuild, 1, (h->nrep + 1) * sizeof(int), h->stream);
       launch_build<TF>(h, h->stream);
     });
-    if (ms < best) best = ms, best_w = w;
+    if (ms < best) best = ms, best_w = kw[1], best_k = kw[0];
   }
   h->build_warps = best_w;
+  h->build_kind = best_k;
   // rebuild the lists once more with the chosen shape, then the forces
   OTF_CUDA(cudaMemsetAsync(h->d.rebuild, 1, (h->nrep + 1) * sizeof(int), h->stream));
   launch_build<TF>(h, h->stream);
@@ -1335,6 +1523,7 @@ int autotune(md_handle *h) {
 
 int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int count, int mem) {
   h->prm = *p;
+  h->build_kind = p->list_build == 0 ? kDefaultBuildKind : p->list_build - 1;
   h->fp64 = p->precision == MD_PREC_FP64;
   h->nrep = count;
   Sys &d = h->d;
@@ -1373,6 +1562,7 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   for (int t = 0; t < 8; ++t) {
     d.mass[t] = t < p->ntypes ? p->mass[t] : 1.0;
     d.invm[t] = 1.0 / d.mass[t];
+    d.charge[t] = (p->potential == MD_POT_BUCK_EWALD && t < p->ntypes) ? p->charge[t] : 0.0;
   }
   int maxnb = p->max_neighbors;
   if (maxnb <= 0) {
@@ -1510,6 +1700,15 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   // initial layout, forces and observables
   int rc = h->fp64 ? launch_rebuild<double>(h, st) : launch_rebuild<float>(h, st);
   if (rc) return rc;
+  if (p->potential == MD_POT_BUCK_EWALD) {
+    SpmeParams sp;
+    sp.K = p->mesh;
+    sp.order = p->order;
+    sp.L = h->reps[0].L;
+    sp.alpha = p->ewald_alpha;
+    sp.ke = p->coulomb;
+    if ((rc = h->spme.create(sp, h->fp64, st))) return rc;
+  }
   rc = h->fp64 ? launch_pair<double>(h, st) : launch_pair<float>(h, st);
   if (rc) return rc;
   if ((rc = refresh_obs(h))) return rc;
@@ -1779,6 +1978,7 @@ int md_get_config(md_handle *h, md_config *out) {
   out->max_neighbors = h->d.maxnb;
   out->pair_threads = h->pair_threads;
   out->build_warps = h->build_warps;
+  out->build_kind = h->build_kind;
   return MD_OK;
 }
 

@@ -9,10 +9,14 @@ a tensor-core network trained to output the Green-Kubo viscosity and thermal
 conductivity (Sec. 2.3) that a much longer run of the same replica reaches.
 The long run's correlator integral is the training target and the judge.
 The short run's own integral is the fallback: it is returned outside the
-temperature-density box of the training set, and wherever the run is large
-or long enough that this integral is expected to be more accurate than the
-network (its error falls as 1/sqrt(atoms x steps); the network's is measured
-on validation replicas).
+temperature-density box of the training set, and wherever the run is long
+enough that this integral is expected to be more accurate than the network.
+The expected error of a run's own integral falls as 1/sqrt(steps) and does
+not fall with the number of atoms: the Green-Kubo integrand is the
+autocorrelation of one global flux, whose relative fluctuation is the same
+for any box size (measured on 4,096 replicas of 500 to 32,000 atoms: 0.29 to
+0.31 rms at every size).  The network's error is measured on validation
+replicas.
 """
 from __future__ import annotations
 
@@ -144,7 +148,7 @@ class LearnedTail:
                             stream=stream)
         self.box = None
         self.val_error = None    # rms relative error of (eta, kappa) on the validation replicas
-        self.short_coeff = None  # short-run rms relative error ~ coeff / sqrt(atoms x steps)
+        self.short_coeff = None  # short-run rms relative error ~ coeff / sqrt(steps)
 
     def fit(self, train, val, epochs, shuffle_seed=1):
         """train, val: dicts as returned by generate() (rows with a
@@ -159,10 +163,10 @@ class LearnedTail:
         va = _usable(val)
         eta, kappa = self._net(val["X"][va])
         self.val_error = (_rms_rel(eta, val["eta_long"][va]), _rms_rel(kappa, val["kappa_long"][va]))
-        # the short-run integral's error falls as 1/sqrt(atoms x steps)
+        # the short-run integral's error falls as 1/sqrt(steps), whatever the size
         both = {k: np.concatenate([train[k][tr], val[k][va]])
-                for k in ("eta_short", "kappa_short", "eta_long", "kappa_long", "atoms", "steps_short")}
-        w = np.sqrt(both["atoms"] * both["steps_short"])
+                for k in ("eta_short", "kappa_short", "eta_long", "kappa_long", "steps_short")}
+        w = np.sqrt(both["steps_short"])
         self.short_coeff = tuple(float(np.sqrt(np.mean(((both[k + "_short"] - both[k + "_long"]) /
                                                         both[k + "_long"] * w) ** 2))) for k in ("eta", "kappa"))
         return hist
@@ -171,16 +175,16 @@ class LearnedTail:
         Y = self.net.forward(np.ascontiguousarray(X, dtype=np.float32))
         return np.exp(Y[:, 0].astype(np.float64)), np.exp(Y[:, 1].astype(np.float64))
 
-    def predict(self, X, eta_short, kappa_short, atoms, steps):
+    def predict(self, X, eta_short, kappa_short, steps):
         """(eta, kappa, used_eta, used_kappa): per output, the network's value
-        where the run lies in the training box and its short-run integral is
-        expected to be less accurate than the network; elsewhere the
-        short-run integral."""
+        where the run lies in the training box and its own integral (after
+        `steps` correlated steps) is expected to be less accurate than the
+        network; elsewhere the run's own integral."""
         X = np.ascontiguousarray(X, dtype=np.float32)
         eta, kappa = self._net(X)
         T0, T1, r0, r1 = self.box
         inside = (X[:, 130] >= T0) & (X[:, 130] <= T1) & (X[:, 131] >= r0) & (X[:, 131] <= r1)
-        w = np.sqrt(np.asarray(atoms, dtype=np.float64) * np.asarray(steps, dtype=np.float64))
+        w = np.sqrt(np.asarray(steps, dtype=np.float64))
         use_e = inside & (self.short_coeff[0] / w > self.val_error[0])
         use_k = inside & (self.short_coeff[1] / w > self.val_error[1])
         return (np.where(use_e, eta, eta_short), np.where(use_k, kappa, kappa_short), use_e, use_k)

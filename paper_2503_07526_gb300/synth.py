@@ -119,3 +119,34 @@ def permutations(seed: int, count: int, n: int) -> np.ndarray:
     by sorting SplitMix64 keys (ties broken by index)."""
     keys = splitmix64(seed, count * n).reshape(count, n)
     return np.argsort(keys, axis=1, kind="stable").astype(np.int64)
+
+
+def rock_salt_lattice(cells: int, rho: float):
+    """Ions of a rock-salt crystal of number density rho (cells^3 cubic
+    unit cells of 8 ions) in a periodic cubic box, shifted by a quarter
+    spacing: positions [3, n] (cations first, then anions), types (0 for
+    cations, 1 for anions) and the box side."""
+    a = (8.0 / rho) ** (1.0 / 3.0)
+    base = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.0], [0.5, 0.0, 0.5], [0.0, 0.5, 0.5]])
+    g = np.arange(cells, dtype=np.float64)
+    cz, cy, cx = np.meshgrid(g, g, g, indexing="ij")
+    org = np.stack([cx.ravel(), cy.ravel(), cz.ravel()], axis=1)
+    cat = (org[:, None, :] + base[None] + 0.25).reshape(-1, 3)
+    an = (org[:, None, :] + base[None] + np.array([0.75, 0.25, 0.25])).reshape(-1, 3)
+    pos = np.concatenate([cat, an]) * a
+    types = np.concatenate([np.zeros(len(cat), dtype=np.int32), np.ones(len(an), dtype=np.int32)])
+    return np.ascontiguousarray(pos.T), types, cells * a
+
+
+def ionic_system(cells: int, rho: float, T: float, seed: int, masses=(22.99, 35.45), jitter: float = 0.0):
+    """A binary ionic melt start: a rock-salt lattice of number density rho
+    with every ion displaced uniformly by up to +-jitter per axis, and
+    Maxwell-Boltzmann velocities at temperature T (kB = 1, in the caller's
+    energy unit) for the two masses.  Returns dict(r, v, types, L, n, masses)."""
+    r, types, L = rock_salt_lattice(cells, rho)
+    n = r.shape[1]
+    if jitter:
+        r = r + jitter * (2.0 * uniform01(seed + 77, 3 * n).reshape(3, n) - 1.0)
+    m = np.asarray(masses, dtype=np.float64)[types]
+    v = maxwell_velocities(n, T, seed, masses_of=m)
+    return dict(r=np.ascontiguousarray(r), v=v, types=types, L=L, n=n, masses=np.asarray(masses, dtype=np.float64))

@@ -8,8 +8,8 @@ targets, and the judge).  The network is trained on replicas 0-255 by its
 own tensor-core kernels, validated on 256-383 and judged on 384-511: its
 eta and kappa must sit closer to the long-run integrals than the short-run
 integrals do (root-mean-square relative error, both against the same long
-run).  The fallback rule must send a run of 16 million atoms back to its own
-integral."""
+run).  The fallback rule must send a long run (200,000 steps) back to its
+own integral, and keep the network for a short run of any size."""
 import numpy as np
 import pytest
 
@@ -42,7 +42,7 @@ def test_learned_tail_beats_the_short_run_integral(pkg):
     m = lt.LearnedTail(lr=1e-3, weight_decay=1e-3, seed=1)
     hist = m.fit(tr, va, epochs=30)
     assert hist[-1] < 0.5 * hist[0]
-    eta, kappa, ue, uk = m.predict(te["X"], te["eta_short"], te["kappa_short"], te["atoms"], te["steps_short"])
+    eta, kappa, ue, uk = m.predict(te["X"], te["eta_short"], te["kappa_short"], te["steps_short"])
     e_net, e_short = rms_rel(eta, te["eta_long"]), rms_rel(te["eta_short"], te["eta_long"])
     k_net, k_short = rms_rel(kappa, te["kappa_long"]), rms_rel(te["kappa_short"], te["kappa_long"])
     print(f"eta: learned tail {e_net:.3f}, short-run integral {e_short:.3f}; kappa: learned tail {k_net:.3f}, "
@@ -50,9 +50,11 @@ def test_learned_tail_beats_the_short_run_integral(pkg):
           f"error {m.val_error}, short-run coefficients {m.short_coeff}")
     assert e_net < 0.75 * e_short
     assert k_net < 0.75 * k_short
-    # fallback: outside the training box, and for a run whose own integral is precise
-    X2 = te["X"][:2].copy()
+    # fallback: outside the training box, and for a run long enough that its
+    # own integral is the more precise
+    X2 = te["X"][:3].copy()
     X2[0, 130] = 5.0
-    e2, k2, u2e, u2k = m.predict(X2, te["eta_short"][:2], te["kappa_short"][:2], [2000, 16_384_000], [2000, 5000])
+    e2, k2, u2e, u2k = m.predict(X2, te["eta_short"][:3], te["kappa_short"][:3], [2000, 200_000, 5000])
     assert not u2e[0] and not u2k[0] and e2[0] == te["eta_short"][0] and k2[0] == te["kappa_short"][0]
     assert not u2e[1] and not u2k[1] and e2[1] == te["eta_short"][1]
+    assert u2e[2] and u2k[2]
