@@ -399,7 +399,8 @@ def run_ionic(pkg, synth, torch, steps=100, fp64_steps=10, cells=None):
                        f"Ewald ({c['mesh']}^3 mesh, order {c['order']}, alpha {c['alpha']}/A, rc {c['rc']} A), "
                        "dt 1 fs, stress and heat-flux correlators with per-particle reciprocal energy and virial",
            "n_ions": n}
-    for name, prec, k in (("mixed", pkg.MD_PREC_MIXED, steps), ("fp64_gpu", pkg.MD_PREC_FP64, fp64_steps)):
+    forms = [("mixed", pkg.MD_PREC_MIXED, steps)] + ([("fp64_gpu", pkg.MD_PREC_FP64, fp64_steps)] if fp64_steps else [])
+    for name, prec, k in forms:
         p = pkg.make_params(n, L, rc=c["rc"], dt=c["dt_fs"] / FS_PER_UNIT, skin=c["skin"], precision=prec,
                             masses=c["masses"], potential=pkg.MD_POT_BUCK_EWALD, charges=(1.0, -1.0),
                             buckingham=(c["A"], c["brho"], c["C"]), ewald_alpha=c["alpha"], mesh=c["mesh"],
@@ -424,7 +425,8 @@ def run_ionic(pkg, synth, torch, steps=100, fp64_steps=10, cells=None):
         out[name] = {"atom_steps_per_s": n * k / sec_graph, "ms_per_step": 1e3 * sec_graph / k, "steps": k,
                      "kernel_ms_per_step": {kk: v[0] / k for kk, v in kt.items()},
                      "T_K": o["T"] / KB_EV, "rebuilds": o["rebuilds"]}
-    out["speedup_mixed_over_fp64"] = out["mixed"]["atom_steps_per_s"] / out["fp64_gpu"]["atom_steps_per_s"]
+    if fp64_steps:
+        out["speedup_mixed_over_fp64"] = out["mixed"]["atom_steps_per_s"] / out["fp64_gpu"]["atom_steps_per_s"]
     return out
 
 
@@ -725,6 +727,8 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the replica ensemble and time-to-viscosity")
     ap.add_argument("--cells", type=int, default=CELLS, help="fcc cells per side (4 cells^3 atoms)")
     ap.add_argument("--quick", action="store_true", help="short melt, timed region only (for profilers)")
+    ap.add_argument("--ionic-only", action="store_true",
+                    help="run only the ionic melt for --steps steps (mixed form; with --quick no FP64 form)")
     ap.add_argument("--learned-tail-full", action="store_true",
                     help="run only the full learned-tail workload (4,096 replicas, 16.4M-atom judge)")
     ap.add_argument("--lt-replicas", type=int, default=4096)
@@ -734,7 +738,16 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.learned_tail_full:
+    if args.ionic_only:
+        import torch
+
+        import paper_2503_07526_gb300 as pkg
+        from paper_2503_07526_gb300 import synth
+
+        pkg.lib()
+        print(json.dumps(run_ionic(pkg, synth, torch, steps=args.steps,
+                                   fp64_steps=0 if args.quick else max(1, args.steps // 10))), flush=True)
+    elif args.learned_tail_full:
         run_learned_tail_full(args)
     elif args.impl == "reference":
         run_reference(args)
