@@ -66,6 +66,15 @@ extern "C" {
 #define MD_CORR_HEATFLUX 1 /* 3 series: q_x, q_y, q_z */
 #define MD_CORR_VACF 2     /* 3n series: v_x of every atom, then v_y, then v_z;
                               read out per component, averaged over atoms */
+#define MD_CORR_MASSFLUX 3 /* cross correlator, 6 series per replica:
+                              <q_a(0) j_a(t)> for a = x, y, z, then
+                              <j_a(0) j_a(t)>, with j the partial momentum
+                              density of one species (Sec. 2.3, multi-component
+                              kappa).  For a binary system (total momentum
+                              zero) the mass-flux corrected conductivity is
+                              V/T^2 [I_qq - I_qj^2 / I_jj], I the time
+                              integrals of the component means of the heat-flux,
+                              cross and partial momentum correlations. */
 
 /* Interaction (md_params.potential). */
 #define MD_POT_LJ 0          /* Lennard-Jones (eps, sigma), optionally energy-shifted */
@@ -119,6 +128,9 @@ typedef struct {
   int32_t mesh;       /* MD_POT_BUCK_EWALD: SPME mesh points per side (even,
                          >= order) */
   int32_t order;      /* MD_POT_BUCK_EWALD: B-spline order: 4, 6 or 8 */
+  int32_t flux_species; /* atom type whose partial momentum density j is
+                         observed and correlated with q (MD_CORR_MASSFLUX) */
+  corr_spec massflux; /* MD_CORR_MASSFLUX settings (u = 0: off) */
 } md_params;
 
 typedef struct {
@@ -156,6 +168,8 @@ typedef struct {
   double q[3];         /* heat flux: sum_i (E_i v_i + W_i v_i) / V */
   double T_mean;       /* mean of T over the steps since md_init */
   int64_t rebuilds;    /* cell sorts / neighbour-list builds since md_init */
+  double j[3];         /* partial momentum density of the flux species:
+                          sum over its atoms of m v / V */
 } md_obs;
 
 typedef struct md_handle_s md_handle;

@@ -11,6 +11,7 @@ marshals arguments.
 from ._lib import (  # noqa: F401
     EXPORTS,
     MD_CORR_HEATFLUX,
+    MD_CORR_MASSFLUX,
     MD_CORR_STRESS,
     MD_CORR_VACF,
     MD_K_NAMES,

@@ -17,7 +17,7 @@ from . import build_lib
 MD_OK, MD_EINVAL, MD_ENOMEM, MD_ECUDA, MD_ESTATE, MD_ETIMEOUT, MD_ECAP = 0, -1, -2, -3, -4, -5, -6
 MD_PREC_FP64, MD_PREC_MIXED = 0, 1
 MD_MEM_HOST, MD_MEM_DEVICE = 0, 1
-MD_CORR_STRESS, MD_CORR_HEATFLUX, MD_CORR_VACF = 0, 1, 2
+MD_CORR_STRESS, MD_CORR_HEATFLUX, MD_CORR_VACF, MD_CORR_MASSFLUX = 0, 1, 2, 3
 MD_PAIR_VERLET, MD_PAIR_CELLS = 0, 1
 MD_POT_LJ, MD_POT_BUCK_EWALD = 0, 1
 MD_K_NAMES = ("integrate", "rebuild", "pair", "reduce", "vacf", "spme")
@@ -46,7 +46,7 @@ class md_params(C.Structure):
                 ("heatflux", corr_spec), ("vacf", corr_spec), ("list_build", C.c_int32),
                 ("potential", C.c_int32), ("charge", C.c_double * 8), ("buck_A", C.c_double), ("buck_rho", C.c_double),
                 ("buck_C", C.c_double), ("coulomb", C.c_double), ("ewald_alpha", C.c_double), ("mesh", C.c_int32),
-                ("order", C.c_int32)]
+                ("order", C.c_int32), ("flux_species", C.c_int32), ("massflux", corr_spec)]
 
 
 class md_system(C.Structure):
@@ -66,7 +66,7 @@ class md_config(C.Structure):
 class md_obs(C.Structure):
     _fields_ = [("step", C.c_int64), ("U", C.c_double), ("K", C.c_double), ("T", C.c_double),
                 ("sigma", C.c_double * 6), ("q", C.c_double * 3), ("T_mean", C.c_double),
-                ("rebuilds", C.c_int64)]
+                ("rebuilds", C.c_int64), ("j", C.c_double * 3)]
 
 
 class corr_params(C.Structure):
@@ -216,7 +216,7 @@ def make_params(n, box, *, eps=1.0, sigma=1.0, rc=2.5, shift=True, masses=(1.0,)
                 precision=MD_PREC_FP64, pair_mode=MD_PAIR_VERLET, skin=0.3, max_neighbors=0, use_graph=True,
                 autotune=False, stress=(12, 16, 2, 1), heatflux=(12, 16, 2, 1), vacf=(8, 16, 2, 1), list_build=0,
                 potential=MD_POT_LJ, charges=(), buckingham=(0.0, 1.0, 0.0), coulomb=KE_EV_ANGSTROM, ewald_alpha=0.0,
-                mesh=0, order=8):
+                mesh=0, order=8, flux_species=0, massflux=None):
     p = md_params()
     p.n, p.box, p.eps, p.sigma, p.rc, p.shift = int(n), float(box), eps, sigma, rc, int(bool(shift))
     p.ntypes = len(masses)
@@ -230,7 +230,8 @@ def make_params(n, box, *, eps=1.0, sigma=1.0, rc=2.5, shift=True, masses=(1.0,)
         p.charge[t] = float(q)
     p.buck_A, p.buck_rho, p.buck_C = (float(x) for x in buckingham)
     p.coulomb, p.ewald_alpha, p.mesh, p.order = float(coulomb), float(ewald_alpha), int(mesh), int(order)
-    for name, spec in (("stress", stress), ("heatflux", heatflux), ("vacf", vacf)):
+    p.flux_species = int(flux_species)
+    for name, spec in (("stress", stress), ("heatflux", heatflux), ("vacf", vacf), ("massflux", massflux)):
         cs = getattr(p, name)
         cs.b, cs.p, cs.m, cs.u = spec if spec is not None else (1, 2, 1, 0)
     return p
@@ -360,7 +361,7 @@ class System:
         o = md_obs()
         _check(lib().md_replica_observables(self._h, int(r), C.byref(o)))
         return dict(step=o.step, U=o.U, K=o.K, T=o.T, sigma=np.array(o.sigma[:]), q=np.array(o.q[:]),
-                    T_mean=o.T_mean, rebuilds=o.rebuilds)
+                    T_mean=o.T_mean, rebuilds=o.rebuilds, j=np.array(o.j[:]))
 
     def replica_observables_all(self):
         """Every replica's observables in one device read: dict of arrays
@@ -370,7 +371,7 @@ class System:
         return dict(step=arr[0].step, rebuilds=arr[0].rebuilds,
                     U=np.array([o.U for o in arr]), K=np.array([o.K for o in arr]), T=np.array([o.T for o in arr]),
                     sigma=np.array([o.sigma[:] for o in arr]), q=np.array([o.q[:] for o in arr]),
-                    T_mean=np.array([o.T_mean for o in arr]))
+                    T_mean=np.array([o.T_mean for o in arr]), j=np.array([o.j[:] for o in arr]))
 
     def replica_scale_velocities(self, lams):
         lam = np.ascontiguousarray(lams, dtype=np.float64)
@@ -390,7 +391,7 @@ class System:
         o = md_obs()
         _check(lib().md_observables(self._h, C.byref(o)))
         return dict(step=o.step, U=o.U, K=o.K, T=o.T, sigma=np.array(o.sigma[:]), q=np.array(o.q[:]),
-                    T_mean=o.T_mean, rebuilds=o.rebuilds)
+                    T_mean=o.T_mean, rebuilds=o.rebuilds, j=np.array(o.j[:]))
 
     def particles(self):
         n = self.n
@@ -413,9 +414,14 @@ class System:
     def corr(self, which):
         h = C.c_void_p()
         _check(lib().md_corr(self._h, int(which), C.byref(h)))
-        spec = (self.params.stress, self.params.heatflux, self.params.vacf)[which]
-        ns, ng = (3 * self.n, 3) if which == MD_CORR_VACF else (3 * self.nrep, 3 * self.nrep)
-        return Corr(h, False, ns, ng, False, spec.b, spec.p, keep=self)
+        spec = (self.params.stress, self.params.heatflux, self.params.vacf, self.params.massflux)[which]
+        if which == MD_CORR_VACF:
+            ns, ng = 3 * self.n, 3
+        elif which == MD_CORR_MASSFLUX:
+            ns, ng = 6 * self.nrep, 6 * self.nrep
+        else:
+            ns, ng = 3 * self.nrep, 3 * self.nrep
+        return Corr(h, False, ns, ng, which == MD_CORR_MASSFLUX, spec.b, spec.p, keep=self)
 
     def set_timing(self, on=True):
         _check(lib().md_set_timing(self._h, int(bool(on))))

@@ -48,7 +48,8 @@ constexpr int kDefaultBuildKind = 0;  // list build without autotuning: 0 j-para
 constexpr int kPairThreads = 128;     // default CTA of the pair kernel (the autotuner may pick 64 or 256)
 constexpr int kMaxPairThreads = 256;
 constexpr int kCellWarps = 4;  // warps (cells) per CTA in the link-cell kernels
-constexpr int kNRed = 11;      // K, U, V*sigma[6], V*q[3]
+constexpr int kNRed = 14;      // K, U, V*sigma[6], V*q[3], V*j[3]
+constexpr int kNBanks = 4;     // stress, heat flux, velocity, mass flux
 constexpr int kMaxRedBlocks = 152 * 4;
 
 // Step counters shared by all replicas.
@@ -66,6 +67,7 @@ struct ObsDev {
   double sigma[6];
   double q[3];
   double Tsum;
+  double j[3];  // partial momentum density of the flux species
 };
 
 // Constants of one replica.  Its atoms occupy [atom0, atom1) of the
@@ -85,6 +87,7 @@ struct Sys {
   double dt, lim2;
   double invm[8], mass[8];
   double charge[8];            // per type (MD_POT_BUCK_EWALD); the pair records carry it in w
+  int flux_species;            // type whose partial momentum density is observed
   float hdtm_h[8], hdtm_l[8];  // mixed form: dt / (2 m) per type, double-float
   float dt_h, dt_l;
   const Rep *rep;            // [nrep]
@@ -753,7 +756,7 @@ __global__ void __launch_bounds__(kMaxPairThreads) k_pair_list(Sys d, LJ<TF> lj)
 // scattered to atom-id order.
 template <typename TF, typename A, bool KICK>
 __global__ void __launch_bounds__(kThreads)
-    k_kick_reduce(Sys d, double hdt, CorrDev cs, int64_t us, CorrDev ch, int64_t uh) {
+    k_kick_reduce(Sys d, double hdt, CorrDev cs, int64_t us, CorrDev ch, int64_t uh, CorrDev cm, int64_t um) {
   __shared__ double red[kThreads / 32][kNRed];
   __shared__ double tot[kNRed];
   __shared__ int last;
@@ -822,6 +825,10 @@ __global__ void __launch_bounds__(kThreads)
     acc[8] += E * vx + w[0] * vx + w[3] * vy + w[4] * vz;
     acc[9] += E * vy + w[3] * vx + w[1] * vy + w[5] * vz;
     acc[10] += E * vz + w[4] * vx + w[5] * vy + w[2] * vz;
+    const A sel = t == d.flux_species ? m : A(0);
+    acc[11] += sel * vx;
+    acc[12] += sel * vy;
+    acc[13] += sel * vz;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -857,6 +864,7 @@ __global__ void __launch_bounds__(kThreads)
     ow->T = nr > 1 ? 2.0 * tot[0] / (3.0 * (double)nr - 3.0) : 0.0;
     for (int a = 0; a < 6; ++a) ow->sigma[a] = tot[2 + a] / V;
     for (int a = 0; a < 3; ++a) ow->q[a] = tot[8 + a] / V;
+    for (int a = 0; a < 3; ++a) ow->j[a] = tot[11 + a] / V;
     if (KICK) {
       ow->Tsum += ow->T;
       ow->Tn += 1;
@@ -872,6 +880,12 @@ __global__ void __launch_bounds__(kThreads)
     } else if (tid >= 3 && tid < 6 && uh > 0 && ch.b > 0 && tc % uh == 0) {
       const double x = tot[8 + tid - 3] / V;  // q_x, q_y, q_z
       push_one_series<double>(ch, 3 * r + tid - 3, x, x, tc / uh);
+    } else if (tid >= 6 && tid < 12 && um > 0 && cm.b > 0 && tc % um == 0) {
+      // (q_a, j_a) then (j_a, j_a): series 6r .. 6r+5 of the cross correlator
+      const int a = (tid - 6) % 3;
+      const double y = tot[11 + a] / V;
+      const double x = tid < 9 ? tot[8 + a] / V : y;
+      push_one_series<double>(cm, 6 * r + tid - 6, x, y, tc / um);
     }
   }
   // the last replica to finish closes the step
@@ -1089,8 +1103,8 @@ struct md_handle_s {
   double *d_lam = nullptr;
   int64_t steps_done = 0;
   int64_t corr_base = 0;
-  corr_handle banks[3];  // system-owned correlators (borrowed by md_corr)
-  bool bank_on[3] = {false, false, false};
+  corr_handle banks[kNBanks];  // system-owned correlators (borrowed by md_corr)
+  bool bank_on[kNBanks] = {false, false, false, false};
   double *d_out = nullptr;  // unsort staging [16][n]
   ObsDev *h_obs = nullptr;  // pinned [nrep]
   StepDev *h_st = nullptr;  // pinned
@@ -1238,8 +1252,10 @@ int launch_reduce(md_handle *h, cudaStream_t s) {
   const Sys &d = h->d;
   CorrDev cs = h->bank_on[0] ? h->banks[0].c.dev : CorrDev{};
   CorrDev ch = h->bank_on[1] ? h->banks[1].c.dev : CorrDev{};
+  CorrDev cm = h->bank_on[3] ? h->banks[3].c.dev : CorrDev{};
   k_kick_reduce<TF, A, KICK><<<h->red_blocks, kThreads, 0, s>>>(
-      d, 0.5 * h->prm.dt, cs, h->bank_on[0] ? h->prm.stress.u : 0, ch, h->bank_on[1] ? h->prm.heatflux.u : 0);
+      d, 0.5 * h->prm.dt, cs, h->bank_on[0] ? h->prm.stress.u : 0, ch, h->bank_on[1] ? h->prm.heatflux.u : 0, cm,
+      h->bank_on[3] ? h->prm.massflux.u : 0);
   OTF_LAUNCH_CHECK();
   return MD_OK;
 }
@@ -1361,8 +1377,12 @@ int validate_params(const md_params *p) {
     set_error("md_init: unknown potential");
     return MD_EINVAL;
   }
-  const corr_spec *cs[3] = {&p->stress, &p->heatflux, &p->vacf};
-  for (int k = 0; k < 3; ++k) {
+  if (p->flux_species < 0 || p->flux_species >= p->ntypes) {
+    set_error("md_init: flux_species must be a type in [0, ntypes)");
+    return MD_EINVAL;
+  }
+  const corr_spec *cs[kNBanks] = {&p->stress, &p->heatflux, &p->vacf, &p->massflux};
+  for (int k = 0; k < kNBanks; ++k) {
     if (cs[k]->u < 0) {
       set_error("md_init: correlator update interval must be >= 0");
       return MD_EINVAL;
@@ -1453,7 +1473,7 @@ void release(md_handle *h) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   h->spme.destroy();
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < kNBanks; ++k)
     if (h->bank_on[k]) h->banks[k].c.destroy();
   if (h->h_obs) cudaFreeHost(h->h_obs);
   if (h->h_st) cudaFreeHost(h->h_st);
@@ -1564,6 +1584,7 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
     d.invm[t] = 1.0 / d.mass[t];
     d.charge[t] = (p->potential == MD_POT_BUCK_EWALD && t < p->ntypes) ? p->charge[t] : 0.0;
   }
+  d.flux_species = p->flux_species;
   int maxnb = p->max_neighbors;
   if (maxnb <= 0) {
     const double mean = rho_max * 4.18879020478639 * rl * rl * rl;
@@ -1683,10 +1704,12 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   OTF_CUDA(cudaStreamSynchronize(st));
   // correlators: stress and heat flux have 3 series per replica, the
   // velocity correlator 3n series in 3 groups (single system)
-  const corr_spec *specs[3] = {&p->stress, &p->heatflux, &p->vacf};
-  for (int k = 0; k < 3; ++k) {
+  // and the mass-flux cross correlator 6 series per replica
+  const corr_spec *specs[kNBanks] = {&p->stress, &p->heatflux, &p->vacf, &p->massflux};
+  for (int k = 0; k < kNBanks; ++k) {
     if (specs[k]->u <= 0) continue;
-    corr_params cp{specs[k]->b, specs[k]->p, specs[k]->m, 0, k == 2 ? 3 * n : 3 * (int64_t)count, k == 2 ? n : 1,
+    const int64_t ns = k == 2 ? 3 * n : (k == 3 ? 6 : 3) * (int64_t)count;
+    corr_params cp{specs[k]->b, specs[k]->p, specs[k]->m, k == 3 ? 1 : 0, ns, k == 2 ? n : 1,
                    k == 2 ? p->precision : MD_PREC_FP64, specs[k]->u * p->dt};
     Correlator &c = h->banks[k].c;
     h->bank_on[k] = true;
@@ -1732,6 +1755,7 @@ void fill_obs(const md_handle *h, int r, md_obs *out) {
   for (int a = 0; a < 3; ++a) out->q[a] = o.q[a];
   out->T_mean = o.Tn > 0 ? o.Tsum / (double)o.Tn : o.T;
   out->rebuilds = h->h_st->rebuilds;
+  for (int a = 0; a < 3; ++a) out->j[a] = o.j[a];
 }
 
 int fetch_obs(md_handle *h) {
@@ -1932,7 +1956,7 @@ int md_replica_scale_velocities(md_handle *h, const double *lambda) {
 int md_reset_correlators(md_handle *h) {
   clear_error();
   if (!h) return MD_EINVAL;
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < kNBanks; ++k)
     if (h->bank_on[k]) {
       int rc = h->banks[k].c.reset();
       if (rc) return rc;
@@ -1954,7 +1978,7 @@ int md_reset_correlators(md_handle *h) {
 
 int md_corr(md_handle *h, int32_t which, corr_handle **out) {
   clear_error();
-  if (!h || !out || which < 0 || which > 2) {
+  if (!h || !out || which < 0 || which >= kNBanks) {
     set_error("md_corr: bad argument");
     return MD_EINVAL;
   }

@@ -200,4 +200,4 @@ def _rms_rel(a, b):
 
 def split(d, rows):
     """The rows `rows` (a slice or index array) of a generate() result."""
-    return {k: (v[rows] if isinstance(v, np.ndarray) else v) for k, v in d.items()}
+    return {k: (v[rows] if isinstance(v, np.ndarray) and v.ndim > 0 else v) for k, v in d.items()}

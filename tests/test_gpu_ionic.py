@@ -112,6 +112,43 @@ def test_observables_match_oracle(pkg, system, precision, oracle_mod):
     assert rel(o["q"], want[9:12]) <= max(tol, 1e-4 if precision else tol)
 
 
+def test_mass_flux_correlations(pkg, system, oracle_mod):
+    """The partial momentum density of the cations, j = sum m v / V over
+    them, and its correlations with the heat flux (Sec. 2.3, the mass-flux
+    correction of kappa for multi-component systems): j against its
+    definition from the velocities (and against minus the anions' share:
+    total momentum is zero), and the device's cross correlator against the
+    oracle's correlator fed the same per-step (q, j) samples."""
+    s = system
+    p = params(pkg, s, 0, mesh=16)
+    p.massflux.b, p.massflux.p, p.massflux.m, p.massflux.u = 4, 16, 2, 1
+    g = pkg.System(p, s["r"], s["v"], types=s["types"])
+    qs, js = [], []
+    for _ in range(80):
+        g.step(1)
+        o = g.observables()
+        qs.append(o["q"])
+        js.append(o["j"])
+    part = g.particles()
+    V = s["L"] ** 3
+    mass_of = np.asarray(MASSES)[s["types"]]
+    mv = mass_of[None, :] * part["v"]
+    want = mv[:, s["types"] == 0].sum(axis=1) / V
+    other = mv[:, s["types"] == 1].sum(axis=1) / V
+    assert rel(o["j"], want) <= 1e-12
+    assert np.abs(want + other).max() <= 1e-10 * np.abs(want).max()
+    c = g.corr(pkg.MD_CORR_MASSFLUX)
+    oc = oracle_mod.Corr(4, 16, 2, 6, cross=True)
+    for q, j in zip(qs, js):
+        oc.push(np.concatenate([q, j]), np.concatenate([j, j]))
+    for k in range(6):
+        t, v = c.read(k)
+        to, vo = oc.read(k)
+        assert np.allclose(t / p.dt, to, rtol=1e-12)
+        assert np.abs(v - vo).max() <= 1e-12 * np.abs(vo).max(), k
+    g.close()
+
+
 def test_short_run_conserves_energy(pkg, system):
     """200 NVE steps of 1 fs in the mixed form: total energy drift below
     1e-4 of the kinetic energy per step, no state error."""
