@@ -83,27 +83,30 @@ __device__ __forceinline__ void load_input(const Tin *p, T *o) {
   for (int q = 0; q < V; ++q) o[q] = (T)a[q];
 }
 
-constexpr int kLagChunk = 8;  // ring loads issued together per thread
+constexpr int kLoadsInFlight = 8;  // ring vectors loaded together per thread
 
 // Grouped correlators (e.g. the per-atom velocity autocorrelation).  Thread
-// (cx, g, tid) owns the V consecutive series s = g gs + (cx blockDim + tid) V
-// for good (so the per-block partial sums are deterministic), and each push
-// is a pure stream: for every block the push reaches, the thread stores the
-// new sample and loads kLagChunk older ring vectors at a time (16-byte
-// loads, one plane per lag: coalesced across the warp), forms the lag
-// products in the ring type (FP32 in the mixed form), sums them over its V
-// series and the warp with shuffles, then the CTA adds the FP64 sum over its
-// warps into its own row of partial lag sums.  VIN: the input is 16-byte
-// aligned and can be read as vectors.
-template <typename T, typename Tin, int V, bool VIN>
+// (cx, g, tid) owns U vectors of V consecutive series, s = g gs +
+// (cx blockDim + tid) U V, for good (so the per-block partial sums are
+// deterministic), and each push is a pure stream: for every block the push
+// reaches, the thread stores the new sample and loads the older ring vectors
+// of kLoadsInFlight / U lags at a time (16-byte loads, one plane per lag:
+// coalesced across the warp), forms the lag products in the ring type (FP32
+// in the mixed form), sums them over its U V series and the warp with
+// shuffles, then the CTA adds the FP64 sum over its warps into its own row
+// of partial lag sums.  Two vectors per thread halve the shuffle reductions
+// per byte streamed.  VIN: the input is 16-byte aligned and can be read as
+// vectors.
+template <typename T, typename Tin, int V, bool VIN, int U>
 __global__ void __launch_bounds__(kPushThreads)
     k_push_grouped(CorrDev c, const Tin *__restrict__ x, const Tin *__restrict__ y, PushIdx pi) {
+  constexpr int kLC = kLoadsInFlight / U;  // lags per load batch
   int64_t t;
   if (!resolve_push(pi, &t)) return;
   __shared__ double red[kPushWarps][64];
   const int g = blockIdx.y, cx = blockIdx.x;
   const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x / kWarp;
-  const int64_t i0 = ((int64_t)cx * blockDim.x + threadIdx.x) * V;  // index within the group
+  const int64_t i0 = ((int64_t)cx * blockDim.x + threadIdx.x) * U * V;  // index within the group
   const bool act = i0 < c.gs;
   const int64_t s = (int64_t)g * c.gs + (act ? i0 : 0);
   const int64_t plane = c.ns;
@@ -120,70 +123,80 @@ __global__ void __launch_bounds__(kPushThreads)
     const int lo = (k == 0) ? 0 : c.p / c.m;
     const int nl = (int)min((int64_t)c.p - 1, nk - 1) - lo + 1;
     T *rxk = rx + (int64_t)k * c.p * plane;
-    T xk[V], yk[V];
+    T xk[U][V], yk[U][V];
 #pragma unroll
-    for (int q = 0; q < V; ++q) xk[q] = yk[q] = T(0);
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int q = 0; q < V; ++q) xk[u][q] = yk[u][q] = T(0);
     if (act) {
-      if (k == 0) {
-        load_input<T, Tin, V, VIN>(x + s, xk);
-        if (c.cross)
-          load_input<T, Tin, V, VIN>(y + s, yk);
-      } else {
-        // block k's sample: mean of block k-1's last m samples, oldest first
-        const int64_t nprev = nk * c.m;
-        const T *rp = rx + (int64_t)(k - 1) * c.p * plane;
-        const T *rq = ry + (int64_t)(k - 1) * c.p * plane;
-        T sx[V], sy[V], a[V];
 #pragma unroll
-        for (int q = 0; q < V; ++q) sx[q] = sy[q] = T(0);
-        for (int j = c.m - 1; j >= 0; --j) {
-          const int sl = (int)((nprev - 1 - j) % c.p);
-          VecIO<T, V>::load(rp + sl * plane + s, a);
-#pragma unroll
-          for (int q = 0; q < V; ++q) sx[q] += a[q];
-          if (c.cross) {
-            VecIO<T, V>::load(rq + sl * plane + s, a);
-#pragma unroll
-            for (int q = 0; q < V; ++q) sy[q] += a[q];
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < V; ++q) {
-          xk[q] = sx[q] / T(c.m);
-          yk[q] = sy[q] / T(c.m);
-        }
-      }
-      if (!c.cross)
-#pragma unroll
-        for (int q = 0; q < V; ++q) yk[q] = xk[q];
-      VecIO<T, V>::store(rxk + slot * plane + s, xk);
-      if (c.cross) VecIO<T, V>::store(ry + (int64_t)k * c.p * plane + slot * plane + s, yk);
-    }
-    for (int l0 = 0; l0 < nl; l0 += kLagChunk) {
-      T older[kLagChunk][V];
-#pragma unroll
-      for (int l = 0; l < kLagChunk; ++l) {
-        const int lag = lo + l0 + l;
-        if (act && l0 + l < nl) {
-          if (lag == 0) {
-#pragma unroll
-            for (int q = 0; q < V; ++q) older[l][q] = xk[q];
-          } else {
-            int j = slot - lag;
-            if (j < 0) j += c.p;
-            VecIO<T, V>::load(rxk + j * plane + s, older[l]);
-          }
+      for (int u = 0; u < U; ++u) {
+        const int64_t su = s + u * V;
+        if (k == 0) {
+          load_input<T, Tin, V, VIN>(x + su, xk[u]);
+          if (c.cross) load_input<T, Tin, V, VIN>(y + su, yk[u]);
         } else {
+          // block k's sample: mean of block k-1's last m samples, oldest first
+          const int64_t nprev = nk * c.m;
+          const T *rp = rx + (int64_t)(k - 1) * c.p * plane;
+          const T *rq = ry + (int64_t)(k - 1) * c.p * plane;
+          T sx[V], sy[V], av[V];
 #pragma unroll
-          for (int q = 0; q < V; ++q) older[l][q] = T(0);
+          for (int q = 0; q < V; ++q) sx[q] = sy[q] = T(0);
+          for (int j = c.m - 1; j >= 0; --j) {
+            const int sl = (int)((nprev - 1 - j) % c.p);
+            VecIO<T, V>::load(rp + sl * plane + su, av);
+#pragma unroll
+            for (int q = 0; q < V; ++q) sx[q] += av[q];
+            if (c.cross) {
+              VecIO<T, V>::load(rq + sl * plane + su, av);
+#pragma unroll
+              for (int q = 0; q < V; ++q) sy[q] += av[q];
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < V; ++q) {
+            xk[u][q] = sx[q] / T(c.m);
+            yk[u][q] = sy[q] / T(c.m);
+          }
+        }
+        if (!c.cross)
+#pragma unroll
+          for (int q = 0; q < V; ++q) yk[u][q] = xk[u][q];
+        VecIO<T, V>::store(rxk + slot * plane + su, xk[u]);
+        if (c.cross) VecIO<T, V>::store(ry + (int64_t)k * c.p * plane + slot * plane + su, yk[u]);
+      }
+    }
+    for (int l0 = 0; l0 < nl; l0 += kLC) {
+      T older[kLC][U][V];
+#pragma unroll
+      for (int l = 0; l < kLC; ++l) {
+        const int lag = lo + l0 + l;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (act && l0 + l < nl) {
+            if (lag == 0) {
+#pragma unroll
+              for (int q = 0; q < V; ++q) older[l][u][q] = xk[u][q];
+            } else {
+              int j = slot - lag;
+              if (j < 0) j += c.p;
+              VecIO<T, V>::load(rxk + j * plane + s + u * V, older[l][u]);
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < V; ++q) older[l][u][q] = T(0);
+          }
         }
       }
 #pragma unroll
-      for (int l = 0; l < kLagChunk; ++l) {
+      for (int l = 0; l < kLC; ++l) {
         if (l0 + l < nl) {
           T a = T(0);
 #pragma unroll
-          for (int q = 0; q < V; ++q) a += older[l][q] * yk[q];
+          for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int q = 0; q < V; ++q) a += older[l][u][q] * yk[u][q];
           a = warp_sum(a);
           if (lane == 0) red[warp][l0 + l] = (double)a;
         }
@@ -218,12 +231,18 @@ int launch_grouped(const CorrDev &c, const Tin *x, const Tin *y, PushIdx pi, cud
   if (c.vec == V) {
     const bool vin = (reinterpret_cast<uintptr_t>(x) % (V * sizeof(Tin)) == 0) &&
                      (!c.cross || reinterpret_cast<uintptr_t>(y) % (V * sizeof(Tin)) == 0);
-    if (vin)
-      k_push_grouped<T, Tin, V, true><<<grid, kPushThreads, 0, s>>>(c, x, y, pi);
-    else
-      k_push_grouped<T, Tin, V, false><<<grid, kPushThreads, 0, s>>>(c, x, y, pi);
+    if (c.vu == 2) {
+      if (vin)
+        k_push_grouped<T, Tin, V, true, 2><<<grid, kPushThreads, 0, s>>>(c, x, y, pi);
+      else
+        k_push_grouped<T, Tin, V, false, 2><<<grid, kPushThreads, 0, s>>>(c, x, y, pi);
+    } else if (vin) {
+      k_push_grouped<T, Tin, V, true, 1><<<grid, kPushThreads, 0, s>>>(c, x, y, pi);
+    } else {
+      k_push_grouped<T, Tin, V, false, 1><<<grid, kPushThreads, 0, s>>>(c, x, y, pi);
+    }
   } else {
-    k_push_grouped<T, Tin, 1, false><<<grid, kPushThreads, 0, s>>>(c, x, y, pi);
+    k_push_grouped<T, Tin, 1, false, 1><<<grid, kPushThreads, 0, s>>>(c, x, y, pi);
   }
   OTF_LAUNCH_CHECK();
   return MD_OK;
@@ -278,10 +297,13 @@ int Correlator::create(const corr_params &p, cudaStream_t s) {
     // one 16-byte vector of series per thread when the group size allows it
     const int vw = (int)(16 / (p.precision == MD_PREC_FP64 ? sizeof(double) : sizeof(float)));
     dev.vec = (dev.gs % vw == 0) ? vw : 1;
-    const int64_t per_block = (int64_t)kPushThreads * dev.vec;
+    // two vectors per thread when the group splits evenly into them
+    dev.vu = (dev.vec == vw && dev.gs % (2 * vw) == 0) ? 2 : 1;
+    const int64_t per_block = (int64_t)kPushThreads * dev.vec * dev.vu;
     dev.nchunk = (int)((dev.gs + per_block - 1) / per_block);
   } else {
     dev.vec = 1;
+    dev.vu = 1;
     dev.nchunk = 1;
   }
   const size_t esz = prec == MD_PREC_FP64 ? sizeof(double) : sizeof(float);

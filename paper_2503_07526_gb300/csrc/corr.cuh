@@ -25,7 +25,8 @@ struct CorrDev {
   int b, p, m, cross;
   int64_t ns, gs, ng;  // series, series per group, groups
   int nchunk;          // blocks per group (grouped kernel)
-  int vec;             // series per thread in the grouped kernel (1, 2 or 4)
+  int vec;             // series per vector in the grouped kernel (1, 2 or 4)
+  int vu;              // vectors per thread in the grouped kernel (1 or 2)
   void *ringx, *ringy; // [b][p][ns] of the ring type
   double *vals;        // per-series: [ns][b][p]; grouped: [ng][nchunk][b][p]
 };
