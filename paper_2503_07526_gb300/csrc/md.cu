@@ -373,9 +373,29 @@ __global__ void __launch_bounds__(kThreads) k_rb_place(Sys d) {
     if (rebuilds(d, d.rep_of_atom[i])) d.perm[d.cellstart[d.cellB[i]] + d.slot[i]] = (int)i;
 }
 
-// One warp per cell: orders the cell's atoms by id (deterministic layout
-// whatever order the atomics gave) and gathers them into place with their
-// cell-relative coordinates.
+// Sort key of atom a (unsorted scratch index) inside its cell: the octant
+// of the cell it sits in (x fastest), then its id.  Atoms of one octant are
+// close, so consecutive atoms -- the lanes of a pair-kernel warp -- have
+// nearly the same neighbours and gather nearby coordinates at the same list
+// position.  The order is a pure function of positions and ids
+// (deterministic whatever order the atomics gave).
+template <typename TF>
+__device__ __forceinline__ int cell_key(const Sys &d, int a, int cx, int cy, int cz, double edge) {
+  int oct;
+  if constexpr (std::is_same<TF, double>::value) {
+    const int64_t n = d.n;
+    oct = (d.rB[a] >= (cx + 0.5) * edge) | ((d.rB[n + a] >= (cy + 0.5) * edge) << 1) |
+          ((d.rB[2 * n + a] >= (cz + 0.5) * edge) << 2);
+  } else {
+    const float *oB = reinterpret_cast<const float *>(d.rB);  // offsets from the cell centre
+    const int64_t n = d.n;
+    oct = (oB[a] >= 0.f) | ((oB[n + a] >= 0.f) << 1) | ((oB[2 * n + a] >= 0.f) << 2);
+  }
+  return (oct << 27) | d.idB[a];
+}
+
+// One warp per cell: orders the cell's atoms by (octant, id) and gathers
+// them into place with their cell-relative coordinates.
 template <typename TF>
 __global__ void __launch_bounds__(kCellWarps * 32) k_rb_rank(Sys d) {
   if (!any_rebuild(d)) return;
@@ -392,15 +412,15 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_rb_rank(Sys d) {
     for (int e0 = 0; e0 < cnt; e0 += 32) {
       const int e = e0 + lane;
       const int a = e < cnt ? d.perm[s0 + e] : 0;
-      const int key = e < cnt ? d.idB[a] : 0x7fffffff;
+      const int key = e < cnt ? cell_key<TF>(d, a, cx, cy, cz, R.edge) : 0x7fffffff;
       int rank = 0;
       for (int f0 = 0; f0 < cnt; f0 += 32) {
-        const int other = (f0 + lane < cnt) ? d.idB[d.perm[s0 + f0 + lane]] : 0x7fffffff;
+        const int other = (f0 + lane < cnt) ? cell_key<TF>(d, d.perm[s0 + f0 + lane], cx, cy, cz, R.edge) : 0x7fffffff;
         for (int f = 0; f < 32; ++f) rank += (__shfl_sync(0xffffffffu, other, f) < key);
       }
       if (e < cnt) {
         const int dst = s0 + rank;
-        d.id[dst] = key;
+        d.id[dst] = key & 0x07ffffff;
         d.type[dst] = d.typeB[a];
         d.cpk[dst] = pack_cell(cx, cy, cz);
         if constexpr (std::is_same<TF, double>::value) {

@@ -116,8 +116,8 @@ def test_mass_flux_correlations(pkg, system, oracle_mod):
     """The partial momentum density of the cations, j = sum m v / V over
     them, and its correlations with the heat flux (Sec. 2.3, the mass-flux
     correction of kappa for multi-component systems): j against its
-    definition from the velocities (and against minus the anions' share:
-    total momentum is zero), and the device's cross correlator against the
+    definition from the velocities (and against minus the anions' share, up
+    to SPME's small net force), and the device's cross correlator against the
     oracle's correlator fed the same per-step (q, j) samples."""
     s = system
     p = params(pkg, s, 0, mesh=16)
@@ -136,7 +136,10 @@ def test_mass_flux_correlations(pkg, system, oracle_mod):
     want = mv[:, s["types"] == 0].sum(axis=1) / V
     other = mv[:, s["types"] == 1].sum(axis=1) / V
     assert rel(o["j"], want) <= 1e-12
-    assert np.abs(want + other).max() <= 1e-10 * np.abs(want).max()
+    # the two species' shares cancel up to the momentum SPME's small net force
+    # has added since the start (the interpolated energy is not translation
+    # invariant)
+    assert np.abs(want + other).max() <= 1e-2 * np.abs(want).max()
     c = g.corr(pkg.MD_CORR_MASSFLUX)
     oc = oracle_mod.Corr(4, 16, 2, 6, cross=True)
     for q, j in zip(qs, js):
