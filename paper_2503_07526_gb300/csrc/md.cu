@@ -50,7 +50,7 @@ constexpr int kMaxPairThreads = 256;
 constexpr int kCellWarps = 4;  // warps (cells) per CTA in the link-cell kernels
 constexpr int kNRed = 14;      // K, U, V*sigma[6], V*q[3], V*j[3]
 constexpr int kNBanks = 4;     // stress, heat flux, velocity, mass flux
-constexpr int kMaxRedBlocks = 152 * 4;
+constexpr int kMaxRedBlocks = 152 * 8;
 
 // Step counters shared by all replicas.
 struct StepDev {
@@ -1584,7 +1584,7 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
     R.atom1 = n + reps[k].n;
     R.cell0 = ncell;
     R.block0 = blocks;
-    R.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxRedBlocks, (reps[k].n + 4095) / 4096));
+    R.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxRedBlocks, (reps[k].n + 2047) / 2048));
     n += reps[k].n;
     ncell += (int64_t)R.nc * R.nc * R.nc;
     blocks += R.nblk;
