@@ -50,7 +50,7 @@ constexpr int kMaxPairThreads = 256;
 constexpr int kCellWarps = 4;  // warps (cells) per CTA in the link-cell kernels
 constexpr int kNRed = 14;      // K, U, V*sigma[6], V*q[3], V*j[3]
 constexpr int kNBanks = 4;     // stress, heat flux, velocity, mass flux
-constexpr int kMaxRedBlocks = 152 * 8;
+constexpr int kMaxRedBlocks = 152 * 4;
 
 // Step counters shared by all replicas.
 struct StepDev {
@@ -163,12 +163,22 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift64(Sys d, double hdt) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double h = hdt * d.invm[type_of(d, i)];
+    // every load first (the stores below could alias them for the compiler)
+    double fa[3], va0[3], ra[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      fa[a] = F[a * n + i];
+      va0[a] = d.v[a * n + i];
+      ra[a] = d.r[a * n + i];
+    }
+    const double qw = rel[i].w;
+    const dvec4 b = Vec4<double>::load(relb + i);
     double x[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double va = fma(h, F[a * n + i], d.v[a * n + i]);
+      const double va = fma(h, fa[a], va0[a]);
       d.v[a * n + i] = va;
-      x[a] = fma(d.dt, va, d.r[a * n + i]);
+      x[a] = fma(d.dt, va, ra[a]);
       d.r[a * n + i] = x[a];
     }
     int cx, cy, cz;
@@ -177,8 +187,7 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift64(Sys d, double hdt) {
     const double px = fma(-(cx + 0.5), edge, x[0]);
     const double py = fma(-(cy + 0.5), edge, x[1]);
     const double pz = fma(-(cz + 0.5), edge, x[2]);
-    Vec4<double>::store(rel + i, px, py, pz, rel[i].w);
-    const dvec4 b = Vec4<double>::load(relb + i);
+    Vec4<double>::store(rel + i, px, py, pz, qw);
     const double dx = px - b.x, dy = py - b.y, dz = pz - b.z;
     if ((dx * dx + dy * dy + dz * dz) > d.lim2) request_rebuild(d, d.rep_of_atom[i]);
     bad |= !(isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]));
@@ -202,22 +211,31 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift_df(Sys d) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int t = type_of(d, i);
-    const dfloat h{d.hdtm_h[t], d.hdtm_l[t]};
+    // every load first (the stores below could alias them for the compiler)
     const float4 o = rel[i];
+    const float4 b = relb[i];
+    float fa[3], vh[3], vl[3], ol[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      fa[a] = F[a * n + i];
+      vh[a] = d.vh[a * n + i];
+      vl[a] = d.vl[a * n + i];
+      ol[a] = d.offl[a * n + i];
+    }
+    const dfloat h{d.hdtm_h[t], d.hdtm_l[t]};
     float oh[3] = {o.x, o.y, o.z};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      dfloat v{d.vh[a * n + i], d.vl[a * n + i]};
-      v = df_add(v, df_mul_f(h, F[a * n + i]));
+      dfloat v{vh[a], vl[a]};
+      v = df_add(v, df_mul_f(h, fa[a]));
       d.vh[a * n + i] = v.h;
       d.vl[a * n + i] = v.l;
-      dfloat x{oh[a], d.offl[a * n + i]};
+      dfloat x{oh[a], ol[a]};
       x = df_add(x, df_mul(dt, v));
       oh[a] = x.h;
       d.offl[a * n + i] = x.l;
     }
     rel[i] = make_float4(oh[0], oh[1], oh[2], o.w);
-    const float4 b = relb[i];
     const float dx = oh[0] - b.x, dy = oh[1] - b.y, dz = oh[2] - b.z;
     if ((dx * dx + dy * dy + dz * dz) > lim2) request_rebuild(d, d.rep_of_atom[i]);
     bad |= !(isfinite(oh[0]) && isfinite(oh[1]) && isfinite(oh[2]));
@@ -796,25 +814,44 @@ __global__ void __launch_bounds__(kThreads)
   for (int q = 0; q < kNRed; ++q) acc[q] = A(0);
   for (int64_t i = R.atom0 + (int64_t)lb * blockDim.x + threadIdx.x; i < R.atom1;
        i += (int64_t)R.nblk * blockDim.x) {
+    // every load of the atom first (the stores below could alias them for
+    // the compiler), so they are all in flight together
     const int t = type_of(d, i);
+    const A ep = (A)Ep[i];
+    A w[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) w[q] = (A)Wp[q * n + i];
+    TF f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) f[a] = KICK ? F[a * n + i] : TF(0);
+    const int id = vacf_due ? d.id[i] : 0;
     A v[3];
     if constexpr (std::is_same<TF, double>::value) {
+      double vv[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) vv[a] = d.v[a * n + i];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        double va = d.v[a * n + i];
+        double va = vv[a];
         if (KICK) {
-          va = fma(hdt * d.invm[t], F[a * n + i], va);
+          va = fma(hdt * d.invm[t], f[a], va);
           d.v[a * n + i] = va;
         }
         v[a] = (A)va;
       }
     } else {
+      float vh[3], vl[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        vh[a] = d.vh[a * n + i];
+        vl[a] = d.vl[a * n + i];
+      }
       const dfloat h{d.hdtm_h[t], d.hdtm_l[t]};
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        dfloat va{d.vh[a * n + i], d.vl[a * n + i]};
+        dfloat va{vh[a], vl[a]};
         if (KICK) {
-          va = df_add(va, df_mul_f(h, (float)F[a * n + i]));
+          va = df_add(va, df_mul_f(h, (float)f[a]));
           d.vh[a * n + i] = va.h;
           d.vl[a * n + i] = va.l;
         }
@@ -822,16 +859,11 @@ __global__ void __launch_bounds__(kThreads)
       }
     }
     if (vacf_due) {
-      const int id = d.id[i];
 #pragma unroll
       for (int a = 0; a < 3; ++a) vb[a * n + id] = (TF)v[a];
     }
     const A m = (A)d.mass[t];
     const A vx = v[0], vy = v[1], vz = v[2];
-    const A ep = (A)Ep[i];
-    A w[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) w[q] = (A)Wp[q * n + i];
     const A ke = A(0.5) * m * (vx * vx + vy * vy + vz * vz);
     const A E = ke + ep;
     acc[0] += ke;
@@ -868,11 +900,28 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int q = warp; q < kNRed; q += kThreads / 32) {
-    double sm = 0.0;
-    for (int b = lane; b < R.nblk; b += 32) sm += __ldcg(d.partials + (R.block0 + b) * kNRed + q);
-    sm = warp_sum(sm);
-    if (lane == 0) tot[q] = sm;
+  // the replica's partials: thread t sums CTAs t, t + 256, ... (all kNRed
+  // values at once, independent loads), then a fixed tree over the threads
+  {
+    double ps[kNRed];
+#pragma unroll
+    for (int q = 0; q < kNRed; ++q) ps[q] = 0.0;
+    for (int b = threadIdx.x; b < R.nblk; b += kThreads) {
+      const double *pp = d.partials + (R.block0 + b) * kNRed;
+#pragma unroll
+      for (int q = 0; q < kNRed; ++q) ps[q] += __ldcg(pp + q);
+    }
+#pragma unroll
+    for (int q = 0; q < kNRed; ++q) {
+      const double sm = warp_sum(ps[q]);
+      if (lane == 0) red[warp][q] = sm;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNRed) {
+      double sm = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) sm += red[w][threadIdx.x];
+      tot[threadIdx.x] = sm;
+    }
   }
   __syncthreads();
   const int64_t nr = R.atom1 - R.atom0;
@@ -1584,7 +1633,7 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
     R.atom1 = n + reps[k].n;
     R.cell0 = ncell;
     R.block0 = blocks;
-    R.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxRedBlocks, (reps[k].n + 2047) / 2048));
+    R.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxRedBlocks, (reps[k].n + 4095) / 4096));
     n += reps[k].n;
     ncell += (int64_t)R.nc * R.nc * R.nc;
     blocks += R.nblk;
