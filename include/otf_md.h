@@ -112,12 +112,14 @@ typedef struct {
   int32_t use_graph;  /* 1: md_step replays a captured CUDA graph of a step */
   int32_t autotune;   /* 1: md_init times the pair kernel (64/128/256 threads
                          per CTA) and the list build (j-parallel at 2/4/8,
-                         i-parallel at 4/8 warps per CTA) on the system and
+                         i-parallel and staged at 4/8 warps per CTA) on the
+                         system and
                          keeps the fastest (md_get_config) */
   corr_spec stress, heatflux, vacf; /* the three correlators of Sec. 2.3/2.7 */
   int32_t list_build; /* neighbour-list build when not autotuned: 0 = the
-                         library's default, 1 = j-parallel, 2 = i-parallel
-                         (both give the same lists in the same order) */
+                         library's default, 1 = j-parallel, 2 = i-parallel,
+                         3 = staged (all give the same lists in the same
+                         order) */
   int32_t potential;  /* MD_POT_LJ or MD_POT_BUCK_EWALD */
   double charge[8];   /* MD_POT_BUCK_EWALD: charge of each type */
   double buck_A, buck_rho, buck_C; /* MD_POT_BUCK_EWALD: Buckingham parameters
@@ -157,7 +159,7 @@ typedef struct {
   int32_t build_warps;    /* warps per CTA of the neighbour-list build */
   int32_t max_neighbors;  /* neighbour-list capacity per atom */
   int64_t atoms, cells;   /* totals over all replicas */
-  int32_t build_kind;     /* 0: j-parallel list build, 1: i-parallel */
+  int32_t build_kind;     /* 0: j-parallel list build, 1: i-parallel, 2: staged */
 } md_config;
 
 /* Observables of the last completed step (Sec. 2.3). */

@@ -44,7 +44,7 @@ namespace otf {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kDefaultBuildKind = 0;  // list build without autotuning: 0 j-parallel, 1 i-parallel
+constexpr int kDefaultBuildKind = 0;  // list build without autotuning: 0 j-parallel, 1 i-parallel, 2 staged
 constexpr int kPairThreads = 128;     // default CTA of the pair kernel (the autotuner may pick 64 or 256)
 constexpr int kMaxPairThreads = 256;
 constexpr int kCellWarps = 4;  // warps (cells) per CTA in the link-cell kernels
@@ -1069,6 +1069,129 @@ __global__ void k_unsort(Sys d, double *r, double *v, double *F, double *epot, d
   }
 }
 
+// Verlet-list build, staged: one warp per chunk of 32 consecutive atoms
+// (the list layout of k_build).  For each segment (the chunk's atoms of one
+// cell) the warp copies the candidates -- the atoms of the 27 neighbour
+// cells, row by row, already moved into the segment cell's frame and tagged
+// with their list entry -- into shared memory in batches of kStageBatch,
+// densely packed (k_build leaves lanes idle at the end of every 3-cell
+// row).  Each atom of the segment then tests a batch 32 candidates at a
+// time; the running list length is warp-uniform inside a batch, so an
+// append is one ballot and one population count.  Same candidates in the
+// same order as k_build, so the same lists.
+template <typename TF, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_build_staged(Sys d, LJ<TF> lj) {
+  using V4 = typename Vec4<TF>::type;
+  constexpr int kStageBatch = sizeof(TF) == 4 ? 256 : 128;  // staged candidates per warp
+  if (!any_rebuild(d)) return;
+  __shared__ V4 sxyz[WARPS][kStageBatch];
+  __shared__ uint32_t stag[WARPS][kStageBatch];
+  __shared__ V4 spi[WARPS][32];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int64_t n = d.n;
+  const V4 *rel = static_cast<const V4 *>(d.rel);
+  const unsigned below = (1u << lane) - 1u;
+  const int64_t nchunks = (n + 31) / 32;
+  for (int64_t q = blockIdx.x * (int64_t)WARPS + wl; q < nchunks; q += (int64_t)gridDim.x * WARPS) {
+    const int a0 = (int)(q * 32), a1 = (int)min((int64_t)a0 + 32, n);
+    __syncwarp();
+    if (a0 + lane < a1) spi[wl][lane] = Vec4<TF>::load(rel + a0 + lane);
+    __syncwarp();
+    uint32_t *blk = d.nbr + q * d.maxnb * 32;
+    int cnt = 0;  // lane l: list length of atom a0 + l
+    int s = a0;
+    while (s < a1) {
+      const Rep &R = rep_of(d, s);
+      const int nc = R.nc;
+      const TF edge = (TF)R.edge;
+      int cx, cy, cz;
+      unpack_cell(d.cpk[s], cx, cy, cz);
+      const int e = min(d.cellstart[R.cell0 + (cz * nc + cy) * nc + cx + 1], a1);
+      if (!rebuilds(d, d.rep_of_atom[s])) {
+        s = e;
+        continue;
+      }
+      int fill = 0;  // candidates in the batch
+      // tests the staged batch against every atom of the segment
+      auto flush = [&]() {
+        __syncwarp();
+        for (int ii = s; ii < e; ++ii) {
+          const int li = ii - a0;
+          const V4 pi = spi[wl][li];
+          int c0 = __shfl_sync(0xffffffffu, cnt, li);
+          for (int b0 = 0; b0 < fill; b0 += 32) {
+            const int k = b0 + lane;
+            bool acc = false;
+            uint32_t tag = 0;
+            if (k < fill) {
+              const V4 t = sxyz[wl][k];
+              tag = stag[wl][k];
+              const TF dx = pi.x - t.x, dy = pi.y - t.y, dz = pi.z - t.z;
+              const TF r2 = dx * dx + dy * dy + dz * dz;
+              acc = r2 < lj.rlist2 && (int)(tag & 0x07ffffffu) != ii;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, acc);
+            const int pos = c0 + __popc(m & below);
+            if (acc && pos < d.maxnb) blk[pos * 32 + li] = tag;
+            c0 += __popc(m);
+          }
+          if (lane == li) cnt = c0;
+        }
+        __syncwarp();
+        fill = 0;
+      };
+      for (int row = 0; row < 9; ++row) {
+        const int oy = row % 3 - 1, oz = row / 3 - 1;
+        const int jy = (cy + oy + nc) % nc, jz = (cz + oz + nc) % nc;
+        const int64_t rb = R.cell0 + ((int64_t)jz * nc + jy) * nc;
+        const bool contig = cx >= 1 && cx <= nc - 2;
+        for (int piece = 0; piece < (contig ? 1 : 3); ++piece) {
+          int ra, rbnd, b1, b2;
+          if (contig) {  // cells cx-1, cx, cx+1 of the row are contiguous
+            ra = d.cellstart[rb + cx - 1];
+            rbnd = d.cellstart[rb + cx + 2];
+            b1 = d.cellstart[rb + cx];
+            b2 = d.cellstart[rb + cx + 1];
+          } else {
+            const int ox = piece - 1;
+            const int jx = (cx + ox + nc) % nc;
+            ra = d.cellstart[rb + jx];
+            rbnd = d.cellstart[rb + jx + 1];
+            b1 = ox == -1 ? rbnd : ra;  // every j of this cell gets offset ox
+            b2 = ox == 1 ? ra : rbnd;
+          }
+          for (int jb = ra; jb < rbnd;) {
+            const int take = min(rbnd - jb, kStageBatch - fill);
+            if (lane < 32) {
+              for (int u = lane; u < take; u += 32) {
+                const int j = jb + u;
+                const int ox = j < b1 ? -1 : (j < b2 ? 0 : 1);
+                const V4 pj = Vec4<TF>::load(rel + j);
+                V4 t;
+                t.x = pj.x + ox * edge;
+                t.y = pj.y + oy * edge;
+                t.z = pj.z + oz * edge;
+                t.w = TF(0);
+                sxyz[wl][fill + u] = t;
+                stag[wl][fill + u] = (uint32_t)j | ((uint32_t)((ox + 1) + 3 * row) << 27);
+              }
+            }
+            fill += take;
+            jb += take;
+            if (fill == kStageBatch) flush();
+          }
+        }
+      }
+      if (fill > 0) flush();
+      s = e;
+    }
+    if (a0 + lane < a1 && rebuilds(d, d.rep_of_atom[a0 + lane])) {
+      d.nnb[a0 + lane] = min(cnt, d.maxnb);
+      if (cnt > d.maxnb) atomicOr(d.err, ERR_NBR_OVERFLOW);
+    }
+  }
+}
+
 // Verlet-list build, i-parallel: one warp per chunk of 32 consecutive atoms
 // of the cell-sorted order, lane l owning atom a0 + l (the same list layout
 // as k_build).  The chunk's lanes are taken in groups that share a replica
@@ -1165,7 +1288,7 @@ struct md_handle_s {
   int red_blocks = 1;                // reduction CTAs over all replicas
   int pair_threads = kPairThreads;   // launch shapes (autotuned when asked)
   int build_warps = kCellWarps;
-  int build_kind = 0;                // 0: j-parallel k_build, 1: i-parallel k_build_ip
+  int build_kind = 0;                // 0: j-parallel k_build, 1: i-parallel k_build_ip, 2: k_build_staged
   std::vector<Rep> reps;             // host copy of the descriptor table
   Rep *d_rep = nullptr;
   int *d_rep_of_atom = nullptr, *d_rep_of_cell = nullptr, *d_rep_of_block = nullptr;
@@ -1241,6 +1364,13 @@ void launch_build(const md_handle *h, cudaStream_t s) {
   const Sys &d = h->d;
   const int64_t chunks = (d.n + 31) / 32;
   const LJ<TF> lj = lj_of<TF>(h->prm);
+  if (h->build_kind == 2) {
+    if (h->build_warps == 8)
+      k_build_staged<TF, 8><<<std::min(ceil_div(chunks, 8), 152 * 4), 256, 0, s>>>(d, lj);
+    else
+      k_build_staged<TF, 4><<<std::min(ceil_div(chunks, 4), 152 * 8), 128, 0, s>>>(d, lj);
+    return;
+  }
   if (h->build_kind == 1) {
     if (h->build_warps == 8)
       k_build_ip<TF, 8><<<std::min(ceil_div(chunks, 8), 152 * 8), 256, 0, s>>>(d, lj);
@@ -1419,8 +1549,8 @@ int validate_params(const md_params *p) {
     set_error("md_init: unknown precision");
     return MD_EINVAL;
   }
-  if (p->list_build < 0 || p->list_build > 2) {
-    set_error("md_init: list_build must be 0, 1 or 2");
+  if (p->list_build < 0 || p->list_build > 3) {
+    set_error("md_init: list_build must be 0, 1, 2 or 3");
     return MD_EINVAL;
   }
   if (p->pair_mode != MD_PAIR_VERLET && p->pair_mode != MD_PAIR_CELLS) {
@@ -1571,7 +1701,7 @@ float time_runs(md_handle *h, int reps, Fn fn) {
 }
 
 // Autotuner: times the pair kernel at 64 / 128 / 256 threads per CTA and
-// the list build (j-parallel at 2 / 4 / 8 warps per CTA, i-parallel at 4 / 8)
+// the list build (j-parallel at 2 / 4 / 8 warps per CTA, i-parallel and staged at 4 / 8)
 // on the system itself (forces
 // and lists are recomputed from the unchanged state, so the trajectory is
 // not touched) and keeps the fastest of each.
@@ -1588,7 +1718,7 @@ int autotune(md_handle *h) {
   h->pair_threads = best_t;
   best = 1e30f;
   int best_w = h->build_warps, best_k = h->build_kind;
-  const int shapes[5][2] = {{0, 2}, {0, 4}, {0, 8}, {1, 4}, {1, 8}};
+  const int shapes[7][2] = {{0, 2}, {0, 4}, {0, 8}, {1, 4}, {1, 8}, {2, 4}, {2, 8}};
   for (const auto &kw : shapes) {
     h->build_kind = kw[0];
     h->build_warps = kw[1];

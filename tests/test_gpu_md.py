@@ -293,13 +293,13 @@ def test_lattice_start_mixed_forces(pkg, oracle_mod):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_list_builds_agree(pkg, precision):
-    """The j-parallel and i-parallel list builds produce the same lists in
-    the same order, so the forces agree bit for bit, over rebuilds, for a
-    single system and a batch with short (3-cell) rows."""
+    """The j-parallel, i-parallel and staged list builds produce the same
+    lists in the same order, so the forces agree bit for bit, over rebuilds,
+    for a single system and a batch with short (3-cell) rows."""
     s = synth.lj_system(12, rho=0.8442, T=2.5, seed=8)
     r = s["r"] + 0.15 * (synth.uniform01(9, s["r"].size).reshape(s["r"].shape) - 0.5)
     out = []
-    for lb in (1, 2):
+    for lb in (1, 2, 3):
         p = pkg.make_params(s["n"], s["L"], precision=precision, list_build=lb)
         g = pkg.System(p, r, s["v"])
         g.step(40)
@@ -307,17 +307,19 @@ def test_list_builds_agree(pkg, precision):
         assert g.observables()["rebuilds"] >= 2
         g.close()
     for key in ("r", "v", "F", "W", "epot"):
-        assert np.array_equal(out[0][key], out[1][key]), key
+        for o in out[1:]:
+            assert np.array_equal(out[0][key], o[key]), key
     reps = []
     for k, (cells, rho) in enumerate(((5, 0.7), (5, 0.9), (7, 0.8))):
         t = synth.lj_system(cells, rho=rho, T=1.5, seed=20 + k)
         reps.append(dict(r=t["r"], v=t["v"], box=t["L"]))
     outb = []
-    for lb in (1, 2):
+    for lb in (1, 2, 3):
         p = pkg.make_params(1, 1.0, precision=precision, skin=0.2, list_build=lb, vacf=None)
         g = pkg.System(p, replicas=reps)
         g.step(30)
         outb.append(g.particles())
         g.close()
     for key in ("r", "v", "F", "W"):
-        assert np.array_equal(outb[0][key], outb[1][key]), key
+        for o in outb[1:]:
+            assert np.array_equal(outb[0][key], o[key]), key
