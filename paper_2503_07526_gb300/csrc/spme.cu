@@ -387,7 +387,7 @@ __device__ __forceinline__ void gather_atom(const int (&base)[3], const T (&frac
 // staged in shared memory (one coalesced read per mesh point instead of one
 // per atom touching it), then every atom sums over its points.
 template <typename T, int N>
-__global__ void __launch_bounds__(kRowThreads) k_spme_gather(SpmeAtoms a, int K, double kl, const T *phi,
+__global__ void __launch_bounds__(kRowThreads, 4) k_spme_gather(SpmeAtoms a, int K, double kl, const T *phi,
                                                              const T *psi, T ke, T kL, T cw, T self, T *F, T *epot,
                                                              T *W) {
   using R = typename Rec<T>::type;
