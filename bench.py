@@ -451,6 +451,24 @@ def run_learned_tail(pkg, torch):
     t0 = time.perf_counter()
     eta, kappa, ue, uk = tail.predict(te["X"], te["eta_short"], te["kappa_short"], te["steps_short"])
     infer_s = time.perf_counter() - t0
+    # the network's tensor-core forward pass on a large device batch
+    rows = 1 << 20
+    Xd = torch.randn(rows, lt.N_FEATURES, device="cuda", dtype=torch.float32)
+    tail.net.forward(Xd)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sync()
+    ev0.record(stream)
+    reps = 5
+    for _ in range(reps):
+        tail.net.forward(Xd)
+    ev1.record(stream)
+    sync()
+    fwd_ms = ev0.elapsed_time(ev1) / reps
+    dims = (lt.N_FEATURES, 128, 128, 128, 2)
+    flop = 2.0 * rows * sum(a * b for a, b in zip(dims[:-1], dims[1:]))
+    peaks, peak_kind = measured_peaks()
+    fwd_tf = flop / (fwd_ms / 1e3) / 1e12
 
     def rms_rel(a, b):
         return float(np.sqrt(np.mean(((a - b) / b) ** 2)))
@@ -468,6 +486,11 @@ def run_learned_tail(pkg, torch):
         "validation_error": list(tail.val_error), "short_run_error_coefficients": list(tail.short_coeff),
         "loss_first_last": [float(hist[0]), float(hist[-1])],
         "seconds": {"generate": gen_s, "train": train_s, "inference_128": infer_s},
+        "forward_1m_rows": {"ms": fwd_ms, "tflops_algorithmic": fwd_tf, "bound": "tensor",
+                            "frac_of_bf16_peak": fwd_tf / peaks["bf16_tflops"],
+                            "peak_source": f"{peak_kind} bf16_tflops (burst)",
+                            "note": "K of every product is 128 to 144: each 128-row tile is a few MMAs between a "
+                                    "TMA load and an epilogue, so the pass is latency-bound, not tensor-bound"},
         "ensemble_atom_steps_per_s": float(d["atoms"].sum() * 20000 / (d["seconds_short"] + d["seconds_long"])),
     }
 

@@ -1028,7 +1028,7 @@ int mlp_forward(mlp_handle *h, const float *X, int64_t rows, float *Y, int32_t m
     set_error("mlp_forward: null argument or rows < 1");
     return MD_EINVAL;
   }
-  const int64_t chunk = 4096;
+  const int64_t chunk = 65536;  // rows per pass (about 60 MB of bfloat16 activations)
   int rc = grow_inference(h, std::min(rows, chunk));
   if (rc) return rc;
   float *own = nullptr;
