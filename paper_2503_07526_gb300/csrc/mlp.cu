@@ -241,6 +241,14 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc(const __grid_constant__ CU
   const bool run = done_ok && *flag == 0;
   if (!run && tid == 0) atomicOr(err, 1u);
 
+  // bfloat16 row-major output: staged through the (now idle) operand
+  // buffers and written row by row with 16-byte stores, so a warp writes
+  // whole lines (a thread owns a row of the accumulator, so direct stores
+  // would touch 32 rows per instruction)
+  const bool stage_b = e.out_b && e.n_store == N && N % 8 == 0 && e.ld_b % 8 == 0 &&
+                       (reinterpret_cast<uintptr_t>(e.out_b) & 15) == 0;
+  const int pitch = N + 8;  // staged row, in bfloat16
+  bf16 *stile = reinterpret_cast<bf16 *>(smem);
   if (run) {
     const int row = warp * 32 + lane;
     const int64_t m = (int64_t)m0 + row;
@@ -250,23 +258,52 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc(const __grid_constant__ CU
       float v[16];
       tmem_ld16(trow + (uint32_t)c0, v);  // warp-collective: every lane loads
       if (!live) continue;
+      float hd[16];
+      if (e.dact) {  // the 16 stored activations of this row and column group
+        const bf16 *hp = e.dact + m * e.ld_dact + c0;
+        if ((e.ld_dact % 8) == 0 && (reinterpret_cast<uintptr_t>(e.dact) & 15) == 0 && c0 + 16 <= e.n_store) {
+          const uint4 q0 = *reinterpret_cast<const uint4 *>(hp), q1 = *reinterpret_cast<const uint4 *>(hp + 8);
+          const bf16 *b0 = reinterpret_cast<const bf16 *>(&q0), *b1 = reinterpret_cast<const bf16 *>(&q1);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            hd[i] = __bfloat162float(b0[i]);
+            hd[8 + i] = __bfloat162float(b1[i]);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) hd[i] = c0 + i < e.n_store ? __bfloat162float(hp[i]) : 0.f;
+        }
+      }
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int n = c0 + i;
         if (n >= e.n_store) break;
         float x = v[i];
         if (e.bias) x += e.bias[n];
-        if (e.dact) {
-          const float h = __bfloat162float(e.dact[m * e.ld_dact + n]);
-          x *= 1.0f - h * h;
-        }
+        if (e.dact) x *= 1.0f - hd[i] * hd[i];
         if (e.act_tanh) x = tanhf(x);
         if (e.post_scale) x = fmaf(x, e.post_scale[n], e.post_shift[n]);
         if (e.out_f) e.out_f[m * e.ld_f + n] = x;
         if (e.out_ft) e.out_ft[(int64_t)n * e.ld_ft + m] = x;
         const bf16 xb = __float2bfloat16_rn(x);
-        if (e.out_b) e.out_b[m * e.ld_b + n] = xb;
+        if (stage_b)
+          stile[row * pitch + n] = xb;
+        else if (e.out_b)
+          e.out_b[m * e.ld_b + n] = xb;
         if (e.out_bt) e.out_bt[(int64_t)n * e.ld_bt + m] = xb;
+      }
+    }
+  }
+  if (stage_b) {
+    __syncthreads();
+    if (run) {
+      const int per_row = N / 8;
+      for (int k = tid; k < kBM * per_row; k += kThreads) {
+        const int row = k / per_row, c8 = k % per_row;
+        const int64_t m = (int64_t)m0 + row;
+        if (m < e.m_rows)
+          *reinterpret_cast<uint4 *>(e.out_b + m * e.ld_b + c8 * 8) =
+              *reinterpret_cast<const uint4 *>(stile + row * pitch + c8 * 8);
       }
     }
   }
