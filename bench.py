@@ -189,7 +189,8 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # --- timed region: K steps, every kernel bracketed by CUDA events
+    # --- timed region: K steps of the product launch path (8-step CUDA graphs),
+    # every kernel class bracketed by CUDA events recorded inside the graphs
     g.set_timing(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
@@ -207,7 +208,7 @@ def run_ours(args):
     ms_step = ms_total / args.steps
     value = replicas.weak_scaling_rate(n, args.steps, world, ms_total / 1e3)
 
-    # graph-replay time of the same step (product default), for reference
+    # the same graphs without the event records, for reference
     barrier()
     e0.record(stream)
     g.step(args.steps)
@@ -299,7 +300,8 @@ def run_ours(args):
         "config": {"workload": workload_name(n), "n_atoms": n, "precision": "mixed", "pair": f"Verlet list, skin {SKIN}",
                    "replicas": "one independent system per GPU" if world > 1 else "one system",
                    "l2": "inputs larger than L2 (state + neighbour lists + VACF ring about 5 GB)",
-                   "timing": "CUDA events around every kernel on the system stream; eager launches"},
+                   "timing": "CUDA events around every kernel class, recorded inside the replayed 8-step CUDA "
+                             "graphs (the product launch path; velocity pushes overlap the next step)"},
         "clocks": clk.summary(),
         "e2e": {"value": replicas.weak_scaling_rate(n, args.steps, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,

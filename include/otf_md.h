@@ -255,10 +255,14 @@ OTF_API int md_corr(md_handle *h, int32_t which, corr_handle **out);
 #define MD_K_SPME 5      /* reciprocal-space Ewald (MD_POT_BUCK_EWALD) */
 #define MD_NKCLASS 6
 
-/* on = 1: the following md_step calls launch every kernel directly (no graph)
- * between CUDA events on the system's stream and add each kernel class's
- * device time to counters; on = 0 stops that.  Enabling clears the
- * counters. */
+/* on = 1: the following md_step calls bracket every kernel class with CUDA
+ * events and add its device time to counters; on = 0 stops that.  Enabling
+ * clears the counters.  With graphs on (md_params.use_graph), whole groups of
+ * 8 steps replay graphs that carry the event records, so the times are those
+ * of the normal launch path (the velocity-correlator push then overlaps the
+ * next step's kernels, and their times include that sharing of the GPU);
+ * the remaining steps of a call, and every step without graphs, launch
+ * directly between events. */
 OTF_API int md_set_timing(md_handle *h, int32_t on);
 
 /* Accumulated device milliseconds [MD_NKCLASS] and launches [MD_NKCLASS]

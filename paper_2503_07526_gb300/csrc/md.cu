@@ -44,6 +44,7 @@ namespace otf {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kGraphSteps = 8;  // steps per replayed graph (velocity pushes overlap the next step)
 constexpr int kDefaultBuildKind = 0;  // list build without autotuning: 0 j-parallel, 1 i-parallel, 2 staged
 constexpr int kPairThreads = 128;     // default CTA of the pair kernel (the autotuner may pick 64 or 256)
 constexpr int kMaxPairThreads = 256;
@@ -1282,7 +1283,19 @@ struct md_handle_s {
   Sys d{};
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;   // one step
+  cudaGraphExec_t graphN = nullptr;  // kGraphSteps steps, each velocity push overlapping the next step
+  cudaStream_t side = nullptr;       // the velocity-correlator push runs here, beside the next step
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool vacf_pending = false;         // a push on `side` the next reduction must wait for
+  // timed graphs (md_set_timing with graphs): two instances of the
+  // kGraphSteps-step graph, each with its own event records inside, replayed
+  // alternately so that one is read while the other runs
+  cudaGraphExec_t graphT[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> tev[2];
+  std::vector<int> tev_class[2];
+  bool tev_pending[2] = {false, false};
+  int tset = -1;                     // the set KTimer records into while capturing (-1: eager pool)
   bool fp64 = true;
   int nrep = 1;
   int red_blocks = 1;                // reduction CTAs over all replicas
@@ -1348,6 +1361,14 @@ struct KTimer {
   ~KTimer() { mark(); }
   void mark() {
     if (!h || !h->timing) return;
+    if (h->tset >= 0) {  // capturing a timed graph: an event-record node
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      h->tev[h->tset].push_back(e);
+      h->tev_class[h->tset].push_back(cls);
+      cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+      return;
+    }
     if (h->ev_used == h->ev.size()) {
       cudaEvent_t e;
       if (cudaEventCreate(&e) != cudaSuccess) return;
@@ -1460,7 +1481,7 @@ int launch_reduce(md_handle *h, cudaStream_t s) {
 }
 
 template <typename TF, typename A>
-int launch_step(md_handle *h, cudaStream_t s) {
+int launch_step(md_handle *h, cudaStream_t s, bool overlap) {
   const Sys &d = h->d;
   {
     KTimer tm(h, s, MD_K_INTEGRATE);
@@ -1473,17 +1494,44 @@ int launch_step(md_handle *h, cudaStream_t s) {
   int rc = launch_rebuild<TF>(h, s);
   if (rc) return rc;
   if ((rc = launch_pair<TF>(h, s))) return rc;
+  // the previous step's velocity push reads the velocity buffer and the
+  // step counter this reduction rewrites
+  if (h->vacf_pending) {
+    OTF_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+    h->vacf_pending = false;
+  }
   if ((rc = launch_reduce<TF, A, true>(h, s))) return rc;
   if (h->bank_on[2]) {
-    KTimer tm(h, s, MD_K_VACF);
-    const PushIdx pi{&h->d.st->step, &h->d.st->corr_base, h->prm.vacf.u, 0};
-    if ((rc = h->banks[2].c.launch_push(h->d.vbuf, h->d.vbuf, !h->fp64, pi, s))) return rc;
+    // the push only reads this step's velocities, so it can run beside the
+    // next step's integration, sort and forces (forked onto `side`)
+    cudaStream_t ps = overlap ? h->side : s;
+    if (overlap) {
+      OTF_CUDA(cudaEventRecord(h->ev_fork, s));
+      OTF_CUDA(cudaStreamWaitEvent(ps, h->ev_fork, 0));
+    }
+    {
+      KTimer tm(h, ps, MD_K_VACF);
+      const PushIdx pi{&h->d.st->step, &h->d.st->corr_base, h->prm.vacf.u, 0};
+      if ((rc = h->banks[2].c.launch_push(h->d.vbuf, h->d.vbuf, !h->fp64, pi, ps))) return rc;
+    }
+    if (overlap) {
+      OTF_CUDA(cudaEventRecord(h->ev_join, ps));
+      h->vacf_pending = true;
+    }
   }
   return MD_OK;
 }
 
-int step_once(md_handle *h, cudaStream_t s) {
-  return h->fp64 ? launch_step<double, double>(h, s) : launch_step<float, float>(h, s);
+int step_once(md_handle *h, cudaStream_t s, bool overlap = false) {
+  return h->fp64 ? launch_step<double, double>(h, s, overlap) : launch_step<float, float>(h, s, overlap);
+}
+
+// Waits (on s) for a velocity push still running beside the step sequence.
+int join_vacf(md_handle *h, cudaStream_t s) {
+  if (!h->vacf_pending) return MD_OK;
+  OTF_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+  h->vacf_pending = false;
+  return MD_OK;
 }
 
 int refresh_obs(md_handle *h) {
@@ -1504,10 +1552,15 @@ int check_device(md_handle *h) {
   return MD_OK;
 }
 
-int build_graph(md_handle *h) {
+// Captures `steps` steps into one graph; with several, each velocity push
+// overlaps the next step (the graph ends joined).
+int capture_steps(md_handle *h, int steps, cudaGraphExec_t *out) {
   cudaGraph_t g = nullptr;
   OTF_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  int rc = step_once(h, h->cap_stream);
+  int rc = MD_OK;
+  for (int k = 0; k < steps && !rc; ++k) rc = step_once(h, h->cap_stream, steps > 1);
+  if (!rc) rc = join_vacf(h, h->cap_stream);
+  h->vacf_pending = false;
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
   if (rc) {
     if (g) cudaGraphDestroy(g);
@@ -1517,12 +1570,44 @@ int build_graph(md_handle *h) {
     set_error("graph capture failed: %s", cudaGetErrorString(e));
     return MD_ECUDA;
   }
-  e = cudaGraphInstantiate(&h->graph, g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    h->graph = nullptr;
+    *out = nullptr;
     set_error("graph instantiate failed: %s", cudaGetErrorString(e));
     return MD_ECUDA;
+  }
+  return MD_OK;
+}
+
+int build_graph(md_handle *h) {
+  int rc = capture_steps(h, 1, &h->graph);
+  if (!rc && h->bank_on[2]) rc = capture_steps(h, kGraphSteps, &h->graphN);
+  return rc;
+}
+
+int build_timed_graphs(md_handle *h) {
+  for (int k = 0; k < 2; ++k) {
+    h->tset = k;
+    const int rc = capture_steps(h, kGraphSteps, &h->graphT[k]);
+    h->tset = -1;
+    if (rc) return rc;
+  }
+  return MD_OK;
+}
+
+// Waits for the last replay of timed graph k and adds its kernel times to
+// the counters (its events come in start / stop pairs).
+int read_timed(md_handle *h, int k) {
+  if (!h->tev_pending[k]) return MD_OK;
+  h->tev_pending[k] = false;
+  const std::vector<cudaEvent_t> &ev = h->tev[k];
+  for (size_t e = 0; e + 1 < ev.size(); e += 2) {
+    OTF_CUDA(cudaEventSynchronize(ev[e + 1]));
+    float ms = 0.f;
+    OTF_CUDA(cudaEventElapsedTime(&ms, ev[e], ev[e + 1]));
+    h->kms[h->tev_class[k][e]] += ms;
+    h->klaunch[h->tev_class[k][e]] += 1;
   }
   return MD_OK;
 }
@@ -1663,7 +1748,18 @@ void release(md_handle *h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->graphN) cudaGraphExecDestroy(h->graphN);
+  for (int k = 0; k < 2; ++k) {
+    if (h->graphT[k]) cudaGraphExecDestroy(h->graphT[k]);
+    for (cudaEvent_t e : h->tev[k]) cudaEventDestroy(e);
+  }
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side) {
+    cudaStreamSynchronize(h->side);
+    cudaStreamDestroy(h->side);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   Sys &d = h->d;
   void *ptrs[] = {d.r, d.v, d.offl, d.vh, d.vl, d.F, d.epot, d.W, d.rel, d.relb, d.vbuf, d.id, d.type,
                   d.cpk, d.rB, d.vB, d.idB, d.typeB, d.cellB, d.slot, d.perm, d.cellcount, d.cellstart,
@@ -1805,6 +1901,9 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   const size_t tf = h->fp64 ? sizeof(double) : sizeof(float);
   const size_t v4 = h->fp64 ? sizeof(dvec4) : sizeof(float4);
   OTF_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  OTF_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  OTF_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  OTF_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   if (h->fp64) {
     OTF_CUDA(cudaMalloc(&d.r, 3 * n * sizeof(double)));
     OTF_CUDA(cudaMalloc(&d.v, 3 * n * sizeof(double)));
@@ -2036,11 +2135,37 @@ int md_step(md_handle *h, int64_t nsteps) {
   }
   if (nsteps == 0) return MD_OK;
   int rc = MD_OK;
-  if (h->timing || !h->prm.use_graph) {
-    for (int64_t s = 0; s < nsteps && !rc; ++s) rc = step_once(h, h->stream);
+  if (!h->prm.use_graph) {
+    for (int64_t s = 0; s < nsteps && !rc; ++s) rc = step_once(h, h->stream, true);
+    if (!rc) rc = join_vacf(h, h->stream);
+  } else if (h->timing) {
+    // the production graphs with event records inside; set k is read (which
+    // waits for its previous replay) while set k ^ 1 is queued behind it
+    if (!h->graphT[0] && (rc = build_timed_graphs(h))) return rc;
+    int64_t s = 0;
+    for (int k = 0; s + kGraphSteps <= nsteps; s += kGraphSteps, k ^= 1) {
+      if ((rc = read_timed(h, k))) return rc;
+      cudaError_t e = cudaGraphLaunch(h->graphT[k], h->stream);
+      if (e != cudaSuccess) {
+        set_error("cudaGraphLaunch failed: %s", cudaGetErrorString(e));
+        return MD_ECUDA;
+      }
+      h->tev_pending[k] = true;
+    }
+    for (int k = 0; k < 2 && !rc; ++k) rc = read_timed(h, k);
+    // the remaining steps one by one, timed by the eager event pool
+    for (; s < nsteps && !rc; ++s) rc = step_once(h, h->stream, false);
   } else {
     if (!h->graph && (rc = build_graph(h))) return rc;
-    for (int64_t s = 0; s < nsteps; ++s) {
+    int64_t s = 0;
+    for (; h->graphN && s + kGraphSteps <= nsteps; s += kGraphSteps) {
+      cudaError_t e = cudaGraphLaunch(h->graphN, h->stream);
+      if (e != cudaSuccess) {
+        set_error("cudaGraphLaunch failed: %s", cudaGetErrorString(e));
+        return MD_ECUDA;
+      }
+    }
+    for (; s < nsteps; ++s) {
       cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
       if (e != cudaSuccess) {
         set_error("cudaGraphLaunch failed: %s", cudaGetErrorString(e));

@@ -323,3 +323,35 @@ def test_list_builds_agree(pkg, precision):
     for key in ("r", "v", "F", "W"):
         for o in outb[1:]:
             assert np.array_equal(outb[0][key], o[key]), key
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_launch_paths_agree(pkg, precision):
+    """Direct launches, the 8-step graphs (each step's velocity-correlator push
+    running on a second stream beside the next step's kernels) and the timed
+    graphs give the same particles, observables and correlators bit for bit,
+    over neighbour-list rebuilds and calls that are not multiples of 8 steps;
+    the timed run counts one event bracket per kernel class and step."""
+    s = jittered(8, seed=13, T=1.2)
+    out = []
+    for graph, timing in ((False, False), (True, False), (True, True)):
+        g = pkg.System(params(pkg, s, precision=precision, skin=0.1, use_graph=graph), s["r"], s["v"])
+        g.set_timing(timing)
+        g.step(21)
+        g.step(16)
+        o = g.observables()
+        res = dict(g.particles(), U=o["U"], sigma=o["sigma"], q=o["q"])
+        for which in (pkg.MD_CORR_STRESS, pkg.MD_CORR_HEATFLUX, pkg.MD_CORR_VACF):
+            c = g.corr(which)
+            for grp in range(3):
+                res[f"c{which}_{grp}"] = c.read(grp)[1]
+        assert o["rebuilds"] >= 2
+        if timing:
+            kt = g.kernel_times()
+            for name in ("integrate", "rebuild", "pair", "reduce", "vacf"):
+                assert kt[name][1] == 37 and kt[name][0] > 0.0, name
+        g.close()
+        out.append(res)
+    for key in out[0]:
+        for o in out[1:]:
+            assert np.array_equal(out[0][key], o[key]), key
