@@ -312,6 +312,325 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc(const __grid_constant__ CU
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
+// ------------------------------------------------- fused inference forward
+//
+// The whole forward pass of a 128-row tile in one CTA: every layer's weights
+// stay in shared memory (loaded once per CTA by TMA), the inputs are
+// standardised and rounded to bfloat16 on the way into shared memory, and
+// each hidden layer's activations go from TMEM through the epilogue straight
+// back into shared memory as the next product's A operand, so only the
+// FP32 inputs and outputs cross HBM.  A CTA runs two groups of eight warps,
+// each group on its own tile (its own activation buffer and 128 TMEM
+// columns; two warps share each 32-lane quarter of TMEM and split its
+// columns), so one group's epilogue overlaps the other's tensor-core
+// products; the CTA is persistent over tiles.  Rounding points are those of
+// the layered path (bfloat16 inputs, weights and activations, FP32
+// accumulation); the inputs are standardised with the FP32 reciprocal of the
+// scale (within two FP32 units of the quotient) and tanh is evaluated as in
+// tanh2_epi below.
+constexpr int kFusedGroup = 256;                   // threads of a group: eight warps, one tile
+constexpr int kFusedThreads = 2 * kFusedGroup;     // two groups
+constexpr uint32_t kPanelBytes = kBM * 128;        // 128 rows x 64 bfloat16
+
+struct FusedMaps {
+  CUtensorMap w[kMaxLayers];  // W_l [out_p][in_k] bfloat16, boxes {64, out_p}
+};
+struct FusedArgs {
+  int L = 0, n_in = 0, k_in = 0, n_out = 0, unscale = 0;
+  int in_k[kMaxLayers] = {}, out_p[kMaxLayers] = {};
+  uint32_t w_off[kMaxLayers] = {};  // byte offset of layer l's panels in shared memory
+  uint32_t w_bytes = 0, act_bytes = 0;
+  int b_off[kMaxLayers] = {};       // offset of layer l's bias in the shared bias table
+  int nbias = 0;                    // a multiple of 16
+  const float *bias[kMaxLayers] = {};
+  const float *xmean = nullptr, *xstd = nullptr, *ymean = nullptr, *ystd = nullptr;
+};
+
+// Paired FP32 arithmetic (two lanes of a 64-bit register, each rounded to
+// nearest like the scalar instruction) for the epilogue.
+__device__ __forceinline__ uint64_t f2_pack(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t r, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// tanh of two pre-activations z = acc + bias for the epilogue, as
+// 1 - 2 / (exp(2z) + 1) from the hardware base-2 exponential and reciprocal.
+// The result tends to +-1 with the right sign as exp(2z) overflows or
+// underflows; its absolute error is about 2e-7 everywhere, below the
+// bfloat16 rounding of every activation larger than 1e-4 in magnitude that
+// follows (smaller ones are off by at most that 2e-7, which no normwise
+// comparison can see).
+__device__ __forceinline__ uint64_t tanh2_epi(uint64_t acc, uint64_t bias) {
+  const uint64_t y = f2_mul(f2_add(acc, bias), f2_pack(2.8853900817779268f, 2.8853900817779268f));  // 2 log2(e) z
+  float y0, y1, e0, e1, r0, r1;
+  f2_unpack(y, y0, y1);
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e0) : "f"(y0));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e1) : "f"(y1));
+  const uint64_t d = f2_add(f2_pack(e0, e1), f2_pack(1.0f, 1.0f));
+  f2_unpack(d, e0, e1);
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(e0));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r1) : "f"(e1));
+  return f2_fma(f2_pack(-2.0f, -2.0f), f2_pack(r0, r1), f2_pack(1.0f, 1.0f));
+}
+
+// Waits on a phase of an mbarrier with the potentially blocking try_wait
+// (the thread is suspended in hardware rather than spinning); gives up
+// (false) after kWaitNs.
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ bool mbar_wait_blocking(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_timer();
+  while (!mbar_try(bar, parity))
+    if (global_timer() - t0 > kWaitNs) return false;
+  return true;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void group_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kFusedGroup) : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Eight values as bfloat16 into 16-byte chunk `ch` of row `r` of a K-major
+// operand tile laid out as a 128-byte-swizzled TMA load would leave it:
+// 64-column panels of 128 rows x 128 bytes, chunk j of row r at
+// r * 128 + ((j ^ (r mod 8)) * 16) within its panel.
+__device__ __forceinline__ void store_chunk_sw128(uint8_t *tile, int r, int ch, const float (&x)[8]) {
+  uint4 q;
+  __nv_bfloat162 b0 = __floats2bfloat162_rn(x[0], x[1]), b1 = __floats2bfloat162_rn(x[2], x[3]);
+  __nv_bfloat162 b2 = __floats2bfloat162_rn(x[4], x[5]), b3 = __floats2bfloat162_rn(x[6], x[7]);
+  q.x = *reinterpret_cast<uint32_t *>(&b0);
+  q.y = *reinterpret_cast<uint32_t *>(&b1);
+  q.z = *reinterpret_cast<uint32_t *>(&b2);
+  q.w = *reinterpret_cast<uint32_t *>(&b3);
+  const int p = ch >> 3, j = ch & 7;
+  *reinterpret_cast<uint4 *>(tile + (size_t)p * kPanelBytes + r * 128 + ((j ^ (r & 7)) << 4)) = q;
+}
+
+// Shared tables after the activation tiles: biases [nbias], input means and
+// reciprocal scales [k_in] each (zero past n_in), output scale and shift
+// [16] each; then the barriers.
+__host__ __device__ constexpr size_t fused_tables_bytes(int nbias, int k_in) {
+  return sizeof(float) * ((size_t)nbias + 2 * (size_t)k_in + 2 * kOutPad) + 64;
+}
+
+__global__ void __launch_bounds__(kFusedThreads, 1)
+    k_mlp_fused(const __grid_constant__ FusedMaps maps, const FusedArgs a, const float *__restrict__ X,
+                int64_t rows, float *__restrict__ Y, unsigned *err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t *sw = smem;
+  uint8_t *sact = smem + a.w_bytes;
+  float *sbias = reinterpret_cast<float *>(sact + 2 * (size_t)a.act_bytes);
+  float *sxm = sbias + a.nbias, *sxr = sxm + a.k_in, *sym = sxr + a.k_in, *sys = sym + kOutPad;
+  uint64_t *bars = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(sys + kOutPad) + 7) & ~(uintptr_t)7);
+  uint32_t *slot = reinterpret_cast<uint32_t *>(bars + 3);  // bars: weights, group 0 MMA, group 1 MMA
+  int *gflag = reinterpret_cast<int *>(slot + 1);            // [2]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = tid / kFusedGroup, gt = tid % kFusedGroup, gw = warp & 7;
+  const int quarter = gw & 3, half = gw >> 2;  // TMEM lane quarter, column half of the warp
+  const uint32_t wbar = smem_u32(&bars[0]);
+
+  if (tid == 0) {
+    for (int s = 0; s < 3; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    gflag[0] = gflag[1] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(smem_u32(slot), 256);
+  for (int l = 0; l < a.L; ++l)
+    for (int c = tid; c < a.out_p[l]; c += kFusedThreads) sbias[a.b_off[l] + c] = a.bias[l][c];
+  for (int c = tid; c < a.k_in; c += kFusedThreads) {
+    sxm[c] = c < a.n_in ? a.xmean[c] : 0.f;
+    sxr[c] = c < a.n_in ? 1.0f / a.xstd[c] : 0.f;
+  }
+  for (int c = tid; c < kOutPad; c += kFusedThreads) {
+    sym[c] = a.unscale ? a.ymean[c] : 0.f;
+    sys[c] = a.unscale ? a.ystd[c] : 1.f;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  if (tid == 0) {  // every layer's weight panels, one transaction
+    mbar_expect_tx(wbar, a.w_bytes);
+    for (int l = 0; l < a.L; ++l) {
+      const uint32_t pb = (uint32_t)a.out_p[l] * 128u;
+      for (int p = 0; p * kBK < a.in_k[l]; ++p)
+        tma_load_2d(smem_u32(sw + a.w_off[l] + p * pb), &maps.w[l], p * kBK, 0, wbar);
+    }
+  }
+
+  uint8_t *act = sact + (size_t)g * a.act_bytes;
+  const uint32_t act_s = smem_u32(act);
+  const uint32_t mbar = smem_u32(&bars[1 + g]);
+  const uint32_t dcol = tmem + (uint32_t)(g * 128);                                 // the group's accumulator
+  const uint32_t trow = dcol + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 64);  // this warp's part
+  const int row = quarter * 32 + lane;                                              // tile row = TMEM lane
+  const int nch = a.k_in / 8;
+  const int r0 = gt / nch, ch0 = gt % nch, dr = kFusedGroup / nch, dch = kFusedGroup % nch;
+  const bool vec = (a.n_in % 4) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  uint32_t phase = 0;
+  bool have_w = false;
+  const int64_t ntiles = (rows + kBM - 1) / kBM;
+  for (int64_t t = 2 * (int64_t)blockIdx.x + g; t < ntiles && !gflag[g]; t += 2 * (int64_t)gridDim.x) {
+    const int64_t m0 = t * kBM;
+    // inputs: standardised, rounded to bfloat16, swizzled into the A tile;
+    // unit (r, ch) is eight columns of row r
+    int r = r0, ch = ch0;
+    const int units = kBM * nch;
+    for (int u0 = gt; u0 < units; u0 += 3 * kFusedGroup) {
+      // three units' loads in flight before any of them is used
+      float x[3][8];
+      int rr[3], cc[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        rr[k] = r;
+        cc[k] = ch;
+        const int64_t m = m0 + r;
+        const int c0 = ch * 8;
+        if (u0 + k * kFusedGroup < units && m < rows && vec && c0 + 8 <= a.n_in) {
+          const float4 p0 = __ldcs(reinterpret_cast<const float4 *>(X + m * a.n_in + c0));
+          const float4 p1 = __ldcs(reinterpret_cast<const float4 *>(X + m * a.n_in + c0 + 4));
+          x[k][0] = p0.x, x[k][1] = p0.y, x[k][2] = p0.z, x[k][3] = p0.w;
+          x[k][4] = p1.x, x[k][5] = p1.y, x[k][6] = p1.z, x[k][7] = p1.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            x[k][e] = (u0 + k * kFusedGroup < units && m < rows && c0 + e < a.n_in) ? X[m * a.n_in + c0 + e] : 0.f;
+        }
+        r += dr;
+        ch += dch;
+        if (ch >= nch) {
+          ch -= nch;
+          ++r;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        if (u0 + k * kFusedGroup >= units) break;
+        const int c0 = cc[k] * 8;
+        const float4 mu0 = *reinterpret_cast<const float4 *>(sxm + c0);
+        const float4 mu1 = *reinterpret_cast<const float4 *>(sxm + c0 + 4);
+        const float4 rs0 = *reinterpret_cast<const float4 *>(sxr + c0);
+        const float4 rs1 = *reinterpret_cast<const float4 *>(sxr + c0 + 4);
+        float y[8] = {(x[k][0] - mu0.x) * rs0.x, (x[k][1] - mu0.y) * rs0.y, (x[k][2] - mu0.z) * rs0.z,
+                      (x[k][3] - mu0.w) * rs0.w, (x[k][4] - mu1.x) * rs1.x, (x[k][5] - mu1.y) * rs1.y,
+                      (x[k][6] - mu1.z) * rs1.z, (x[k][7] - mu1.w) * rs1.w};
+        store_chunk_sw128(act, rr[k], cc[k], y);
+      }
+    }
+    fence_proxy_async();
+    group_sync(1 + g);
+    for (int l = 0; l < a.L; ++l) {
+      if (gt == 0) {
+        const bool ok = have_w || mbar_wait_blocking(wbar, 0);
+        have_w = ok;
+        tc_fence_after();
+        if (ok) {
+          const uint32_t idesc = idesc_bf16(kBM, a.out_p[l]);
+          const uint32_t wb = smem_u32(sw + a.w_off[l]), pb = (uint32_t)a.out_p[l] * 128u;
+          for (int kk = 0; kk < a.in_k[l] / 16; ++kk) {
+            const int p = kk >> 2, j = kk & 3;
+            mma_bf16(dcol, sw128_desc(act_s + p * kPanelBytes + 32u * j), sw128_desc(wb + p * pb + 32u * j), idesc,
+                     kk > 0);
+          }
+        } else {
+          gflag[g] = 1;
+        }
+        mma_commit(mbar);  // arrives once the products (if any) are done
+      }
+      const bool done = __all_sync(0xffffffffu, mbar_wait_blocking(mbar, phase));
+      phase ^= 1u;
+      tc_fence_after();
+      if (!done) {
+        gflag[g] = 1;
+      } else if (l < a.L - 1) {
+        // bias, tanh, bfloat16 of this warp's 32 rows x 64 columns: the next
+        // product's A tile
+        const float *bl = sbias + a.b_off[l] + half * 64;
+#pragma unroll 1
+        for (int c0 = 0; c0 < 64; c0 += 32) {
+          float v[32];
+          tmem_ld32(trow + (uint32_t)c0, v);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float x[8];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+              const int c = c0 + q * 8 + e;
+              const float2 b2 = *reinterpret_cast<const float2 *>(bl + c);
+              f2_unpack(tanh2_epi(f2_pack(v[q * 8 + e], v[q * 8 + e + 1]), f2_pack(b2.x, b2.y)), x[e], x[e + 1]);
+            }
+            store_chunk_sw128(act, row, half * 8 + c0 / 8 + q, x);
+          }
+        }
+      } else if (half == 0) {
+        float v[16];
+        tmem_ld16(trow, v);
+        const int64_t m = m0 + row;
+        if (m < rows) {
+          const float *bl = sbias + a.b_off[l];
+#pragma unroll
+          for (int c = 0; c < kOutPad; ++c)
+            if (c < a.n_out) Y[m * a.n_out + c] = fmaf(v[c] + bl[c], sys[c], sym[c]);
+        }
+      }
+      tc_fence_before();
+      fence_proxy_async();
+      group_sync(1 + g);
+      if (gflag[g]) break;
+    }
+  }
+  if (tid == 0) mbar_wait(wbar, 0);  // the weight copies have landed before the CTA can exit
+  if (gt == 0 && gflag[g]) atomicOr(err, 1u);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
 // Standardised, bfloat16-rounded inputs: out [rows_pad][k] row-major and
 // (optional) out_t [k][ld_t]; pad columns and rows past `rows` are zero.
 __global__ void k_prep_x(const float *__restrict__ X, int64_t rows, int n_in, const float *__restrict__ mean,
@@ -602,6 +921,13 @@ struct mlp_handle_s {
   Mat hi[2];
   float *Yi = nullptr;
   AdamTable table{};
+  // fused inference forward (when every layer's weights and two activation
+  // tiles fit in one CTA's shared memory)
+  bool fused = false;
+  size_t fused_smem = 0;
+  int nsm = 0;
+  FusedArgs fa{};
+  FusedMaps fm;
 };
 
 namespace {
@@ -836,6 +1162,48 @@ void destroy(mlp_handle *h) {
   delete h;
 }
 
+// Shared-memory plan of the fused forward: layer l's weight panels (64
+// columns x out_p rows each) back to back, then two activation tiles, then
+// the bias and scaler tables and the barriers.
+int setup_fused(mlp_handle *h) {
+  FusedArgs &a = h->fa;
+  a.L = h->L;
+  a.n_in = h->p.n_in;
+  a.k_in = h->k_in;
+  a.n_out = h->p.n_out;
+  uint32_t off = 0;
+  int boff = 0, maxp = 2;
+  for (int l = 0; l < h->L; ++l) {
+    const auto &Ly = h->lay[l];
+    const int np = (Ly.in_k + kBK - 1) / kBK;
+    a.in_k[l] = Ly.in_k;
+    a.out_p[l] = Ly.out_p;
+    a.w_off[l] = off;
+    off += (uint32_t)np * (uint32_t)Ly.out_p * 128u;
+    a.b_off[l] = boff;
+    boff += Ly.out_p;
+    a.bias[l] = h->w + Ly.b_off;
+    h->fm.w[l] = Ly.wb.map;
+    maxp = std::max(maxp, np);
+  }
+  a.w_bytes = off;
+  a.act_bytes = (uint32_t)maxp * kPanelBytes;
+  a.nbias = boff;
+  a.xmean = h->xmean;
+  a.xstd = h->xstd;
+  a.ymean = h->ymean;
+  a.ystd = h->ystd;
+  const size_t need = 1024 + (size_t)off + 2 * (size_t)a.act_bytes + fused_tables_bytes(boff, a.k_in) + 64;
+  int dev = 0, optin = 0;
+  OTF_CUDA(cudaGetDevice(&dev));
+  OTF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  OTF_CUDA(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
+  h->fused = h->p.width == kBM && need <= (size_t)optin;
+  h->fused_smem = need;
+  if (h->fused) OTF_CUDA(cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  return MD_OK;
+}
+
 int create_impl(mlp_handle *h) {
   const mlp_params &p = h->p;
   h->L = p.depth + 1;
@@ -922,7 +1290,43 @@ int create_impl(mlp_handle *h) {
   OTF_CUDA(cudaMalloc(&h->err, sizeof(unsigned)));
   OTF_CUDA(cudaMemset(h->err, 0, sizeof(unsigned)));
   OTF_CUDA(cudaDeviceSynchronize());
-  return MD_OK;
+  return setup_fused(h);
+}
+
+// One launch over all rows: inputs read once, outputs written once.
+int forward_fused(mlp_handle *h, const float *X, int64_t rows, float *Y, int32_t mem) {
+  float *own = nullptr, *own_y = nullptr;
+  const float *dX = nullptr;
+  int rc = to_device(h, X, rows * h->p.n_in, mem, &own, &dX);
+  float *dY = Y;
+  if (!rc && mem == MD_MEM_HOST) {
+    if (cudaMalloc(&own_y, sizeof(float) * rows * h->p.n_out) != cudaSuccess) {
+      set_error("mlp_forward: output buffer allocation failed");
+      rc = MD_ENOMEM;
+    }
+    dY = own_y;
+  }
+  if (!rc) {
+    const int64_t tiles = (rows + kBM - 1) / kBM;
+    const int grid = (int)std::min<int64_t>((tiles + 1) / 2, std::max(h->nsm, 1));
+    FusedArgs a = h->fa;
+    a.unscale = 1;
+    k_mlp_fused<<<grid, kFusedThreads, h->fused_smem, h->st>>>(h->fm, a, dX, rows, dY, h->err);
+    if (cudaGetLastError() != cudaSuccess) {
+      set_error("k_mlp_fused launch failed");
+      rc = MD_ECUDA;
+    }
+  }
+  if (!rc && mem == MD_MEM_HOST &&
+      cudaMemcpyAsync(Y, own_y, sizeof(float) * rows * h->p.n_out, cudaMemcpyDeviceToHost, h->st) != cudaSuccess) {
+    set_error("mlp_forward: output copy failed");
+    rc = MD_ECUDA;
+  }
+  if (!rc) rc = check_err(h);
+  cudaStreamSynchronize(h->st);
+  if (own) cudaFree(own);
+  if (own_y) cudaFree(own_y);
+  return rc;
 }
 
 }  // namespace
@@ -1065,6 +1469,7 @@ int mlp_forward(mlp_handle *h, const float *X, int64_t rows, float *Y, int32_t m
     set_error("mlp_forward: null argument or rows < 1");
     return MD_EINVAL;
   }
+  if (h->fused) return forward_fused(h, X, rows, Y, mem);
   const int64_t chunk = 65536;  // rows per pass (about 60 MB of bfloat16 activations)
   int rc = grow_inference(h, std::min(rows, chunk));
   if (rc) return rc;

@@ -76,6 +76,41 @@ def test_forward_matches_oracle(pkg, omlp, rows):
     assert e_exact <= 3e-2
 
 
+def test_forward_layered_path_matches_oracle(pkg, omlp):
+    """A five-layer network's weights and activation tiles do not fit one
+    CTA's shared memory, so its forward pass runs layer by layer (one
+    tensor-core product per layer); same bound as the fused pass."""
+    dims = (132, 128, 128, 128, 128, 128, 2)
+    params = f32(synth.mlp_init(21, dims, bias_scale=0.2))
+    net = pkg.MLP(132, 2, depth=5, seed=1)
+    net.set_params(params)
+    X = synth.normal(22, 700 * 132).reshape(700, 132).astype(np.float32)
+    Y = net.forward(X)
+    ye, _ = omlp.forward(params, X.astype(np.float64), emulate=True)
+    assert rel(Y, ye) <= 4e-3
+
+
+def test_forward_many_tiles_device_buffers(pkg, omlp):
+    """The fused pass over 1,205 tiles (each CTA loops over several, two at a
+    time) from and to device memory: sampled rows against the oracle, and
+    every sampled row equal bit for bit to the same row run in a small batch
+    on the host path (rows are independent and take the same arithmetic)."""
+    import torch
+
+    params = f32(synth.mlp_init(31, DIMS, bias_scale=0.2))
+    net = pkg.MLP(132, 2, seed=1)
+    net.set_params(params)
+    rows = 128 * 1204 + 77
+    X = synth.normal(32, rows * 132).reshape(rows, 132).astype(np.float32)
+    Yd = net.forward(torch.from_numpy(X).cuda()).cpu().numpy()
+    idx = np.unique(np.concatenate([np.arange(130), synth.permutations(33, 1, rows)[0, :1500],
+                                    np.arange(rows - 130, rows)]))
+    ye, _ = omlp.forward(params, X[idx].astype(np.float64), emulate=True)
+    assert rel(Yd[idx], ye) <= 4e-3
+    Ys = net.forward(np.ascontiguousarray(X[idx]))
+    assert np.array_equal(Ys, Yd[idx])
+
+
 def test_loss_and_gradients_match_oracle(pkg, omlp):
     B = 256
     params = f32(synth.mlp_init(21, DIMS, bias_scale=0.2))
