@@ -453,24 +453,7 @@ def run_learned_tail(pkg, torch):
     t0 = time.perf_counter()
     eta, kappa, ue, uk = tail.predict(te["X"], te["eta_short"], te["kappa_short"], te["steps_short"])
     infer_s = time.perf_counter() - t0
-    # the network's tensor-core forward pass on a large device batch
-    rows = 1 << 20
-    Xd = torch.randn(rows, lt.N_FEATURES, device="cuda", dtype=torch.float32)
-    tail.net.forward(Xd)
-    stream = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sync()
-    ev0.record(stream)
-    reps = 5
-    for _ in range(reps):
-        tail.net.forward(Xd)
-    ev1.record(stream)
-    sync()
-    fwd_ms = ev0.elapsed_time(ev1) / reps
-    dims = (lt.N_FEATURES, 128, 128, 128, 2)
-    flop = 2.0 * rows * sum(a * b for a, b in zip(dims[:-1], dims[1:]))
-    peaks, peak_kind = measured_peaks()
-    fwd_tf = flop / (fwd_ms / 1e3) / 1e12
+    fwd = mlp_forward_rate(tail.net, torch, rows=1 << 20, reps=5)
 
     def rms_rel(a, b):
         return float(np.sqrt(np.mean(((a - b) / b) ** 2)))
@@ -488,13 +471,41 @@ def run_learned_tail(pkg, torch):
         "validation_error": list(tail.val_error), "short_run_error_coefficients": list(tail.short_coeff),
         "loss_first_last": [float(hist[0]), float(hist[-1])],
         "seconds": {"generate": gen_s, "train": train_s, "inference_128": infer_s},
-        "forward_1m_rows": {"ms": fwd_ms, "tflops_algorithmic": fwd_tf, "bound": "tensor",
-                            "frac_of_bf16_peak": fwd_tf / peaks["bf16_tflops"],
-                            "peak_source": f"{peak_kind} bf16_tflops (burst)",
-                            "note": "K of every product is 128 to 144: each 128-row tile is a few MMAs between a "
-                                    "TMA load and an epilogue, so the pass is latency-bound, not tensor-bound"},
+        "forward_1m_rows": fwd,
         "ensemble_atom_steps_per_s": float(d["atoms"].sum() * 20000 / (d["seconds_short"] + d["seconds_long"])),
     }
+
+
+def mlp_forward_rate(net, torch, rows, reps, warmup=1):
+    """The network's forward pass (mlp_forward, the fused tensor-core kernel)
+    on `rows` device rows of 132 FP32 features, timed with CUDA events over
+    `reps` calls after `warmup`; FLOPs of the 132-128-128-128-2 products and
+    the HBM bytes of the FP32 inputs and outputs set its two rooflines."""
+    Xd = torch.randn(rows, net.n_in, device="cuda", dtype=torch.float32)
+    for _ in range(warmup):
+        net.forward(Xd)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(reps):
+        net.forward(Xd)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    flop = 2.0 * rows * sum(a * b for a, b in zip(net.dims[:-1], net.dims[1:]))
+    hbm = 4.0 * rows * (net.n_in + net.n_out)
+    peaks, peak_kind = measured_peaks()
+    tf = flop / (ms / 1e3) / 1e12
+    gbs = hbm / (ms / 1e3) / 1e9
+    t_hbm, t_tc = hbm / (peaks["hbm_gbs"] * 1e9), flop / (peaks["bf16_tflops"] * 1e12)  # seconds at the peaks
+    return {"rows": rows, "ms_per_call": ms, "tflops_algorithmic": tf,
+            "frac_of_bf16_peak": tf / peaks["bf16_tflops"], "input_output_gbs": gbs,
+            "frac_of_hbm": gbs / peaks["hbm_gbs"],
+            "bound": "hbm" if t_hbm > t_tc else "tensor", "frac_of_roofline": max(t_hbm, t_tc) / (ms / 1e3),
+            "peak_source": f"{peak_kind} bf16_tflops (burst), hbm_gbs",
+            "timing": "CUDA events around whole mlp_forward calls (each ends with a status read and a "
+                      "stream synchronisation)"}
 
 
 def run_learned_tail_full(args):
@@ -760,6 +771,9 @@ def main():
     ap.add_argument("--lt-judge-cells", type=int, default=160)
     ap.add_argument("--save-dataset", default=None, help="npz path for the learned-tail training set")
     ap.add_argument("--lt-dataset", default=None, help="train on this saved training set instead of generating it")
+    ap.add_argument("--mlp-only", action="store_true",
+                    help="time only the learned-tail network's forward pass (--mlp-rows rows, --steps calls)")
+    ap.add_argument("--mlp-rows", type=int, default=1 << 20)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -774,6 +788,17 @@ def main():
                                    fp64_steps=0 if args.quick else max(1, args.steps // 10))), flush=True)
     elif args.learned_tail_full:
         run_learned_tail_full(args)
+    elif args.mlp_only:
+        import torch
+
+        import paper_2503_07526_gb300 as pkg
+        from paper_2503_07526_gb300 import synth
+
+        pkg.lib()
+        net = pkg.MLP(132, 2, seed=1)
+        net.set_params(synth.mlp_init(11, net.dims, bias_scale=0.2))
+        print(json.dumps({"mlp_forward": mlp_forward_rate(net, torch, args.mlp_rows, args.steps, args.warmup)}),
+              flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:

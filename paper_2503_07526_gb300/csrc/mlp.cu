@@ -564,6 +564,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     }
     fence_proxy_async();
     group_sync(1 + g);
+    // the group's next tile's inputs (one contiguous block) on their way
+    // into L2 while this tile's products and epilogues run
+    const int64_t mn = m0 + 2 * (int64_t)gridDim.x * kBM;
+    if (gt == 0 && vec && mn < rows) {
+      const uint32_t bytes = (uint32_t)(min((int64_t)kBM, rows - mn) * a.n_in * (int64_t)sizeof(float));
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(X + mn * a.n_in), "r"(bytes) : "memory");
+    }
     for (int l = 0; l < a.L; ++l) {
       if (gt == 0) {
         const bool ok = have_w || mbar_wait_blocking(wbar, 0);
