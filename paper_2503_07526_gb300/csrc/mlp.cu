@@ -922,6 +922,7 @@ struct mlp_handle_s {
   float *T = nullptr;       // [cap][n_out]
   double *loss = nullptr;   // [2]
   unsigned *err = nullptr;
+  unsigned *err_host = nullptr;  // pinned copy of err, read after each call
   // inference state (grown on demand)
   int64_t icap = 0;
   Mat xi;
@@ -940,9 +941,9 @@ struct mlp_handle_s {
 namespace {
 
 int check_err(mlp_handle *h) {
-  unsigned e = 0;
-  OTF_CUDA(cudaMemcpyAsync(&e, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
+  OTF_CUDA(cudaMemcpyAsync(h->err_host, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
   OTF_CUDA(cudaStreamSynchronize(h->st));
+  const unsigned e = *h->err_host;
   if (e) {
     cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->st);
     set_error("a bounded tensor-core pipeline wait gave up");
@@ -1166,6 +1167,7 @@ void destroy(mlp_handle *h) {
                   (void *)h->ymean, (void *)h->ystd, (void *)h->Y, (void *)h->T, (void *)h->loss, (void *)h->err,
                   (void *)h->Yi})
     if (q) cudaFree(q);
+  if (h->err_host) cudaFreeHost(h->err_host);
   delete h;
 }
 
@@ -1296,6 +1298,8 @@ int create_impl(mlp_handle *h) {
   OTF_CUDA(cudaMemset(h->loss, 0, sizeof(double) * 2));
   OTF_CUDA(cudaMalloc(&h->err, sizeof(unsigned)));
   OTF_CUDA(cudaMemset(h->err, 0, sizeof(unsigned)));
+  OTF_CUDA(cudaMallocHost(&h->err_host, sizeof(unsigned)));
+  *h->err_host = 0u;
   OTF_CUDA(cudaDeviceSynchronize());
   return setup_fused(h);
 }
