@@ -330,6 +330,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc(const __grid_constant__ CU
 // tanh2_epi below.
 constexpr int kFusedGroup = 256;                   // threads of a group: eight warps, one tile
 constexpr int kFusedThreads = 2 * kFusedGroup;     // two groups
+constexpr int kInBatch = 3;  // input units (8 columns of a row) whose loads a thread has in flight at once
 constexpr uint32_t kPanelBytes = kBM * 128;        // 128 rows x 64 bfloat16
 
 struct FusedMaps {
@@ -467,7 +468,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   float *sbias = reinterpret_cast<float *>(sact + 2 * (size_t)a.act_bytes);
   float *sxm = sbias + a.nbias, *sxr = sxm + a.k_in, *sym = sxr + a.k_in, *sys = sym + kOutPad;
   uint64_t *bars = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(sys + kOutPad) + 7) & ~(uintptr_t)7);
-  uint32_t *slot = reinterpret_cast<uint32_t *>(bars + 3);  // bars: weights, group 0 MMA, group 1 MMA
+  // bars: weights, group 0 MMA, group 1 MMA, group 0 inputs done, group 1 inputs done
+  uint32_t *slot = reinterpret_cast<uint32_t *>(bars + 5);
   int *gflag = reinterpret_cast<int *>(slot + 1);            // [2]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = tid / kFusedGroup, gt = tid % kFusedGroup, gw = warp & 7;
@@ -475,7 +477,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   const uint32_t wbar = smem_u32(&bars[0]);
 
   if (tid == 0) {
-    for (int s = 0; s < 3; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    for (int s = 0; s < 5; ++s) mbar_init(smem_u32(&bars[s]), 1);
     gflag[0] = gflag[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -515,18 +517,28 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   uint32_t phase = 0;
   bool have_w = false;
   const int64_t ntiles = (rows + kBM - 1) / kBM;
-  for (int64_t t = 2 * (int64_t)blockIdx.x + g; t < ntiles && !gflag[g]; t += 2 * (int64_t)gridDim.x) {
+  // The two groups take turns at their input stages (group 0's k-th, then
+  // group 1's k-th, then group 0's (k+1)-th, ...), so one group streams its
+  // inputs while the other runs products and epilogues instead of both
+  // doing the same phase at the same time.  A group's tile count is at most
+  // one more than the other's, so every wait below has its arrival.
+  int k = 0;
+  for (int64_t t = 2 * (int64_t)blockIdx.x + g; t < ntiles && !gflag[g]; t += 2 * (int64_t)gridDim.x, ++k) {
     const int64_t m0 = t * kBM;
+    if (g == 1 || k > 0) {
+      const int other = 1 - g, kk = g == 1 ? k : k - 1;  // the other group's input stage to follow
+      if (!mbar_wait_blocking(smem_u32(&bars[3 + other]), (uint32_t)kk & 1u)) gflag[g] = 1;
+    }
     // inputs: standardised, rounded to bfloat16, swizzled into the A tile;
     // unit (r, ch) is eight columns of row r
     int r = r0, ch = ch0;
     const int units = kBM * nch;
-    for (int u0 = gt; u0 < units; u0 += 3 * kFusedGroup) {
-      // three units' loads in flight before any of them is used
-      float x[3][8];
-      int rr[3], cc[3];
+    for (int u0 = gt; u0 < units; u0 += kInBatch * kFusedGroup) {
+      // kInBatch units' loads in flight before any of them is used
+      float x[kInBatch][8];
+      int rr[kInBatch], cc[kInBatch];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
+      for (int k = 0; k < kInBatch; ++k) {
         rr[k] = r;
         cc[k] = ch;
         const int64_t m = m0 + r;
@@ -549,7 +561,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         }
       }
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
+      for (int k = 0; k < kInBatch; ++k) {
         if (u0 + k * kFusedGroup >= units) break;
         const int c0 = cc[k] * 8;
         const float4 mu0 = *reinterpret_cast<const float4 *>(sxm + c0);
@@ -564,6 +576,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     }
     fence_proxy_async();
     group_sync(1 + g);
+    if (gt == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bars[3 + g])) : "memory");
+    if (gflag[g]) break;
     // the group's next tile's inputs (one contiguous block) on their way
     // into L2 while this tile's products and epilogues run
     const int64_t mn = m0 + 2 * (int64_t)gridDim.x * kBM;
@@ -1202,7 +1216,7 @@ int setup_fused(mlp_handle *h) {
   a.xstd = h->xstd;
   a.ymean = h->ymean;
   a.ystd = h->ystd;
-  const size_t need = 1024 + (size_t)off + 2 * (size_t)a.act_bytes + fused_tables_bytes(boff, a.k_in) + 64;
+  const size_t need = 1024 + (size_t)off + 2 * (size_t)a.act_bytes + fused_tables_bytes(boff, a.k_in) + 128;
   int dev = 0, optin = 0;
   OTF_CUDA(cudaGetDevice(&dev));
   OTF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
