@@ -121,6 +121,13 @@ __device__ __forceinline__ void spline(T w, T (&m)[N], T (&d1)[N], T (&d2)[N]) {
 }
 
 __device__ __forceinline__ int wrap(int v, int K) { return ((v % K) + K) % K; }
+// wrap() without the divisions for the usual case v in [-K, 2K) (mesh points
+// of atoms at most a cell outside the box), with wrap() as the fallback.
+__device__ __forceinline__ int wrap_near(int v, int K) {
+  int w = v < 0 ? v + K : v;
+  w = w >= K ? w - K : w;
+  return (unsigned)w < (unsigned)K ? w : wrap(v, K);
+}
 
 constexpr int kRowThreads = 128;       // atoms per tile (one CTA)
 constexpr int kTileBytes = 48 * 1024;  // shared mesh tile of the gather
@@ -152,12 +159,12 @@ __device__ __forceinline__ void spread_atom(const int (&base)[3], const T (&frac
   spline<T, N, false>(frac[2], wz, d1, d2);
   int iz[N];
 #pragma unroll
-  for (int t = 0; t < N; ++t) iz[t] = TILE ? base[2] - t - oz : wrap(base[2] - t, K);
+  for (int t = 0; t < N; ++t) iz[t] = TILE ? base[2] - t - oz : wrap_near(base[2] - t, K);
   for (int t0 = 0; t0 < N; ++t0) {
-    const int ix = TILE ? base[0] - t0 - ox : wrap(base[0] - t0, K);
+    const int ix = TILE ? base[0] - t0 - ox : wrap_near(base[0] - t0, K);
     const T qx = q * wx[t0];
     for (int t1 = 0; t1 < N; ++t1) {
-      const int iy = TILE ? base[1] - t1 - oy : wrap(base[1] - t1, K);
+      const int iy = TILE ? base[1] - t1 - oy : wrap_near(base[1] - t1, K);
       const T qxy = qx * wy[t1];
       const int64_t row = TILE ? ((int64_t)ix * ey + iy) * ez : ((int64_t)ix * K + iy) * K;
 #pragma unroll
@@ -278,11 +285,11 @@ __global__ void __launch_bounds__(kRowThreads) k_spme_spread(SpmeAtoms a, int K,
         __syncthreads();
         for (int col = threadIdx.x; col < ncol; col += kRowThreads) {
           const int lx = col / tl.ey, ly = col % tl.ey;
-          const int64_t g0 = ((int64_t)wrap(tl.ox + lx, K) * K + wrap(tl.oy + ly, K)) * K;
+          const int64_t g0 = ((int64_t)wrap_near(tl.ox + lx, K) * K + wrap_near(tl.oy + ly, K)) * K;
           const T *cz = tile + (int64_t)col * ezp;
           for (int z = 0; z < tl.ez; ++z) {
             const long long v = to_fix(cz[z]);
-            if (v != 0) atomicAdd(Qi + g0 + wrap(tl.oz + z, K), (unsigned long long)v);
+            if (v != 0) atomicAdd(Qi + g0 + wrap_near(tl.oz + z, K), (unsigned long long)v);
           }
         }
       } else if (live) {
@@ -345,14 +352,14 @@ __device__ __forceinline__ void gather_atom(const int (&base)[3], const T (&frac
   spline<T, N, true>(frac[2], w2, d2, e2);
   int iz[N];
 #pragma unroll
-  for (int t = 0; t < N; ++t) iz[t] = TILE ? base[2] - t - oz : wrap(base[2] - t, K);
+  for (int t = 0; t < N; ++t) iz[t] = TILE ? base[2] - t - oz : wrap_near(base[2] - t, K);
 #pragma unroll
   for (int k = 0; k < 10; ++k) acc[k] = T(0);
   for (int t0 = 0; t0 < N; ++t0) {
-    const int ix = TILE ? base[0] - t0 - ox : wrap(base[0] - t0, K);
+    const int ix = TILE ? base[0] - t0 - ox : wrap_near(base[0] - t0, K);
 #pragma unroll
     for (int t1 = 0; t1 < N; ++t1) {
-      const int iy = TILE ? base[1] - t1 - oy : wrap(base[1] - t1, K);
+      const int iy = TILE ? base[1] - t1 - oy : wrap_near(base[1] - t1, K);
       const int64_t row = TILE ? ((int64_t)ix * ey + iy) * ez : ((int64_t)ix * K + iy) * K;
       const T ww = w0[t0] * w1[t1], dw = d0[t0] * w1[t1], wd = w0[t0] * d1[t1];
       const T ew = e0[t0] * w1[t1], we = w0[t0] * e1[t1], dd = d0[t0] * d1[t1];
@@ -416,13 +423,30 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_spme_gather(SpmeAtoms a, int
       const Tile tl = chunk_tile<N>(base, live, bmin, bmax);
       const bool tiled = tl.vol() <= cap;
       if (tiled) {
-        for (int64_t k = threadIdx.x; k < tl.vol(); k += kRowThreads) {
-          const int lz = (int)(k % tl.ez), ly = (int)((k / tl.ez) % tl.ey), lx = (int)(k / ((int64_t)tl.ez * tl.ey));
-          const int64_t g = ((int64_t)wrap(tl.ox + lx, K) * K + wrap(tl.oy + ly, K)) * K + wrap(tl.oz + lz, K);
+        // element k = (lx * ey + ly) * ez + lz of the tile; consecutive threads
+        // take consecutive z (coalesced), and each thread steps its (lx, ly,
+        // lz) by the mixed-radix digits of the stride instead of dividing
+        const int vol = (int)tl.vol();
+        const int dz = kRowThreads % tl.ez, qz = kRowThreads / tl.ez, dy = qz % tl.ey, dx = qz / tl.ey;
+        int lz = threadIdx.x % tl.ez, ly = (threadIdx.x / tl.ez) % tl.ey, lx = threadIdx.x / (tl.ez * tl.ey);
+        for (int k = threadIdx.x; k < vol; k += kRowThreads) {
+          const int64_t g =
+              ((int64_t)wrap_near(tl.ox + lx, K) * K + wrap_near(tl.oy + ly, K)) * K + wrap_near(tl.oz + lz, K);
           T2 v;
           v.x = phi[g];
           v.y = psi[g];
           tile[k] = v;
+          lz += dz;
+          ly += dy;
+          lx += dx;
+          if (lz >= tl.ez) {
+            lz -= tl.ez;
+            ++ly;
+          }
+          if (ly >= tl.ey) {
+            ly -= tl.ey;
+            ++lx;
+          }
         }
       }
       __syncthreads();
