@@ -788,14 +788,15 @@ __global__ void __launch_bounds__(kMaxPairThreads) k_pair_list(Sys d, LJ<TF> lj)
 // and strides over that replica's atoms.  Per-thread partial sums in A
 // (float in the mixed form, from the FP32 high words of the velocities;
 // double in FP64), the CTA and replica tree in FP64 (fixed order:
-// deterministic).  The last CTA of a replica writes its observables and
-// takes its stress and heat-flux correlator samples (Algorithm 1; series
-// 3r..3r+2 of the two correlators); the last replica to finish advances the
-// step counter.  When a velocity sample is due, velocities are also
-// scattered to atom-id order.
+// deterministic).  The last CTA of a replica writes its observables; the
+// last replica to finish advances the step counter.  When a velocity sample
+// is due, velocities are also scattered to atom-id order.  The stress,
+// heat-flux and mass-flux correlator samples of the step are taken from the
+// observables by k_push_scalars, a separate launch that can run beside the
+// next step.
 template <typename TF, typename A, bool KICK>
 __global__ void __launch_bounds__(kThreads)
-    k_kick_reduce(Sys d, double hdt, CorrDev cs, int64_t us, CorrDev ch, int64_t uh, CorrDev cm, int64_t um) {
+    k_kick_reduce(Sys d, double hdt) {
   __shared__ double red[kThreads / 32][kNRed];
   __shared__ double tot[kNRed];
   __shared__ int last;
@@ -941,23 +942,6 @@ __global__ void __launch_bounds__(kThreads)
     }
     d.counter[r] = 0u;
   }
-  if (KICK) {
-    const int64_t tc = step_now - st->corr_base;
-    const int tid = threadIdx.x;
-    if (tid < 3 && us > 0 && cs.b > 0 && tc % us == 0) {
-      const double x = tot[5 + tid] / V;  // sigma_xy, sigma_xz, sigma_yz
-      push_one_series<double>(cs, 3 * r + tid, x, x, tc / us);
-    } else if (tid >= 3 && tid < 6 && uh > 0 && ch.b > 0 && tc % uh == 0) {
-      const double x = tot[8 + tid - 3] / V;  // q_x, q_y, q_z
-      push_one_series<double>(ch, 3 * r + tid - 3, x, x, tc / uh);
-    } else if (tid >= 6 && tid < 12 && um > 0 && cm.b > 0 && tc % um == 0) {
-      // (q_a, j_a) then (j_a, j_a): series 6r .. 6r+5 of the cross correlator
-      const int a = (tid - 6) % 3;
-      const double y = tot[11 + a] / V;
-      const double x = tid < 9 ? tot[8 + a] / V : y;
-      push_one_series<double>(cm, 6 * r + tid - 6, x, y, tc / um);
-    }
-  }
   // the last replica to finish closes the step
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -970,6 +954,29 @@ __global__ void __launch_bounds__(kThreads)
   if (threadIdx.x == 0) {
     d.st->reps_done = 0u;
     if (KICK) d.st->step = step_now;
+  }
+}
+
+// The step's samples of the scalar correlators (Algorithm 1), one thread per
+// series: replica r's stress series 3r..3r+2 (sigma_xy, sigma_xz, sigma_yz),
+// heat-flux series 3r..3r+2 (q_x, q_y, q_z) and mass-flux cross series
+// 6r..6r+5 ((q_a, j_a), then (j_a, j_a)), from the observables k_kick_reduce
+// wrote for the step it counted.
+__global__ void k_push_scalars(Sys d, CorrDev cs, int64_t us, CorrDev ch, int64_t uh, CorrDev cm, int64_t um) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= (int64_t)d.nrep * 12) return;
+  const int r = (int)(k / 12), tid = (int)(k % 12);
+  const ObsDev &o = d.obs[r];
+  const int64_t tc = d.st->step - d.st->corr_base;
+  if (tid < 3) {
+    if (us > 0 && cs.b > 0 && tc % us == 0) push_one_series<double>(cs, 3 * r + tid, o.sigma[3 + tid], o.sigma[3 + tid], tc / us);
+  } else if (tid < 6) {
+    if (uh > 0 && ch.b > 0 && tc % uh == 0) push_one_series<double>(ch, 3 * r + tid - 3, o.q[tid - 3], o.q[tid - 3], tc / uh);
+  } else if (um > 0 && cm.b > 0 && tc % um == 0) {
+    const int a = (tid - 6) % 3;
+    const double y = o.j[a];
+    const double x = tid < 9 ? o.q[a] : y;
+    push_one_series<double>(cm, 6 * r + tid - 6, x, y, tc / um);
   }
 }
 
@@ -1285,9 +1292,9 @@ struct md_handle_s {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;   // one step
   cudaGraphExec_t graphN = nullptr;  // kGraphSteps steps, each velocity push overlapping the next step
-  cudaStream_t side = nullptr;       // the velocity-correlator push runs here, beside the next step
+  cudaStream_t side = nullptr;       // the correlator pushes run here, beside the next step
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  bool vacf_pending = false;         // a push on `side` the next reduction must wait for
+  bool vacf_pending = false;         // correlator pushes on `side` the next reduction must wait for
   // timed graphs (md_set_timing with graphs): two instances of the
   // kGraphSteps-step graph, each with its own event records inside, replayed
   // alternately so that one is read while the other runs
@@ -1469,12 +1476,22 @@ int launch_pair(md_handle *h, cudaStream_t s) {
 template <typename TF, typename A, bool KICK>
 int launch_reduce(md_handle *h, cudaStream_t s) {
   KTimer tm(h, s, MD_K_REDUCE);
-  const Sys &d = h->d;
+  k_kick_reduce<TF, A, KICK><<<h->red_blocks, kThreads, 0, s>>>(h->d, 0.5 * h->prm.dt);
+  OTF_LAUNCH_CHECK();
+  return MD_OK;
+}
+
+bool scalar_banks_on(const md_handle *h) { return h->bank_on[0] || h->bank_on[1] || h->bank_on[3]; }
+
+// The scalar correlator samples of the step just reduced (on s).
+int launch_push_scalars(md_handle *h, cudaStream_t s) {
+  KTimer tm(h, s, MD_K_REDUCE);
   CorrDev cs = h->bank_on[0] ? h->banks[0].c.dev : CorrDev{};
   CorrDev ch = h->bank_on[1] ? h->banks[1].c.dev : CorrDev{};
   CorrDev cm = h->bank_on[3] ? h->banks[3].c.dev : CorrDev{};
-  k_kick_reduce<TF, A, KICK><<<h->red_blocks, kThreads, 0, s>>>(
-      d, 0.5 * h->prm.dt, cs, h->bank_on[0] ? h->prm.stress.u : 0, ch, h->bank_on[1] ? h->prm.heatflux.u : 0, cm,
+  const int64_t threads = (int64_t)h->nrep * 12;
+  k_push_scalars<<<(int)ceil_div(threads, 128), 128, 0, s>>>(
+      h->d, cs, h->bank_on[0] ? h->prm.stress.u : 0, ch, h->bank_on[1] ? h->prm.heatflux.u : 0, cm,
       h->bank_on[3] ? h->prm.massflux.u : 0);
   OTF_LAUNCH_CHECK();
   return MD_OK;
@@ -1494,22 +1511,24 @@ int launch_step(md_handle *h, cudaStream_t s, bool overlap) {
   int rc = launch_rebuild<TF>(h, s);
   if (rc) return rc;
   if ((rc = launch_pair<TF>(h, s))) return rc;
-  // the previous step's velocity push reads the velocity buffer and the
-  // step counter this reduction rewrites
+  // the previous step's correlator pushes read the observables, the velocity
+  // buffer and the step counter this reduction rewrites
   if (h->vacf_pending) {
     OTF_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
     h->vacf_pending = false;
   }
   if ((rc = launch_reduce<TF, A, true>(h, s))) return rc;
-  if (h->bank_on[2]) {
-    // the push only reads this step's velocities, so it can run beside the
-    // next step's integration, sort and forces (forked onto `side`)
+  if (h->bank_on[2] || scalar_banks_on(h)) {
+    // the pushes only read this step's observables and velocities, so they
+    // can run beside the next step's integration, sort and forces (forked
+    // onto `side`)
     cudaStream_t ps = overlap ? h->side : s;
     if (overlap) {
       OTF_CUDA(cudaEventRecord(h->ev_fork, s));
       OTF_CUDA(cudaStreamWaitEvent(ps, h->ev_fork, 0));
     }
-    {
+    if (scalar_banks_on(h) && (rc = launch_push_scalars(h, ps))) return rc;
+    if (h->bank_on[2]) {
       KTimer tm(h, ps, MD_K_VACF);
       const PushIdx pi{&h->d.st->step, &h->d.st->corr_base, h->prm.vacf.u, 0};
       if ((rc = h->banks[2].c.launch_push(h->d.vbuf, h->d.vbuf, !h->fp64, pi, ps))) return rc;
@@ -1526,7 +1545,7 @@ int step_once(md_handle *h, cudaStream_t s, bool overlap = false) {
   return h->fp64 ? launch_step<double, double>(h, s, overlap) : launch_step<float, float>(h, s, overlap);
 }
 
-// Waits (on s) for a velocity push still running beside the step sequence.
+// Waits (on s) for correlator pushes still running beside the step sequence.
 int join_vacf(md_handle *h, cudaStream_t s) {
   if (!h->vacf_pending) return MD_OK;
   OTF_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
@@ -1582,7 +1601,7 @@ int capture_steps(md_handle *h, int steps, cudaGraphExec_t *out) {
 
 int build_graph(md_handle *h) {
   int rc = capture_steps(h, 1, &h->graph);
-  if (!rc && h->bank_on[2]) rc = capture_steps(h, kGraphSteps, &h->graphN);
+  if (!rc && (h->bank_on[2] || scalar_banks_on(h))) rc = capture_steps(h, kGraphSteps, &h->graphN);
   return rc;
 }
 
