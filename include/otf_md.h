@@ -109,7 +109,9 @@ typedef struct {
   int32_t pair_mode;  /* MD_PAIR_VERLET or MD_PAIR_CELLS */
   double skin;        /* Verlet skin (MD_PAIR_VERLET); 0 rebuilds every step */
   int32_t max_neighbors; /* neighbour-list capacity per atom; 0 = automatic */
-  int32_t use_graph;  /* 1: md_step replays a captured CUDA graph of a step */
+  int32_t use_graph;  /* 1: md_step replays captured CUDA graphs (8 steps at a time, each step's
+                         correlator pushes on a second stream beside the next step; a one-step
+                         graph for the rest of a call); 0: direct launches */
   int32_t autotune;   /* 1: md_init times the pair kernel (64/128/256 threads
                          per CTA) and the list build (j-parallel at 2/4/8,
                          i-parallel and staged at 4/8 warps per CTA) on the
