@@ -687,9 +687,11 @@ def committed_traffic(kernel):
     ent = tr.get(kernel)
     if not ent:
         return None
-    src = os.path.join(ROOT, "paper_2503_07526_gb300", "csrc", ent["source"])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return ent["bytes_per_launch"] if h == ent.get("source_sha") else None
+    h = hashlib.sha256()
+    for name in ent.get("sources", [ent.get("source")]):
+        with open(os.path.join(ROOT, "paper_2503_07526_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return ent["bytes_per_launch"] if h.hexdigest()[:16] == ent.get("source_sha") else None
 
 
 def cpu_baseline(st, s, budget_s=20.0):
