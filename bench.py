@@ -375,7 +375,7 @@ def run_batched(pkg, synth, steps, torch):
     g.close()
     return {"workload": "256 LJ replicas, sizes log-uniform in [500, 32000] atoms, rho* uniform in [0.7, 0.9], "
                         "T* uniform in [0.7, 2.0], rc=2.5, dt=0.005, skin 0.2, mixed form, one handle, one graph "
-                        "launch per step; stress and heat-flux correlators per replica",
+                        "launch per 8 steps; stress and heat-flux correlators per replica",
             "atoms": cfg["atoms"], "replicas": cfg["replicas"], "steps": steps, "ms_per_step": ms / steps,
             "value": cfg["atoms"] * steps / (ms / 1e3), "unit": UNIT,
             "autotuned": {"pair_threads": cfg["pair_threads"], "build_warps": cfg["build_warps"]}}
