@@ -248,6 +248,220 @@ int launch_grouped(const CorrDev &c, const Tin *x, const Tin *y, PushIdx pi, cud
   return MD_OK;
 }
 
+// Time-blocked pushes of a grouped autocorrelator (the per-atom velocity
+// correlator of an MD run), block 0: the pushes done+1 .. t (at most
+// bi.block) in one pass, with the same series-to-thread map as
+// k_push_grouped (U vectors of V series per thread).  The thread loads the
+// p-1 most recent ring samples of its series once, keeps them and the new
+// samples in registers, forms every lag product of every new push from them
+// and stores only the new samples, so a block of pushes reads the ring once
+// instead of once per push.  Its lag sums are summed over the new pushes and
+// the thread's series before the warp and CTA sums.  Products and lags are
+// those of Algorithm 1; only the order of the additions within a lag sum
+// differs.  k_push_higher then applies the higher blocks.
+template <typename T, typename Tin, int V, bool VIN, int U>
+__global__ void __launch_bounds__(kPushThreads, 1)
+    k_push_block0(CorrDev c, const Tin *__restrict__ xh, BlockIdx bi) {
+  constexpr int P1 = 15;  // older samples kept for block 0 (p - 1 with p = 16)
+  const int64_t st = *bi.d_step - *bi.d_base;
+  const int64_t t = (bi.u > 0 && st > 0) ? st / bi.u : 0;
+  const int64_t done = *bi.d_done;
+  const int nnew = (int)(t - done);
+  if (nnew <= 0 || nnew > bi.block || (!bi.flush && nnew < bi.block)) return;
+  __shared__ double red[kPushWarps][64];
+  const int g = blockIdx.y, cx = blockIdx.x;
+  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x / kWarp;
+  const int64_t i0 = ((int64_t)cx * blockDim.x + threadIdx.x) * U * V;
+  const bool act = i0 < c.gs;
+  const int64_t s = (int64_t)g * c.gs + (act ? i0 : 0);
+  const int64_t plane = c.ns;
+  T *rx = static_cast<T *>(c.ringx);
+
+  // block 0 over the new pushes, one vector of series at a time
+  T acc0[P1 + 1];
+#pragma unroll
+  for (int l = 0; l <= P1; ++l) acc0[l] = T(0);
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t su = s + u * V;
+    T win[P1][V];  // win[l]: the sample of push done - l
+#pragma unroll
+    for (int l = 0; l < P1; ++l) {
+      if (act && l < c.p - 1 && done - l >= 1) {
+        VecIO<T, V>::load(rx + ((done - l - 1) % c.p) * plane + su, win[l]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < V; ++q) win[l][q] = T(0);
+      }
+    }
+    T xn[kPushBlock][V];
+#pragma unroll
+    for (int j = 0; j < kPushBlock; ++j) {
+      if (act && j < nnew)
+        load_input<T, Tin, V, VIN>(xh + ((done + j) % kPushBlock) * plane + su, xn[j]);
+      else
+#pragma unroll
+        for (int q = 0; q < V; ++q) xn[j][q] = T(0);
+    }
+#pragma unroll
+    for (int j = 0; j < kPushBlock; ++j) {
+      if (j < nnew) {
+        const int64_t tp = done + 1 + j;  // this push
+        if (act) VecIO<T, V>::store(rx + ((tp - 1) % c.p) * plane + su, xn[j]);
+#pragma unroll
+        for (int l = 0; l <= P1; ++l) {
+          if (l < c.p && tp - l >= 1) {  // a lag of this block whose older sample exists
+            T a = T(0);
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+              const T o = (l <= j) ? xn[j - l][q] : win[l - j - 1 < P1 ? l - j - 1 : 0][q];
+              a += o * xn[j][q];
+            }
+            acc0[l] += a;
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int l = 0; l <= P1; ++l) {
+    const T a = warp_sum(acc0[l]);
+    if (lane == 0) red[warp][l] = (double)a;
+  }
+  __syncthreads();
+  if (threadIdx.x <= P1 && (int)threadIdx.x < c.p) {
+    double sum = 0.0;
+    for (int w = 0; w < kPushWarps; ++w) sum += red[w][threadIdx.x];
+    c.vals[(((int64_t)g * c.nchunk + cx) * c.b + 0) * c.p + threadIdx.x] += sum;
+  }
+  __syncthreads();
+}
+
+// The higher blocks of the pushes done+1 .. t that k_push_block0 applied to
+// block 0, push by push and block by block as in k_push_grouped (block k's
+// sample is the mean of block k-1's last m samples, already stored); the
+// last CTA to finish records the pushes as applied.
+template <typename T, int V, int U>
+__global__ void __launch_bounds__(kPushThreads) k_push_higher(CorrDev c, BlockIdx bi) {
+  const int64_t st = *bi.d_step - *bi.d_base;
+  const int64_t t = (bi.u > 0 && st > 0) ? st / bi.u : 0;
+  const int64_t done = *bi.d_done;
+  const int nnew = (int)(t - done);
+  if (nnew <= 0 || nnew > bi.block || (!bi.flush && nnew < bi.block)) return;
+  __shared__ double red[kPushWarps][64];
+  const int g = blockIdx.y, cx = blockIdx.x;
+  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x / kWarp;
+  const int64_t i0 = ((int64_t)cx * blockDim.x + threadIdx.x) * U * V;
+  const bool act = i0 < c.gs;
+  const int64_t s = (int64_t)g * c.gs + (act ? i0 : 0);
+  const int64_t plane = c.ns;
+  T *rx = static_cast<T *>(c.ringx);
+  // higher blocks, push by push
+  for (int j = 0; j < nnew; ++j) {
+    const int64_t tp = done + 1 + j;
+    int64_t Mk = 1;
+    for (int k = 1; k < c.b; ++k) {
+      Mk *= c.m;
+      if (tp % Mk) break;
+      const int64_t nk = tp / Mk;
+      const int slot = (int)((nk - 1) % c.p);
+      const int lo = c.p / c.m;
+      const int nl = (int)min((int64_t)c.p - 1, nk - 1) - lo + 1;
+      T *rxk = rx + (int64_t)k * c.p * plane;
+      T xk[U][V];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+#pragma unroll
+        for (int q = 0; q < V; ++q) xk[u][q] = T(0);
+        if (act) {
+          const int64_t su = s + u * V;
+          const int64_t nprev = nk * c.m;
+          const T *rp = rx + (int64_t)(k - 1) * c.p * plane;
+          T sx[V], av[V];
+#pragma unroll
+          for (int q = 0; q < V; ++q) sx[q] = T(0);
+          for (int jj = c.m - 1; jj >= 0; --jj) {
+            const int sl = (int)((nprev - 1 - jj) % c.p);
+            VecIO<T, V>::load(rp + sl * plane + su, av);
+#pragma unroll
+            for (int q = 0; q < V; ++q) sx[q] += av[q];
+          }
+#pragma unroll
+          for (int q = 0; q < V; ++q) xk[u][q] = sx[q] / T(c.m);
+          VecIO<T, V>::store(rxk + slot * plane + su, xk[u]);
+        }
+      }
+      for (int l = 0; l < nl; ++l) {
+        const int lag = lo + l;
+        int jr = slot - lag;
+        if (jr < 0) jr += c.p;
+        T a = T(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          T older[V];
+          if (act) {
+            VecIO<T, V>::load(rxk + jr * plane + s + u * V, older);
+          } else {
+#pragma unroll
+            for (int q = 0; q < V; ++q) older[q] = T(0);
+          }
+#pragma unroll
+          for (int q = 0; q < V; ++q) a += older[q] * xk[u][q];
+        }
+        a = warp_sum(a);
+        if (lane == 0) red[warp][l] = (double)a;
+      }
+      if (nl <= 0) continue;
+      __syncthreads();
+      if (threadIdx.x < nl) {
+        double sum = 0.0;
+        for (int w = 0; w < kPushWarps; ++w) sum += red[w][threadIdx.x];
+        c.vals[(((int64_t)g * c.nchunk + cx) * c.b + k) * c.p + lo + threadIdx.x] += sum;
+      }
+      __syncthreads();
+    }
+  }
+
+  // the last CTA to finish records the pushes as applied
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(bi.d_ctas, 1u) == gridDim.x * gridDim.y - 1) {
+      *bi.d_done = t;
+      *bi.d_ctas = 0u;
+      __threadfence();
+    }
+  }
+}
+
+template <typename T, typename Tin>
+int launch_grouped_block(const CorrDev &c, const Tin *x, BlockIdx bi, cudaStream_t s) {
+  dim3 grid(c.nchunk, (unsigned)c.ng);
+  constexpr int V = 16 / sizeof(T);
+  if (c.vec == V) {
+    const bool vin = reinterpret_cast<uintptr_t>(x) % (V * sizeof(Tin)) == 0 &&
+                     (c.ns * sizeof(Tin)) % (V * sizeof(Tin)) == 0;
+    if (c.vu == 2) {
+      if (vin)
+        k_push_block0<T, Tin, V, true, 2><<<grid, kPushThreads, 0, s>>>(c, x, bi);
+      else
+        k_push_block0<T, Tin, V, false, 2><<<grid, kPushThreads, 0, s>>>(c, x, bi);
+      k_push_higher<T, V, 2><<<grid, kPushThreads, 0, s>>>(c, bi);
+    } else {
+      if (vin)
+        k_push_block0<T, Tin, V, true, 1><<<grid, kPushThreads, 0, s>>>(c, x, bi);
+      else
+        k_push_block0<T, Tin, V, false, 1><<<grid, kPushThreads, 0, s>>>(c, x, bi);
+      k_push_higher<T, V, 1><<<grid, kPushThreads, 0, s>>>(c, bi);
+    }
+  } else {
+    k_push_block0<T, Tin, 1, false, 1><<<grid, kPushThreads, 0, s>>>(c, x, bi);
+    k_push_higher<T, 1, 1><<<grid, kPushThreads, 0, s>>>(c, bi);
+  }
+  OTF_LAUNCH_CHECK();
+  return MD_OK;
+}
+
 template <typename T, typename Tin>
 int launch_series(const CorrDev &c, const Tin *x, const Tin *y, PushIdx pi, cudaStream_t s) {
   int blocks = std::max(1, std::min(ceil_div(c.ns, 128), 152 * 8));
@@ -353,6 +567,19 @@ int Correlator::launch_push(const void *x, const void *y, bool input_fp32, PushI
   }
   if (input_fp32) return launch_series<float, float>(dev, (const float *)x, (const float *)y, pi, s);
   return launch_series<float, double>(dev, (const double *)x, (const double *)y, pi, s);
+}
+
+int Correlator::launch_push_block(const void *x, bool input_fp32, BlockIdx bi, cudaStream_t s) {
+  if (!grouped || dev.cross || prm.p > 16 || bi.block < 1 || bi.block > kPushBlock) {
+    set_error("blocked pushes need a grouped autocorrelator with p <= 16 and 1..%d pushes per block", kPushBlock);
+    return MD_EINVAL;
+  }
+  if (prec == MD_PREC_FP64) {
+    if (input_fp32) return launch_grouped_block<double, float>(dev, (const float *)x, bi, s);
+    return launch_grouped_block<double, double>(dev, (const double *)x, bi, s);
+  }
+  if (input_fp32) return launch_grouped_block<float, float>(dev, (const float *)x, bi, s);
+  return launch_grouped_block<float, double>(dev, (const double *)x, bi, s);
 }
 
 int Correlator::fetch(double *vals_host) {

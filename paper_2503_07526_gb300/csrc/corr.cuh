@@ -40,6 +40,24 @@ struct PushIdx {
   int64_t t_host;
 };
 
+// Time-blocked pushes of a grouped autocorrelator fed by an MD step: the
+// sample of push t waits in input slot (t - 1) mod kPushBlock (each [ns])
+// and the waiting pushes are applied in one pass once `block` of them wait
+// (or whatever waits, when flushing): done+1 .. t, with t from the step
+// counter as in PushIdx.  A block holds at most p - m + 1 pushes, so that
+// its block-0 stores cannot overwrite a sample its first block-1 sample
+// still needs.  The pass's last CTA advances *d_done.
+constexpr int kPushBlock = 8;
+struct BlockIdx {
+  const int64_t *d_step;
+  const int64_t *d_base;
+  int64_t u;
+  int64_t *d_done;   // pushes applied so far
+  unsigned *d_ctas;  // CTAs of the current pass that have finished (returns to 0)
+  int block;         // pushes per pass: min(kPushBlock, p - m + 1)
+  int flush;         // 1: apply a partial block too
+};
+
 __device__ __forceinline__ bool resolve_push(const PushIdx &pi, int64_t *t) {
   if (pi.d_step) {
     const int64_t st = *pi.d_step - (pi.d_base ? *pi.d_base : 0);
@@ -116,6 +134,9 @@ struct Correlator {
   }
   // Enqueues one push whose input already lives on the device.
   int launch_push(const void *x, const void *y, bool input_fp32, PushIdx pi, cudaStream_t s);
+  // Enqueues the waiting pushes of a grouped autocorrelator whose samples sit
+  // in kPushBlock slots of ns values at x (see BlockIdx).
+  int launch_push_block(const void *x, bool input_fp32, BlockIdx bi, cudaStream_t s);
   // Lag sums [ng][b][p] on the host (folds the per-block partial sums).
   int fetch(double *vals_host);
 };

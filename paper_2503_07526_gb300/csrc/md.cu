@@ -59,6 +59,8 @@ struct StepDev {
   int64_t corr_base;  // step at the last correlator reset
   int64_t rebuilds;   // neighbour-list / cell rebuilds since md_init
   unsigned reps_done; // replicas whose reduction finished in this launch
+  unsigned vacf_ctas; // CTAs of a blocked velocity push that have finished (returns to 0)
+  int64_t vacf_done;  // velocity-correlator pushes applied (the rest wait in their input slots)
 };
 
 // Observables of one replica.
@@ -85,6 +87,7 @@ struct Rep {
 struct Sys {
   int64_t n, ncell, maxchunks;  // totals over all replicas
   int nrep, ntypes, maxnb, always_rebuild, vacf_u;
+  int vacf_slots;  // velocity input slots: kPushBlock (blocked pushes) or 1 (one push per step)
   double dt, lim2;
   double invm[8], mass[8];
   double charge[8];            // per type (MD_POT_BUCK_EWALD); the pair records carry it in w
@@ -101,7 +104,8 @@ struct Sys {
   float *offl, *vh, *vl;     // mixed form: offset low words, velocity words [3][n]
   void *F, *epot, *W;        // [3][n], [n], [6][n] in the pair type
   void *rel, *relb;          // Vec4 of the pair type: current / at last rebuild
-  void *vbuf;                // [3][n] velocities in atom-id order (correlator input)
+  void *vbuf;                // [vacf_slots][3][n] velocities in atom-id order, one slot per waiting
+                             // velocity-correlator push ((push - 1) mod vacf_slots)
   int *id, *type, *cpk;      // atom id, type, packed cell coordinates
   // rebuild scratch (24 bytes per atom each)
   double *rB, *vB;
@@ -808,6 +812,8 @@ __global__ void __launch_bounds__(kThreads)
   const StepDev *st = d.st;
   const int64_t step_now = st->step + (KICK ? 1 : 0);
   const bool vacf_due = KICK && d.vacf_u > 0 && ((step_now - st->corr_base) % d.vacf_u == 0);
+  if (vacf_due)  // this push's input slot
+    vb += (((step_now - st->corr_base) / d.vacf_u - 1) % d.vacf_slots) * 3 * n;
   const int r = d.rep_of_block[blockIdx.x];
   const Rep &R = d.rep[r];
   const int lb = (int)(blockIdx.x - R.block0);
@@ -1483,6 +1489,15 @@ int launch_reduce(md_handle *h, cudaStream_t s) {
 
 bool scalar_banks_on(const md_handle *h) { return h->bank_on[0] || h->bank_on[1] || h->bank_on[3]; }
 
+// The waiting velocity-correlator pushes: a full block, or all of them when
+// flushing.
+int launch_vacf_block(md_handle *h, cudaStream_t s, bool flush) {
+  const int block = std::min(kPushBlock, h->prm.vacf.p - h->prm.vacf.m + 1);  // see BlockIdx
+  const BlockIdx bi{&h->d.st->step, &h->d.st->corr_base, h->prm.vacf.u, &h->d.st->vacf_done,
+                    &h->d.st->vacf_ctas, std::max(block, 1), flush ? 1 : 0};
+  return h->banks[2].c.launch_push_block(h->d.vbuf, !h->fp64, bi, s);
+}
+
 // The scalar correlator samples of the step just reduced (on s).
 int launch_push_scalars(md_handle *h, cudaStream_t s) {
   KTimer tm(h, s, MD_K_REDUCE);
@@ -1529,9 +1544,16 @@ int launch_step(md_handle *h, cudaStream_t s, bool overlap) {
     }
     if (scalar_banks_on(h) && (rc = launch_push_scalars(h, ps))) return rc;
     if (h->bank_on[2]) {
+      // the pushes wait in their input slots and are applied a block at a
+      // time (the launches return at once until a block is full); one per
+      // step for p > 16
       KTimer tm(h, ps, MD_K_VACF);
-      const PushIdx pi{&h->d.st->step, &h->d.st->corr_base, h->prm.vacf.u, 0};
-      if ((rc = h->banks[2].c.launch_push(h->d.vbuf, h->d.vbuf, !h->fp64, pi, ps))) return rc;
+      if (h->d.vacf_slots > 1) {
+        if ((rc = launch_vacf_block(h, ps, false))) return rc;
+      } else {
+        const PushIdx pi{&h->d.st->step, &h->d.st->corr_base, h->prm.vacf.u, 0};
+        if ((rc = h->banks[2].c.launch_push(h->d.vbuf, h->d.vbuf, !h->fp64, pi, ps))) return rc;
+      }
     }
     if (overlap) {
       OTF_CUDA(cudaEventRecord(h->ev_join, ps));
@@ -1906,6 +1928,8 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   }
   d.maxnb = maxnb;
   d.vacf_u = p->vacf.u;
+  // blocked velocity pushes keep the p - 1 <= 15 most recent samples in registers
+  d.vacf_slots = (p->vacf.b > 0 && p->vacf.p <= 16) ? kPushBlock : 1;
   d.maxchunks = (n + 31) / 32;  // 32-atom chunks of the neighbour lists
   for (int t = 0; t < 8; ++t) {
     const dfloat hh = df_from_double(0.5 * p->dt * d.invm[t]);
@@ -1936,7 +1960,7 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   OTF_CUDA(cudaMalloc(&d.W, 6 * n * tf));
   OTF_CUDA(cudaMalloc(&d.rel, n * v4));
   OTF_CUDA(cudaMalloc(&d.relb, n * v4));
-  OTF_CUDA(cudaMalloc(&d.vbuf, 3 * n * tf));
+  OTF_CUDA(cudaMalloc(&d.vbuf, (size_t)d.vacf_slots * 3 * n * tf));
   OTF_CUDA(cudaMalloc(&d.id, n * sizeof(int)));
   OTF_CUDA(cudaMalloc(&d.type, n * sizeof(int)));
   OTF_CUDA(cudaMalloc(&d.cpk, n * sizeof(int)));
@@ -1992,7 +2016,7 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   OTF_CUDA(cudaMemsetAsync(d.st, 0, sizeof(StepDev), st));
   OTF_CUDA(cudaMemsetAsync(d.err, 0, sizeof(unsigned), st));
   OTF_CUDA(cudaMemsetAsync(d.F, 0, 3 * n * tf, st));
-  OTF_CUDA(cudaMemsetAsync(d.vbuf, 0, 3 * n * tf, st));
+  OTF_CUDA(cudaMemsetAsync(d.vbuf, 0, (size_t)d.vacf_slots * 3 * n * tf, st));
   OTF_CUDA(cudaMemsetAsync(d.rebuild, 1, (count + 1) * sizeof(int), st));  // every flag set (nonzero)
   // inputs, replica after replica, component-major within the whole system:
   // FP64 form straight into the state; mixed form through the scratch,
@@ -2193,6 +2217,9 @@ int md_step(md_handle *h, int64_t nsteps) {
     }
   }
   if (rc) return rc;
+  // pushes still waiting for a full block are applied before the call
+  // returns, so the correlators always hold every step taken
+  if (h->bank_on[2] && h->d.vacf_slots > 1 && (rc = launch_vacf_block(h, h->stream, true))) return rc;
   h->steps_done += nsteps;
   rc = check_device(h);
   if (h->timing && !rc) {
@@ -2308,6 +2335,8 @@ int md_reset_correlators(md_handle *h) {
   int rc = fetch_obs(h);
   if (rc) return rc;
   h->h_st->corr_base = h->h_st->step;
+  h->h_st->vacf_done = 0;
+  h->h_st->vacf_ctas = 0u;
   for (int k = 0; k < h->nrep; ++k) {
     h->h_obs[k].Tsum = 0.0;
     h->h_obs[k].Tn = 0;

@@ -356,3 +356,46 @@ def test_launch_paths_agree(pkg, precision):
     for key in out[0]:
         for o in out[1:]:
             assert np.array_equal(out[0][key], o[key]), key
+
+
+@pytest.mark.parametrize("prec,p,u", [(0, 16, 1), (0, 16, 2), (0, 8, 1), (1, 16, 1)])
+def test_blocked_velocity_pushes(pkg, oracle_mod, prec, p, u):
+    """The per-atom velocity correlator's pushes wait in input slots and are
+    applied a block at a time (8 pushes, or p - m + 1 when smaller).  Calls
+    of 13, 8, 3 and 40 steps start blocks at several offsets and end in
+    partial flushes.  FP64: against the oracle correlator fed the oracle's
+    own velocities after every step (push every u steps); mixed: against the
+    same system stepped one step per call, whose pushes are applied one at a
+    time (same trajectory, only the order of the additions within a lag sum
+    differs)."""
+    s = jittered(8, seed=11, T=1.0)
+    n = s["n"]
+    spec = dict(stress=(5, 16, 2, 1), heatflux=(5, 8, 2, 2), vacf=(4, p, 2, u))
+    g = pkg.System(params(pkg, s, precision=prec, **spec), s["r"], s["v"])
+    for k in (13, 8, 3, 40):
+        g.step(k)
+    c = g.corr(pkg.MD_CORR_VACF)
+    if prec == 0:
+        cv = oracle_mod.Corr(4, p, 2, 3 * n, gs=n)
+        md = oracle_mod.MD(s["r"], s["v"], s["L"])
+        for step in range(1, 65):
+            md.step(1)
+            if step % u == 0:
+                cv.push(md.get()["v"])
+        for grp in range(3):
+            tg, vg = c.read(grp)
+            to, vo = cv.read(grp)
+            assert np.allclose(tg, to * u * 0.005, rtol=1e-14)
+            assert np.abs(vg - vo).max() <= 1e-11 * abs(vo[0]), grp
+    else:
+        g1 = pkg.System(params(pkg, s, precision=prec, **spec), s["r"], s["v"])
+        for _ in range(64):
+            g1.step(1)
+        assert np.array_equal(g1.particles()["v"], g.particles()["v"])
+        c1 = g1.corr(pkg.MD_CORR_VACF)
+        for grp in range(3):
+            tg, vg = c.read(grp)
+            t1, v1 = c1.read(grp)
+            assert np.array_equal(tg, t1)
+            assert np.abs(vg - v1).max() <= 2e-5 * abs(v1[0]), grp
+    assert c.pushes() == 64 // u
