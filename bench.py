@@ -309,7 +309,7 @@ def run_ours(args):
     vacf_gbs = vacf_timed_bytes(args, b, pp, m, n) / (ktimes["vacf"][0] / 1e3) / 1e9
     pair_tf = PAIR_FLOP_PER_ATOM * n * ktimes["pair"][1] / (ktimes["pair"][0] / 1e3) / 1e12
 
-    launches_per_step = 10  # kick_drift, 5 sort kernels, list build, pair, kick_reduce, VACF push
+    launches_per_step = 12  # kick_drift, 5 sort kernels, list build, pair, kick_reduce, scalar push, 2 VACF push kernels
     out = {
         "metric": METRIC,
         "value": value,
