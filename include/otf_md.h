@@ -206,9 +206,12 @@ OTF_API int md_init_replicas(const md_params *p, const md_replica *reps, int32_t
  * per-particle energy and virial; half kick; reduction to U, K, sigma, q;
  * correlator samples of the stress and heat flux every stress.u /
  * heatflux.u steps and of every atom's velocity every vacf.u steps
- * (Algorithm 1).  Everything stays on the device.  Synchronises the stream
- * at the end and returns MD_ESTATE if a device check failed (the state is
- * then undefined). */
+ * (Algorithm 1; with vacf.p <= 16 the velocity samples wait in device slots
+ * and are applied eight at a time, and whatever waits is applied before the
+ * call returns, so the correlators always hold every step taken).
+ * Everything stays on the device.  Synchronises the stream at the end and
+ * returns MD_ESTATE if a device check failed (the state is then
+ * undefined). */
 OTF_API int md_step(md_handle *h, int64_t nsteps);
 
 /* Observables of the last step (synchronises); replica 0 of a batch. */
@@ -261,8 +264,8 @@ OTF_API int md_corr(md_handle *h, int32_t which, corr_handle **out);
  * events and add its device time to counters; on = 0 stops that.  Enabling
  * clears the counters.  With graphs on (md_params.use_graph), whole groups of
  * 8 steps replay graphs that carry the event records, so the times are those
- * of the normal launch path (the velocity-correlator push then overlaps the
- * next step's kernels, and their times include that sharing of the GPU);
+ * of the normal launch path (the correlator pushes then overlap the next
+ * step's kernels, and their times include that sharing of the GPU);
  * the remaining steps of a call, and every step without graphs, launch
  * directly between events. */
 OTF_API int md_set_timing(md_handle *h, int32_t on);
