@@ -200,12 +200,28 @@ int orc_lj_cells(int64_t n, const double *r, double L, double eps, double sig,
 /* For tests of reduced-precision forces: per atom, the number of
  * neighbours whose distance lies within band of rc, where the truncated
  * force jumps by |f(rc)| and a rounded distance may fall on either side of
- * the cutoff (both results are then valid).  Link cells as above. */
+ * the cutoff (both results are then valid).  Link cells as above, at least
+ * rc + band wide, so that a pair up to rc + band apart lies in neighbouring
+ * cells. */
 int orc_lj_near_cutoff(int64_t n, const double *r, double L, double rc, double band,
                        int32_t *count) {
-  if (n < 0 || rc <= 0.0 || band < 0.0) return ORC_EINVAL;
-  int nc = (int)floor(L / rc);
-  if (nc < 3) return ORC_EINVAL;
+  if (n < 0 || rc <= 0.0 || band < 0.0 || !(L > 0.0)) return ORC_EINVAL;
+  int nc = (int)floor(L / (rc + band));
+  if (nc < 3) {  /* a box under three cells wide: every pair */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+      int32_t k = 0;
+      for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        double dx = min_image(r[i] - r[j], L);
+        double dy = min_image(r[n + i] - r[n + j], L);
+        double dz = min_image(r[2 * n + i] - r[2 * n + j], L);
+        if (fabs(sqrt(dx * dx + dy * dy + dz * dz) - rc) <= band) ++k;
+      }
+      count[i] = k;
+    }
+    return ORC_OK;
+  }
   double edge = L / nc;
   int64_t ncell = (int64_t)nc * nc * nc;
   int64_t *head = malloc(sizeof(int64_t) * ncell);

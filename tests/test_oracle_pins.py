@@ -75,6 +75,50 @@ def test_link_cells_equal_brute_force(oracle_mod, cells, rho):
         assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
 
 
+def brute_near_cutoff(r, L, rc, band):
+    """Per atom, the neighbours at minimum-image distance within band of rc,
+    over all pairs (no cells)."""
+    d = r[:, :, None] - r[:, None, :]
+    d -= L * np.round(d / L)
+    dist = np.sqrt((d ** 2).sum(axis=0))
+    np.fill_diagonal(dist, np.inf)
+    return (np.abs(dist - rc) <= band).sum(axis=1)
+
+
+def test_near_cutoff_count_equals_brute_force(oracle_mod):
+    """The near-cutoff pair count (the allowance of the FP32 force parity
+    test) against all pairs: random atoms in a 3-cell box, and planted pairs
+    just inside and outside rc +- band, across the periodic boundary and
+    along a body diagonal, in a box whose cells are exactly rc wide (a pair
+    at rc + band/2 there can lie two cells apart)."""
+    rc, band = 2.5, 0.2
+    L = 9.0
+    r = L * synth.uniform01(77, 3 * 200).reshape(3, 200)
+    got = oracle_mod.near_cutoff_pairs(r, L, rc, band)
+    want = brute_near_cutoff(r, L, rc, band)
+    assert want.sum() > 100
+    assert np.array_equal(got, want)
+    # planted pairs, L = 3 rc: one cell of edge rc per third of the box
+    L, band = 3 * rc, 1e-3
+    dirs = np.array([[1, 0, 0], [0, 1, 0], [1, 1, 1], [1, -1, 0]], dtype=float)
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    starts = np.array([[0.2, 3.0, 3.0], [7.4, 0.3, 5.0], [1.0, 1.0, 1.0], [6.0, 6.2, 2.0]])
+    offsets = [-0.4 * band, 0.4 * band, -1.5 * band, 1.5 * band]
+    pos = []
+    for k, off in enumerate(offsets):
+        a = starts[k]
+        pos += [a, a + (rc + off) * dirs[k]]
+    r = np.mod(np.array(pos).T, L)
+    got = oracle_mod.near_cutoff_pairs(r, L, rc, band)
+    want = brute_near_cutoff(r, L, rc, band)
+    assert want.tolist() == [1, 1, 1, 1, 0, 0, 0, 0]
+    assert np.array_equal(got, want)
+    # L = 5 rc: a pair at rc + band/2 whose atoms sit in cells 0 and 2
+    L = 5 * rc
+    r = np.array([[2.4998, 2.4998 + rc + 0.4 * band], [1.0, 1.0], [1.0, 1.0]])
+    assert np.array_equal(oracle_mod.near_cutoff_pairs(r, L, rc, band), [1, 1])
+
+
 def test_newton_third_law_and_energy_sum(oracle_mod):
     r, L = perturbed_fcc(6, 0.8442, 0.4, seed=3)
     F, e, W = oracle_mod.lj_forces(r, L, method="cells")
