@@ -13,8 +13,9 @@
 // kNoAllocBlocks CTAs.  Every GPU that loads the library holds it until the
 // process exits.  Host code cannot use the array's name as a device
 // address, so the first call on each device looks the address up with
-// cudaGetSymbolAddress (that device current) and clears the counter; that
-// first call should come before any stream capture.  All calls on a device
+// cudaGetSymbolAddress (that device current) and clears the counter on the
+// caller's stream, ahead of its own launch; that first call should come
+// before any stream capture.  All calls on a device
 // share the one array: calls that overlap on the GPU race and must be
 // ordered by the caller (one stream, or events).
 #include <cstdint>
@@ -108,8 +109,10 @@ __global__ void __launch_bounds__(kNoAllocThreads)
 }
 
 // Device address of the scratch on the current device; the first call on a
-// device looks it up and zeroes the completion counter.
-int scratch_for_current_device(double **out) {
+// device looks it up and zeroes the completion counter on `stream` (the
+// stream the caller's launch follows on, so the two are ordered whatever
+// kind of stream it is).
+int scratch_for_current_device(cudaStream_t stream, double **out) {
   int dev = 0;
   OTF_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) {
@@ -120,7 +123,7 @@ int scratch_for_current_device(double **out) {
   if (!g_scratch_ptr[dev]) {
     double *p = nullptr;
     OTF_CUDA(cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_noalloc_scratch));
-    OTF_CUDA(cudaMemset(p + kCounterSlot, 0, sizeof(double)));
+    OTF_CUDA(cudaMemsetAsync(p + kCounterSlot, 0, sizeof(double), stream));
     g_scratch_ptr[dev] = p;
   }
   *out = g_scratch_ptr[dev];
@@ -143,7 +146,7 @@ int md_observables_noalloc(int64_t n, double volume, const double *v, const doub
     return MD_EINVAL;
   }
   double *scratch = nullptr;
-  int rc = scratch_for_current_device(&scratch);
+  int rc = scratch_for_current_device((cudaStream_t)cuda_stream, &scratch);
   if (rc) return rc;
   const int64_t want = (n + kNoAllocThreads - 1) / kNoAllocThreads;
   const int blocks = (int)(want < kNoAllocBlocks ? want : kNoAllocBlocks);

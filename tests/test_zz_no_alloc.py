@@ -1,8 +1,10 @@
 """md_observables_noalloc: the observables reduction for callers that may
 not allocate device memory (fixed device-memory pools, no cudaMalloc after
 start-up).  Checked through the C ABI against the existing md_observables on
-the same particles, twice in a row (the shared scratch must be reusable).
-FP64 tolerance as in the other parity tests: 1e-11 relative per array."""
+the same particles, twice in a row (the shared scratch must be reusable),
+and against the oracle's observables (Sec. 2.3) of the same per-particle
+arrays.  FP64 tolerance as in the other parity tests: 1e-11 relative per
+array."""
 import numpy as np
 import pytest
 
@@ -26,7 +28,7 @@ def rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-def test_noalloc_observables_match_md_observables(pkg):
+def test_noalloc_observables_match_md_observables(pkg, oracle_mod):
     import torch
 
     s = synth.lj_system(10, seed=3)
@@ -48,6 +50,11 @@ def test_noalloc_observables_match_md_observables(pkg):
         assert got[2] == pytest.approx(want["T"], rel=1e-11)
         assert rel(got[3:9], want["sigma"]) <= 1e-11
         assert rel(got[9:12], want["q"]) <= 1e-11
+        ora = oracle_mod.observables(s["L"] ** 3, np.ones(n), v.cpu().numpy(), e.cpu().numpy(), W.cpu().numpy())
+        assert got[0] == pytest.approx(ora[0], rel=1e-11)
+        assert got[1] == pytest.approx(ora[1], rel=1e-11)
+        assert rel(got[3:9], ora[3:9]) <= 1e-11
+        assert rel(got[9:12], ora[9:12]) <= 1e-11
         out.fill_(float("nan"))
 
 
