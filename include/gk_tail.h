@@ -91,6 +91,16 @@ OTF_API int mlp_adam_step(mlp_handle *h, const float *grad, int32_t mem);
 OTF_API int mlp_train(mlp_handle *h, const float *X, const float *T, int64_t rows, int32_t epochs,
                       const int64_t *order, uint64_t shuffle_seed, double *loss_per_epoch, int32_t mem);
 
+/* Limit, in nanoseconds of wall time, of the pipeline waits of the layered
+ * tensor-core kernel (a TMA panel landing, a stage's products done) used by
+ * mlp_loss_grad, mlp_train and the layered forward pass (the paper has no
+ * counterpart; default 2e9).  A wait that runs out stops its CTA cleanly
+ * (the copies and products it issued are still waited for, up to 2 s) and
+ * the call returns MD_ETIMEOUT with the handle still usable.  0 gives up at
+ * once on any wait not already complete, which is how the timeout path is
+ * tested.  MD_EINVAL for a null handle or ns < 0. */
+OTF_API int mlp_set_wait_limit(mlp_handle *h, int64_t ns);
+
 OTF_API void mlp_free(mlp_handle *h);
 
 /* Features of nruns runs for the learned tail, host arrays: c_sigma and c_q

@@ -109,9 +109,10 @@ typedef struct {
   int32_t pair_mode;  /* MD_PAIR_VERLET or MD_PAIR_CELLS */
   double skin;        /* Verlet skin (MD_PAIR_VERLET); 0 rebuilds every step */
   int32_t max_neighbors; /* neighbour-list capacity per atom; 0 = automatic */
-  int32_t use_graph;  /* 1: md_step replays captured CUDA graphs (8 steps at a time, each step's
-                         correlator pushes on a second stream beside the next step; a one-step
-                         graph for the rest of a call); 0: direct launches */
+  int32_t use_graph;  /* 1: md_step replays CUDA graphs (8 steps at a time, each step's
+                         correlator pushes on a second stream beside the next step; one graph
+                         of 1..7 steps for the rest of a call), each captured the first time a
+                         call needs it; 0: direct launches */
   int32_t autotune;   /* 1: md_init times the pair kernel (64/128/256 threads
                          per CTA) and the list build (j-parallel at 2/4/8,
                          i-parallel and staged at 4/8 warps per CTA) on the
@@ -162,6 +163,8 @@ typedef struct {
   int32_t max_neighbors;  /* neighbour-list capacity per atom */
   int64_t atoms, cells;   /* totals over all replicas */
   int32_t build_kind;     /* 0: j-parallel list build, 1: i-parallel, 2: staged */
+  int64_t vacf_input_bytes; /* device bytes of the per-atom velocity correlator's
+                               input slots (0 when that correlator is off) */
 } md_config;
 
 /* Observables of the last completed step (Sec. 2.3). */
@@ -207,8 +210,10 @@ OTF_API int md_init_replicas(const md_params *p, const md_replica *reps, int32_t
  * correlator samples of the stress and heat flux every stress.u /
  * heatflux.u steps and of every atom's velocity every vacf.u steps
  * (Algorithm 1; with vacf.p <= 16 the velocity samples wait in device slots
- * and are applied eight at a time, and whatever waits is applied before the
- * call returns, so the correlators always hold every step taken).
+ * and are applied eight at a time; samples short of a full block stay there
+ * across calls and are applied by the next readout of the velocity
+ * correlator (corr_read, corr_raw, corr_read_rows), so a readout always
+ * holds every step taken).
  * Everything stays on the device.  Synchronises the stream at the end and
  * returns MD_ESTATE if a device check failed (the state is then
  * undefined). */
@@ -262,11 +267,11 @@ OTF_API int md_corr(md_handle *h, int32_t which, corr_handle **out);
 
 /* on = 1: the following md_step calls bracket every kernel class with CUDA
  * events and add its device time to counters; on = 0 stops that.  Enabling
- * clears the counters.  With graphs on (md_params.use_graph), whole groups of
- * 8 steps replay graphs that carry the event records, so the times are those
- * of the normal launch path (the correlator pushes then overlap the next
- * step's kernels, and their times include that sharing of the GPU);
- * the remaining steps of a call, and every step without graphs, launch
+ * clears the counters.  With graphs on (md_params.use_graph), enabling
+ * captures graphs that carry the event records (8 steps, and 1..7 steps for
+ * a call's remainder), so the times are those of the normal launch path
+ * (the correlator pushes then overlap the next step's kernels, and their
+ * times include that sharing of the GPU); without graphs every step launches
  * directly between events. */
 OTF_API int md_set_timing(md_handle *h, int32_t on);
 
@@ -337,12 +342,27 @@ OTF_API int gk_integrate(const double *t, const double *c, int64_t n, double t_c
  * Its scratch is a fixed array inside the library (partial sums for 1024
  * CTAs, about 90 KB per GPU, held until the process exits); n may be up to
  * 2^27 - 1 and larger n is rejected with MD_EINVAL.  The first call on each
- * device looks up that array's address and clears it, so make it before any
+ * device looks up that array's address and clears its completion counter on
+ * cuda_stream, ahead of its own launch, so make that first call before any
  * stream capture.  All calls on one device share the array: calls that
  * overlap on the GPU race. */
 OTF_API int md_observables_noalloc(int64_t n, double volume, const double *v, const double *epot,
                                    const double *W, const double *mass_of, double *obs,
                                    void *cuda_stream);
+
+/* Measurement utility (the paper has no counterpart): the FP32 FMA rate of
+ * the current GPU, which sets the roofline of the pair kernel.  Launches a
+ * grid that fills every SM (occupancy-limited CTAs of 256 threads), each
+ * thread running 8 independent chains of dependent FMAs for iters x 16
+ * steps: scalar fma.rn.f32 (paired = 0) or fma.rn.f32x2 on register pairs
+ * (paired = 1, two FMAs per instruction).  One warm-up launch, then reps
+ * launches timed with CUDA events on cuda_stream.  Outputs (host):
+ * flops per launch (2 per FMA), device milliseconds per launch, and the SM
+ * count.  Allocates and frees a small output buffer and synchronises the
+ * stream.  Errors: MD_EINVAL for iters or reps < 1 or a null output,
+ * MD_ECUDA for a failed CUDA call. */
+OTF_API int md_fp32_peak(int32_t paired, int64_t iters, int32_t reps, void *cuda_stream,
+                         double *flops_per_launch, double *ms_per_launch, int32_t *sm_count);
 
 /* Message of the last failed call on this thread ("" if none). */
 OTF_API const char *md_last_error(void);

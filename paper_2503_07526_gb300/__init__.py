@@ -31,6 +31,7 @@ from ._lib import (  # noqa: F401
     gk_integrate,
     gk_tail_features,
     lib,
+    fp32_peak,
     make_params,
     observables_noalloc,
 )

@@ -60,7 +60,7 @@ class md_replica(C.Structure):
 class md_config(C.Structure):
     _fields_ = [("replicas", C.c_int32), ("pair_threads", C.c_int32), ("build_warps", C.c_int32),
                 ("max_neighbors", C.c_int32), ("atoms", C.c_int64), ("cells", C.c_int64),
-                ("build_kind", C.c_int32)]
+                ("build_kind", C.c_int32), ("vacf_input_bytes", C.c_int64)]
 
 
 class md_obs(C.Structure):
@@ -118,6 +118,8 @@ def lib(build: bool = False):
         "corr_reset": [vp],
         "gk_integrate": [dp, dp, i64, C.c_double, C.c_double, dp, dp],
         "md_observables_noalloc": [i64, C.c_double, vp, vp, vp, vp, vp, vp],
+        "md_fp32_peak": [i32, i64, i32, vp, dp, dp, C.POINTER(C.c_int32)],
+        "mlp_set_wait_limit": [vp, i64],
         "mlp_create": [C.POINTER(mlp_params), vp, C.POINTER(vp)],
         "mlp_param_count": [vp, C.POINTER(C.c_int64)],
         "mlp_get_params": [vp, vp, i64, i32],
@@ -153,7 +155,7 @@ EXPORTS = ("md_init", "md_step", "md_observables", "md_get_particles", "md_scale
            "md_observables_noalloc", "md_init_replicas", "md_replica_observables", "md_replica_scale_velocities",
            "md_get_config", "md_replica_observables_all", "mlp_create", "mlp_param_count", "mlp_get_params",
            "mlp_set_params", "mlp_set_scaler", "mlp_fit_scaler", "mlp_forward", "mlp_loss_grad", "mlp_adam_step",
-           "mlp_train", "mlp_free", "gk_tail_features", "corr_read_rows")
+           "mlp_train", "mlp_free", "gk_tail_features", "corr_read_rows", "md_fp32_peak", "mlp_set_wait_limit")
 
 
 def _check(rc):
@@ -382,7 +384,8 @@ class System:
         _check(lib().md_get_config(self._h, C.byref(c)))
         return dict(replicas=c.replicas, pair_threads=c.pair_threads, build_warps=c.build_warps,
                     build_kind=c.build_kind,
-                    max_neighbors=c.max_neighbors, atoms=c.atoms, cells=c.cells)
+                    max_neighbors=c.max_neighbors, atoms=c.atoms, cells=c.cells,
+                    vacf_input_bytes=c.vacf_input_bytes)
 
     def step(self, nsteps):
         _check(lib().md_step(self._h, int(nsteps)))
@@ -451,6 +454,15 @@ def gk_integrate(t, c, t_cut=float("inf"), prefactor=1.0):
     _check(lib().gk_integrate(t.ctypes.data_as(dp), c.ctypes.data_as(dp), t.size, float(t_cut), float(prefactor),
                               C.byref(out), run.ctypes.data_as(dp)))
     return out.value, run
+
+
+def fp32_peak(paired=False, iters=2048, reps=5, stream=None):
+    """md_fp32_peak: (flops per launch, device ms per launch, SM count) of
+    the FMA-chain kernel (scalar or paired f32x2 FMAs)."""
+    fl, ms, sms = C.c_double(0.0), C.c_double(0.0), C.c_int32(0)
+    _check(lib().md_fp32_peak(int(bool(paired)), int(iters), int(reps), _stream_ptr(stream), C.byref(fl),
+                              C.byref(ms), C.byref(sms)))
+    return fl.value, ms.value, sms.value
 
 
 def observables_noalloc(volume, v, epot, W, mass_of, obs, stream=None):
@@ -531,6 +543,9 @@ class MLP:
             py = Y.data_ptr()
         _check(lib().mlp_forward(self._h, px, rows, py, mem))
         return Y
+
+    def set_wait_limit(self, ns):
+        _check(lib().mlp_set_wait_limit(self._h, int(ns)))
 
     def loss_grad(self, X, T):
         px, mem, kx = _ptr(X, F32)

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libotfmd.so")
-SOURCES = ["capi.cu", "corr.cu", "md.cu", "obs_noalloc.cu", "mlp.cu", "spme.cu"]
+SOURCES = ["capi.cu", "corr.cu", "md.cu", "obs_noalloc.cu", "mlp.cu", "spme.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "-I" + INCLUDE, "-I" + CSRC, "--expt-relaxed-constexpr"]

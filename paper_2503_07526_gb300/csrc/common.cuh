@@ -20,6 +20,7 @@ enum : unsigned {
   ERR_NONFINITE = 1u,      // a coordinate or velocity became NaN / Inf
   ERR_NBR_OVERFLOW = 2u,   // an atom has more neighbours than the list holds
   ERR_BAD_TYPE = 4u,       // an atom type outside [0, ntypes)
+  ERR_PUSH_BACKLOG = 8u,   // more velocity pushes waiting than one blocked pass applies
 };
 
 #define OTF_CUDA(call)                                                                       \
@@ -132,6 +133,35 @@ __device__ __forceinline__ dfloat df_mul_f(dfloat a, float b) {
   e = fmaf(a.l, b, e);
   return df_fast_two_sum(p, e);
 }
+// Products left unnormalised (p + e, |e| << |p|) and a compensated
+// accumulator for them: the running sum s carries the rounded total and c
+// the sum of every rounding error (TwoSum) and low part, so the value
+// s + c keeps about 48 significant bits over a few dozen terms (the
+// cascaded summation of Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005).
+__device__ __forceinline__ dfloat df_prod(dfloat a, dfloat b) {  // unnormalised a * b
+  const float p = a.h * b.h;
+  return dfloat{p, fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)))};
+}
+__device__ __forceinline__ dfloat df_prod_f(float a, dfloat b) {  // unnormalised a * b
+  const float p = a * b.h;
+  return dfloat{p, fmaf(a, b.l, fmaf(a, b.h, -p))};
+}
+struct dfacc {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(dfloat x) {
+    const dfloat t = df_two_sum(s, x.h);
+    s = t.h;
+    c += t.l + x.l;
+  }
+  __device__ __forceinline__ void add(float x) {
+    const dfloat t = df_two_sum(s, x);
+    s = t.h;
+    c += t.l;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // Host / FP64 conversions (used at set-up and output only).
 __host__ __device__ __forceinline__ dfloat df_from_double(double x) {
   const float h = (float)x;

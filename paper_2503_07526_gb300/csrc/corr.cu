@@ -267,7 +267,11 @@ __global__ void __launch_bounds__(kPushThreads, 2)
   const int64_t t = (bi.u > 0 && st > 0) ? st / bi.u : 0;
   const int64_t done = *bi.d_done;
   const int nnew = (int)(t - done);
-  if (nnew <= 0 || nnew > bi.block || (!bi.flush && nnew < bi.block)) return;
+  if (nnew > bi.block) {  // a pass was lost: report it instead of dropping pushes silently
+    if (bi.d_err && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) atomicOr(bi.d_err, ERR_PUSH_BACKLOG);
+    return;
+  }
+  if (nnew <= 0 || (!bi.flush && nnew < bi.block)) return;
   __shared__ double red[kPushWarps][64];
   const int g = blockIdx.y, cx = blockIdx.x;
   const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x / kWarp;
@@ -347,7 +351,11 @@ __global__ void __launch_bounds__(kPushThreads) k_push_higher(CorrDev c, BlockId
   const int64_t t = (bi.u > 0 && st > 0) ? st / bi.u : 0;
   const int64_t done = *bi.d_done;
   const int nnew = (int)(t - done);
-  if (nnew <= 0 || nnew > bi.block || (!bi.flush && nnew < bi.block)) return;
+  if (nnew > bi.block) {  // a pass was lost: report it instead of dropping pushes silently
+    if (bi.d_err && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) atomicOr(bi.d_err, ERR_PUSH_BACKLOG);
+    return;
+  }
+  if (nnew <= 0 || (!bi.flush && nnew < bi.block)) return;
   __shared__ double red[kPushWarps][64];
   const int g = blockIdx.y, cx = blockIdx.x;
   const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x / kWarp;
@@ -583,6 +591,10 @@ int Correlator::launch_push_block(const void *x, bool input_fp32, BlockIdx bi, c
 }
 
 int Correlator::fetch(double *vals_host) {
+  if (before_read) {
+    const int rc = before_read(read_ctx);
+    if (rc) return rc;
+  }
   const size_t n = (size_t)dev.ng * prm.b * prm.p;
   const double *src = dev.vals;
   if (grouped) {

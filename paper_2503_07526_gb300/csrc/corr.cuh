@@ -56,6 +56,7 @@ struct BlockIdx {
   unsigned *d_ctas;  // CTAs of the current pass that have finished (returns to 0)
   int block;         // pushes per pass: min(kPushBlock, p - m + 1)
   int flush;         // 1: apply a partial block too
+  unsigned *d_err;   // device error word (ERR_PUSH_BACKLOG), may be null
 };
 
 __device__ __forceinline__ bool resolve_push(const PushIdx &pi, int64_t *t) {
@@ -122,6 +123,8 @@ struct Correlator {
   const int64_t *host_steps = nullptr;  // MD-owned: host mirror of the step count
   const int64_t *host_base = nullptr;   // MD-owned: step of the last reset
   int64_t u = 1;           // MD-owned: steps per push
+  int (*before_read)(void *) = nullptr;  // MD-owned: applies waiting pushes before a readout
+  void *read_ctx = nullptr;
   double *d_in = nullptr;  // staging for host pushes, [2][ns]
   double *d_fold = nullptr;// [ng][b][p] folded lag sums
 

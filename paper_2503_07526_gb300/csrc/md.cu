@@ -87,12 +87,13 @@ struct Rep {
 struct Sys {
   int64_t n, ncell, maxchunks;  // totals over all replicas
   int nrep, ntypes, maxnb, always_rebuild, vacf_u;
-  int vacf_slots;  // velocity input slots: kPushBlock (blocked pushes) or 1 (one push per step)
+  int vacf_slots;  // velocity input slots: kPushBlock (blocked pushes), 1 (one push per step) or 0 (off)
   double dt, lim2;
   double invm[8], mass[8];
   double charge[8];            // per type (MD_POT_BUCK_EWALD); the pair records carry it in w
   int flux_species;            // type whose partial momentum density is observed
   float hdtm_h[8], hdtm_l[8];  // mixed form: dt / (2 m) per type, double-float
+  float mass_h[8], mass_l[8];  // mixed form: m per type, double-float
   float dt_h, dt_l;
   const Rep *rep;            // [nrep]
   const int *rep_of_atom;    // [n] (sorted order = input order of replicas)
@@ -789,9 +790,12 @@ __global__ void __launch_bounds__(kMaxPairThreads) k_pair_list(Sys d, LJ<TF> lj)
 // Second half kick, then the per-step observables of every replica
 // (Sec. 2.3): K, U, V sigma_ab = sum m v_a v_b + sum W_i,ab,
 // V q = sum (E_i v_i + W_i v_i).  Each CTA works on one replica (rep_of_block)
-// and strides over that replica's atoms.  Per-thread partial sums in A
-// (float in the mixed form, from the FP32 high words of the velocities;
-// double in FP64), the CTA and replica tree in FP64 (fixed order:
+// and strides over that replica's atoms.  Per-thread partial sums: FP64 in
+// the FP64 form; in the mixed form every term is formed in double-float
+// arithmetic from the double-float velocity, the double-float mass and the
+// FP32 per-particle energy and virial, and summed by a compensated FP32
+// accumulator (dfacc), so the partials carry ~48 bits like FP64 sums of
+// the same inputs.  The CTA and replica tree is FP64 (fixed order:
 // deterministic).  The last CTA of a replica writes its observables; the
 // last replica to finish advances the step counter.  When a velocity sample
 // is due, velocities are also scattered to atom-id order.  The stress,
@@ -817,27 +821,101 @@ __global__ void __launch_bounds__(kThreads)
   const int r = d.rep_of_block[blockIdx.x];
   const Rep &R = d.rep[r];
   const int lb = (int)(blockIdx.x - R.block0);
-  A acc[kNRed];
+  double part[kNRed];  // this thread's partial sums
+  if constexpr (std::is_same<TF, float>::value) {
+    dfacc acc[kNRed];
+    for (int64_t i = R.atom0 + (int64_t)lb * blockDim.x + threadIdx.x; i < R.atom1;
+         i += (int64_t)R.nblk * blockDim.x) {
+      // every load of the atom first (the stores below could alias them)
+      const int t = type_of(d, i);
+      const float ep = Ep[i];
+      float w[6];
 #pragma unroll
-  for (int q = 0; q < kNRed; ++q) acc[q] = A(0);
-  for (int64_t i = R.atom0 + (int64_t)lb * blockDim.x + threadIdx.x; i < R.atom1;
-       i += (int64_t)R.nblk * blockDim.x) {
-    // every load of the atom first (the stores below could alias them for
-    // the compiler), so they are all in flight together
-    const int t = type_of(d, i);
-    const A ep = (A)Ep[i];
-    A w[6];
+      for (int q = 0; q < 6; ++q) w[q] = Wp[q * n + i];
+      float f[3], vh[3], vl[3];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) w[q] = (A)Wp[q * n + i];
-    TF f[3];
+      for (int a = 0; a < 3; ++a) {
+        f[a] = KICK ? F[a * n + i] : 0.f;
+        vh[a] = d.vh[a * n + i];
+        vl[a] = d.vl[a * n + i];
+      }
+      const int id = vacf_due ? d.id[i] : 0;
+      const dfloat h{d.hdtm_h[t], d.hdtm_l[t]};
+      dfloat v[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) f[a] = KICK ? F[a * n + i] : TF(0);
-    const int id = vacf_due ? d.id[i] : 0;
-    A v[3];
-    if constexpr (std::is_same<TF, double>::value) {
+      for (int a = 0; a < 3; ++a) {
+        v[a] = dfloat{vh[a], vl[a]};
+        if (KICK) {
+          v[a] = df_add(v[a], df_mul_f(h, f[a]));
+          d.vh[a * n + i] = v[a].h;
+          d.vl[a * n + i] = v[a].l;
+        }
+      }
+      if (vacf_due) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) vb[a * n + id] = v[a].h;
+      }
+      const dfloat m{d.mass_h[t], d.mass_l[t]};
+      dfloat mv[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) mv[a] = df_prod(m, v[a]);
+      // m v_a v_b in the order xx yy zz xy xz yz of sigma and W
+      const dfloat mvv[6] = {df_prod(mv[0], v[0]), df_prod(mv[1], v[1]), df_prod(mv[2], v[2]),
+                             df_prod(mv[0], v[1]), df_prod(mv[0], v[2]), df_prod(mv[1], v[2])};
+      // E_i = m v^2 / 2 + epot_i, kept as an unnormalised pair
+      dfloat E;
+      {
+        const dfloat s1 = df_two_sum(mvv[0].h, mvv[1].h);
+        const dfloat s2 = df_two_sum(s1.h, mvv[2].h);
+        const dfloat s3 = df_two_sum(0.5f * s2.h, ep);
+        E = dfloat{s3.h, s3.l + 0.5f * (s1.l + s2.l + mvv[0].l + mvv[1].l + mvv[2].l)};
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) acc[0].add(mvv[a]);  // 2K (halved below)
+      acc[1].add(ep);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        acc[2 + q].add(mvv[q]);
+        acc[2 + q].add(w[q]);
+      }
+      // (W_i v_i)_a with W symmetric: rows (xx xy xz), (xy yy yz), (xz yz zz)
+      const int row[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        acc[8 + a].add(df_prod(E, v[a]));
+#pragma unroll
+        for (int b = 0; b < 3; ++b) acc[8 + a].add(df_prod_f(w[row[a][b]], v[b]));
+      }
+      if (t == d.flux_species) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[11 + a].add(mv[a]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kNRed; ++q) part[q] = acc[q].value();
+    part[0] *= 0.5;
+  } else {  // FP64 form
+    A acc[kNRed];
+#pragma unroll
+    for (int q = 0; q < kNRed; ++q) acc[q] = A(0);
+    for (int64_t i = R.atom0 + (int64_t)lb * blockDim.x + threadIdx.x; i < R.atom1;
+         i += (int64_t)R.nblk * blockDim.x) {
+      // every load of the atom first (the stores below could alias them for
+      // the compiler), so they are all in flight together
+      const int t = type_of(d, i);
+      const A ep = (A)Ep[i];
+      A w[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) w[q] = (A)Wp[q * n + i];
+      TF f[3];
       double vv[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) vv[a] = d.v[a * n + i];
+      for (int a = 0; a < 3; ++a) {
+        f[a] = KICK ? F[a * n + i] : TF(0);
+        vv[a] = d.v[a * n + i];
+      }
+      const int id = vacf_due ? d.id[i] : 0;
+      A v[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         double va = vv[a];
@@ -847,54 +925,38 @@ __global__ void __launch_bounds__(kThreads)
         }
         v[a] = (A)va;
       }
-    } else {
-      float vh[3], vl[3];
+      if (vacf_due) {
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        vh[a] = d.vh[a * n + i];
-        vl[a] = d.vl[a * n + i];
+        for (int a = 0; a < 3; ++a) vb[a * n + id] = (TF)v[a];
       }
-      const dfloat h{d.hdtm_h[t], d.hdtm_l[t]};
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        dfloat va{vh[a], vl[a]};
-        if (KICK) {
-          va = df_add(va, df_mul_f(h, (float)f[a]));
-          d.vh[a * n + i] = va.h;
-          d.vl[a * n + i] = va.l;
-        }
-        v[a] = (A)va.h;
-      }
+      const A m = (A)d.mass[t];
+      const A vx = v[0], vy = v[1], vz = v[2];
+      const A ke = A(0.5) * m * (vx * vx + vy * vy + vz * vz);
+      const A E = ke + ep;
+      acc[0] += ke;
+      acc[1] += ep;
+      acc[2] += m * vx * vx + w[0];
+      acc[3] += m * vy * vy + w[1];
+      acc[4] += m * vz * vz + w[2];
+      acc[5] += m * vx * vy + w[3];
+      acc[6] += m * vx * vz + w[4];
+      acc[7] += m * vy * vz + w[5];
+      acc[8] += E * vx + w[0] * vx + w[3] * vy + w[4] * vz;
+      acc[9] += E * vy + w[3] * vx + w[1] * vy + w[5] * vz;
+      acc[10] += E * vz + w[4] * vx + w[5] * vy + w[2] * vz;
+      const A sel = t == d.flux_species ? m : A(0);
+      acc[11] += sel * vx;
+      acc[12] += sel * vy;
+      acc[13] += sel * vz;
     }
-    if (vacf_due) {
 #pragma unroll
-      for (int a = 0; a < 3; ++a) vb[a * n + id] = (TF)v[a];
-    }
-    const A m = (A)d.mass[t];
-    const A vx = v[0], vy = v[1], vz = v[2];
-    const A ke = A(0.5) * m * (vx * vx + vy * vy + vz * vz);
-    const A E = ke + ep;
-    acc[0] += ke;
-    acc[1] += ep;
-    acc[2] += m * vx * vx + w[0];
-    acc[3] += m * vy * vy + w[1];
-    acc[4] += m * vz * vz + w[2];
-    acc[5] += m * vx * vy + w[3];
-    acc[6] += m * vx * vz + w[4];
-    acc[7] += m * vy * vz + w[5];
-    acc[8] += E * vx + w[0] * vx + w[3] * vy + w[4] * vz;
-    acc[9] += E * vy + w[3] * vx + w[1] * vy + w[5] * vz;
-    acc[10] += E * vz + w[4] * vx + w[5] * vy + w[2] * vz;
-    const A sel = t == d.flux_species ? m : A(0);
-    acc[11] += sel * vx;
-    acc[12] += sel * vy;
-    acc[13] += sel * vz;
+    for (int q = 0; q < kNRed; ++q) part[q] = (double)acc[q];
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < kNRed; ++q) {
-    const A sm = warp_sum(acc[q]);
-    if (lane == 0) red[warp][q] = (double)sm;
+    const double sm = warp_sum(part[q]);
+    if (lane == 0) red[warp][q] = sm;
   }
   __syncthreads();
   if (threadIdx.x < kNRed) {
@@ -1296,18 +1358,21 @@ struct md_handle_s {
   Sys d{};
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t graph = nullptr;   // one step
-  cudaGraphExec_t graphN = nullptr;  // kGraphSteps steps, each velocity push overlapping the next step
+  // graphR[r]: r steps (1..kGraphSteps) in one graph, each step's correlator
+  // pushes overlapping the next step; built on first use
+  cudaGraphExec_t graphR[kGraphSteps + 1] = {};
   cudaStream_t side = nullptr;       // the correlator pushes run here, beside the next step
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool vacf_pending = false;         // correlator pushes on `side` the next reduction must wait for
-  // timed graphs (md_set_timing with graphs): two instances of the
-  // kGraphSteps-step graph, each with its own event records inside, replayed
-  // alternately so that one is read while the other runs
-  cudaGraphExec_t graphT[2] = {nullptr, nullptr};
-  std::vector<cudaEvent_t> tev[2];
-  std::vector<int> tev_class[2];
-  bool tev_pending[2] = {false, false};
+  // timed graphs (md_set_timing with graphs), each with its own event
+  // records inside: sets 0 and 1 are two instances of the kGraphSteps-step
+  // graph, replayed alternately so that one is read while the other runs;
+  // set 1 + r holds the r-step graph (r < kGraphSteps) of a call's remainder
+  static constexpr int kTimedSets = kGraphSteps + 1;
+  cudaGraphExec_t graphT[kTimedSets] = {};
+  std::vector<cudaEvent_t> tev[kTimedSets];
+  std::vector<int> tev_class[kTimedSets];
+  bool tev_pending[kTimedSets] = {};
   int tset = -1;                     // the set KTimer records into while capturing (-1: eager pool)
   bool fp64 = true;
   int nrep = 1;
@@ -1494,7 +1559,7 @@ bool scalar_banks_on(const md_handle *h) { return h->bank_on[0] || h->bank_on[1]
 int launch_vacf_block(md_handle *h, cudaStream_t s, bool flush) {
   const int block = std::min(kPushBlock, h->prm.vacf.p - h->prm.vacf.m + 1);  // see BlockIdx
   const BlockIdx bi{&h->d.st->step, &h->d.st->corr_base, h->prm.vacf.u, &h->d.st->vacf_done,
-                    &h->d.st->vacf_ctas, std::max(block, 1), flush ? 1 : 0};
+                    &h->d.st->vacf_ctas, std::max(block, 1), flush ? 1 : 0, h->d.err};
   return h->banks[2].c.launch_push_block(h->d.vbuf, !h->fp64, bi, s);
 }
 
@@ -1585,9 +1650,10 @@ int check_device(md_handle *h) {
   OTF_CUDA(cudaStreamSynchronize(h->stream));
   const unsigned e = *h->h_err;
   if (e) {
-    set_error("device check failed (flags 0x%x):%s%s%s", e, (e & ERR_NONFINITE) ? " non-finite coordinates;" : "",
+    set_error("device check failed (flags 0x%x):%s%s%s%s", e, (e & ERR_NONFINITE) ? " non-finite coordinates;" : "",
               (e & ERR_NBR_OVERFLOW) ? " neighbour list over capacity (raise max_neighbors);" : "",
-              (e & ERR_BAD_TYPE) ? " atom type out of range;" : "");
+              (e & ERR_BAD_TYPE) ? " atom type out of range;" : "",
+              (e & ERR_PUSH_BACKLOG) ? " velocity-correlator pushes left unapplied;" : "");
     return MD_ESTATE;
   }
   return MD_OK;
@@ -1621,20 +1687,45 @@ int capture_steps(md_handle *h, int steps, cudaGraphExec_t *out) {
   return MD_OK;
 }
 
-int build_graph(md_handle *h) {
-  int rc = capture_steps(h, 1, &h->graph);
-  if (!rc && (h->bank_on[2] || scalar_banks_on(h))) rc = capture_steps(h, kGraphSteps, &h->graphN);
-  return rc;
+// The r-step graph (captured on first use).
+int graph_of(md_handle *h, int r, cudaGraphExec_t *out) {
+  if (!h->graphR[r]) {
+    const int rc = capture_steps(h, r, &h->graphR[r]);
+    if (rc) return rc;
+  }
+  *out = h->graphR[r];
+  return MD_OK;
 }
 
-int build_timed_graphs(md_handle *h) {
-  for (int k = 0; k < 2; ++k) {
+// Timed graph set k (see md_handle::graphT), captured on first use.
+int timed_graph_of(md_handle *h, int k, cudaGraphExec_t *out) {
+  if (!h->graphT[k]) {
     h->tset = k;
-    const int rc = capture_steps(h, kGraphSteps, &h->graphT[k]);
+    const int rc = capture_steps(h, k < 2 ? kGraphSteps : k - 1, &h->graphT[k]);
     h->tset = -1;
     if (rc) return rc;
   }
+  *out = h->graphT[k];
   return MD_OK;
+}
+
+int launch_graph(cudaGraphExec_t g, cudaStream_t s) {
+  const cudaError_t e = cudaGraphLaunch(g, s);
+  if (e != cudaSuccess) {
+    set_error("cudaGraphLaunch failed: %s", cudaGetErrorString(e));
+    return MD_ECUDA;
+  }
+  return MD_OK;
+}
+
+// The velocity pushes still waiting in their input slots (fewer than a
+// block), applied on the system's stream.  Runs before every readout of the
+// velocity correlator, so a read always sees every step taken, while md_step
+// itself leaves a partial block waiting for the next call.
+int flush_vacf(void *ctx) {
+  md_handle *h = static_cast<md_handle *>(ctx);
+  if (!h->bank_on[2] || h->d.vacf_slots <= 1) return MD_OK;
+  return launch_vacf_block(h, h->stream, true);
 }
 
 // Waits for the last replay of timed graph k and adds its kernel times to
@@ -1788,9 +1879,9 @@ int validate_replicas(const md_params *p, const md_replica *reps, int count, int
 void release(md_handle *h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
-  if (h->graph) cudaGraphExecDestroy(h->graph);
-  if (h->graphN) cudaGraphExecDestroy(h->graphN);
-  for (int k = 0; k < 2; ++k) {
+  for (cudaGraphExec_t g : h->graphR)
+    if (g) cudaGraphExecDestroy(g);
+  for (int k = 0; k < md_handle::kTimedSets; ++k) {
     if (h->graphT[k]) cudaGraphExecDestroy(h->graphT[k]);
     for (cudaEvent_t e : h->tev[k]) cudaEventDestroy(e);
   }
@@ -1928,13 +2019,17 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   }
   d.maxnb = maxnb;
   d.vacf_u = p->vacf.u;
-  // blocked velocity pushes keep the p - 1 <= 15 most recent samples in registers
-  d.vacf_slots = (p->vacf.b > 0 && p->vacf.p <= 16) ? kPushBlock : 1;
+  // blocked velocity pushes keep the p - 1 <= 15 most recent samples in
+  // registers; no input slot at all when the velocity correlator is off
+  d.vacf_slots = p->vacf.u <= 0 ? 0 : (p->vacf.p <= 16 ? kPushBlock : 1);
   d.maxchunks = (n + 31) / 32;  // 32-atom chunks of the neighbour lists
   for (int t = 0; t < 8; ++t) {
     const dfloat hh = df_from_double(0.5 * p->dt * d.invm[t]);
     d.hdtm_h[t] = hh.h;
     d.hdtm_l[t] = hh.l;
+    const dfloat mm = df_from_double(d.mass[t]);
+    d.mass_h[t] = mm.h;
+    d.mass_l[t] = mm.l;
   }
   {
     const dfloat dtf = df_from_double(p->dt);
@@ -1960,7 +2055,7 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   OTF_CUDA(cudaMalloc(&d.W, 6 * n * tf));
   OTF_CUDA(cudaMalloc(&d.rel, n * v4));
   OTF_CUDA(cudaMalloc(&d.relb, n * v4));
-  OTF_CUDA(cudaMalloc(&d.vbuf, (size_t)d.vacf_slots * 3 * n * tf));
+  if (d.vacf_slots > 0) OTF_CUDA(cudaMalloc(&d.vbuf, (size_t)d.vacf_slots * 3 * n * tf));
   OTF_CUDA(cudaMalloc(&d.id, n * sizeof(int)));
   OTF_CUDA(cudaMalloc(&d.type, n * sizeof(int)));
   OTF_CUDA(cudaMalloc(&d.cpk, n * sizeof(int)));
@@ -2016,7 +2111,7 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   OTF_CUDA(cudaMemsetAsync(d.st, 0, sizeof(StepDev), st));
   OTF_CUDA(cudaMemsetAsync(d.err, 0, sizeof(unsigned), st));
   OTF_CUDA(cudaMemsetAsync(d.F, 0, 3 * n * tf, st));
-  OTF_CUDA(cudaMemsetAsync(d.vbuf, 0, (size_t)d.vacf_slots * 3 * n * tf, st));
+  if (d.vacf_slots > 0) OTF_CUDA(cudaMemsetAsync(d.vbuf, 0, (size_t)d.vacf_slots * 3 * n * tf, st));
   OTF_CUDA(cudaMemsetAsync(d.rebuild, 1, (count + 1) * sizeof(int), st));  // every flag set (nonzero)
   // inputs, replica after replica, component-major within the whole system:
   // FP64 form straight into the state; mixed form through the scratch,
@@ -2058,6 +2153,10 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
     if (rc) return rc;
     c.borrowed = true;
     c.host_steps = &h->steps_done;
+    if (k == 2) {
+      c.before_read = flush_vacf;
+      c.read_ctx = h;
+    }
     c.host_base = &h->corr_base;
     c.u = specs[k]->u;
   }
@@ -2081,7 +2180,7 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
     rc = h->fp64 ? autotune<double>(h) : autotune<float>(h);
     if (rc) return rc;
     if ((rc = refresh_obs(h))) return rc;
-    return check_device(h);
+    if ((rc = check_device(h))) return rc;
   }
   return MD_OK;
 }
@@ -2183,43 +2282,32 @@ int md_step(md_handle *h, int64_t nsteps) {
     if (!rc) rc = join_vacf(h, h->stream);
   } else if (h->timing) {
     // the production graphs with event records inside; set k is read (which
-    // waits for its previous replay) while set k ^ 1 is queued behind it
-    if (!h->graphT[0] && (rc = build_timed_graphs(h))) return rc;
+    // waits for its previous replay) while set k ^ 1 is queued behind it;
+    // the remainder of the call is one timed graph of that many steps
     int64_t s = 0;
-    for (int k = 0; s + kGraphSteps <= nsteps; s += kGraphSteps, k ^= 1) {
-      if ((rc = read_timed(h, k))) return rc;
-      cudaError_t e = cudaGraphLaunch(h->graphT[k], h->stream);
-      if (e != cudaSuccess) {
-        set_error("cudaGraphLaunch failed: %s", cudaGetErrorString(e));
-        return MD_ECUDA;
-      }
+    cudaGraphExec_t gx = nullptr;
+    for (int k = 0; s + kGraphSteps <= nsteps && !rc; s += kGraphSteps, k ^= 1) {
+      if ((rc = read_timed(h, k)) || (rc = timed_graph_of(h, k, &gx)) || (rc = launch_graph(gx, h->stream))) break;
       h->tev_pending[k] = true;
     }
-    for (int k = 0; k < 2 && !rc; ++k) rc = read_timed(h, k);
-    // the remaining steps one by one, timed by the eager event pool
-    for (; s < nsteps && !rc; ++s) rc = step_once(h, h->stream, false);
+    const int rem = (int)(nsteps - s);
+    if (!rc && rem > 0 && !(rc = read_timed(h, 1 + rem)) && !(rc = timed_graph_of(h, 1 + rem, &gx)) &&
+        !(rc = launch_graph(gx, h->stream)))
+      h->tev_pending[1 + rem] = true;
+    for (int k = 0; k < md_handle::kTimedSets && !rc; ++k) rc = read_timed(h, k);
   } else {
-    if (!h->graph && (rc = build_graph(h))) return rc;
+    // whole kGraphSteps-step graphs, then one graph for the remainder
     int64_t s = 0;
-    for (; h->graphN && s + kGraphSteps <= nsteps; s += kGraphSteps) {
-      cudaError_t e = cudaGraphLaunch(h->graphN, h->stream);
-      if (e != cudaSuccess) {
-        set_error("cudaGraphLaunch failed: %s", cudaGetErrorString(e));
-        return MD_ECUDA;
-      }
-    }
-    for (; s < nsteps; ++s) {
-      cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
-      if (e != cudaSuccess) {
-        set_error("cudaGraphLaunch failed: %s", cudaGetErrorString(e));
-        return MD_ECUDA;
-      }
-    }
+    cudaGraphExec_t gx = nullptr;
+    for (; s + kGraphSteps <= nsteps && !rc; s += kGraphSteps)
+      if (!(rc = graph_of(h, kGraphSteps, &gx))) rc = launch_graph(gx, h->stream);
+    const int rem = (int)(nsteps - s);
+    if (!rc && rem > 0 && !(rc = graph_of(h, rem, &gx))) rc = launch_graph(gx, h->stream);
   }
   if (rc) return rc;
-  // pushes still waiting for a full block are applied before the call
-  // returns, so the correlators always hold every step taken
-  if (h->bank_on[2] && h->d.vacf_slots > 1 && (rc = launch_vacf_block(h, h->stream, true))) return rc;
+  // velocity pushes short of a full block stay in their input slots; they
+  // are applied by the next call's passes or before the next readout
+  // (flush_vacf)
   h->steps_done += nsteps;
   rc = check_device(h);
   if (h->timing && !rc) {
@@ -2375,10 +2463,12 @@ int md_get_config(md_handle *h, md_config *out) {
   out->pair_threads = h->pair_threads;
   out->build_warps = h->build_warps;
   out->build_kind = h->build_kind;
+  out->vacf_input_bytes = (int64_t)h->d.vacf_slots * 3 * h->d.n * (h->fp64 ? sizeof(double) : sizeof(float));
   return MD_OK;
 }
 
 int md_set_timing(md_handle *h, int32_t on) {
+  clear_error();
   if (!h) return MD_EINVAL;
   h->timing = on != 0;
   for (int k = 0; k < MD_NKCLASS; ++k) {
@@ -2386,6 +2476,13 @@ int md_set_timing(md_handle *h, int32_t on) {
     h->klaunch[k] = 0;
   }
   h->ev_used = 0;
+  if (h->timing && h->prm.use_graph) {  // the timed graphs, captured before any timed call
+    cudaGraphExec_t g = nullptr;
+    for (int k = 0; k < md_handle::kTimedSets; ++k) {
+      const int rc = timed_graph_of(h, k, &g);
+      if (rc) return rc;
+    }
+  }
   return MD_OK;
 }
 

@@ -67,16 +67,19 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 // Waits for the phase with the given parity to complete; gives up (false)
-// after kWaitNs.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// after limit_ns of wall time (at once if the phase is not complete and the
+// limit is 0).
+__device__ bool mbar_wait_for(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_test(bar, parity)) return true;
+  if (limit_ns == 0) return false;
   const uint64_t t0 = global_timer();
   for (;;) {
     if (mbar_test(bar, parity)) return true;
-    if (global_timer() - t0 > kWaitNs) return false;
+    if (global_timer() - t0 > limit_ns) return false;
     __nanosleep(64);
   }
 }
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity) { return mbar_wait_for(bar, parity, kWaitNs); }
 // 2-D tiled TMA load of box {64 columns, rows} at (x = column, y = row).
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
   asm volatile(
@@ -163,12 +166,15 @@ __host__ __device__ constexpr size_t gemm_smem_need(int N) {
 
 // One CTA per 128-row tile of D.  Thread 0 issues the TMA loads and the MMAs
 // (two panels in flight); all four warps then read their 32 TMEM lanes and
-// run the epilogue.  K must be a multiple of 16, N a multiple of 16 in
+// run the epilogue.  The pipeline waits (a panel landing, a stage's products
+// done) give up after wait_ns; the CTA then stops issuing, lets the copies
+// it issued land and its products finish (waits of kWaitNs), flags err and
+// skips the epilogue, so a stalled pipeline ends as an error status.  K must be a multiple of 16, N a multiple of 16 in
 // [16, 256]; rows and columns of A / B past the tensors' ends read as zero.
 __global__ void __launch_bounds__(kThreads) k_gemm_tc(const __grid_constant__ CUtensorMap ta,
                                                       const __grid_constant__ CUtensorMap tb, int K, int N,
                                                       int a_row0, int a_k0, int b_row0, int b_k0, Epi e,
-                                                      unsigned *err) {
+                                                      unsigned *err, uint64_t wait_ns) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const uint32_t a_bytes = kBM * 128, b_bytes = (uint32_t)N * 128;
@@ -209,7 +215,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc(const __grid_constant__ CU
     for (int p = 0; p < np; ++p) {
       const int s = p % kStages;
       const uint32_t ph = (uint32_t)(p / kStages) & 1u;
-      if (!mbar_wait(smem_u32(&bars[s]), ph)) {
+      if (!mbar_wait_for(smem_u32(&bars[s]), ph, wait_ns)) {
         ok = false;
         break;
       }
@@ -221,7 +227,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc(const __grid_constant__ CU
         mma_bf16(tmem, sw128_desc(a0 + 32u * j), sw128_desc(b0 + 32u * j), idesc, (p | j) != 0);
       mma_commit(smem_u32(&bars[kStages + s]));
       if (p + kStages < np) {
-        if (!mbar_wait(smem_u32(&bars[kStages + s]), ph)) {
+        if (!mbar_wait_for(smem_u32(&bars[kStages + s]), ph, wait_ns)) {
           ok = false;
           break;
         }
@@ -874,7 +880,7 @@ void mat_free(Mat &M) {
 }
 
 int launch_gemm(cudaStream_t st, const Mat &A, int a_row0, int a_k0, const Mat &B, int b_row0, int b_k0, int64_t M,
-                int N, int K, const Epi &e, unsigned *err) {
+                int N, int K, const Epi &e, unsigned *err, uint64_t wait_ns) {
   if (N % 16 || N < 16 || N > 256 || K % 16 || K < 16) {
     set_error("k_gemm_tc: N = %d, K = %d not supported", N, K);
     return MD_EINVAL;
@@ -889,7 +895,7 @@ int launch_gemm(cudaStream_t st, const Mat &A, int a_row0, int a_k0, const Mat &
   });
   OTF_CUDA(attr_rc);
   const int grid = ceil_div(M, kBM);
-  k_gemm_tc<<<grid, kThreads, smem, st>>>(A.map, B.map, K, N, a_row0, a_k0, b_row0, b_k0, e, err);
+  k_gemm_tc<<<grid, kThreads, smem, st>>>(A.map, B.map, K, N, a_row0, a_k0, b_row0, b_k0, e, err, wait_ns);
   OTF_LAUNCH_CHECK();
   return MD_OK;
 }
@@ -912,6 +918,7 @@ using namespace otf::tc;
 
 struct mlp_handle_s {
   cudaStream_t st = nullptr;
+  uint64_t wait_ns = kWaitNs;  // limit of the tensor-core pipeline waits (mlp_set_wait_limit)
   mlp_params p{};
   int L = 0;          // layers = depth + 1
   int k_in = 0;       // padded input width
@@ -1042,7 +1049,7 @@ int forward(mlp_handle *h, const Mat &X, int row0, int64_t rows, Mat *Hs, int nH
         e.post_shift = h->ymean;
       }
     }
-    int rc = launch_gemm(h->st, A, l == 0 ? row0 : 0, 0, Ly.wb, 0, 0, rows, Ly.out_p, Ly.in_k, e, h->err);
+    int rc = launch_gemm(h->st, A, l == 0 ? row0 : 0, 0, Ly.wb, 0, 0, rows, Ly.out_p, Ly.in_k, e, h->err, h->wait_ns);
     if (rc) return rc;
   }
   return MD_OK;
@@ -1067,7 +1074,7 @@ int train_step(mlp_handle *h, const Mat &X, const Mat &Xt, int row0, const float
     e.m_rows = Ly.in;
     e.out_ft = h->g + Ly.w_off;
     e.ld_ft = Ly.in_k;
-    rc = launch_gemm(h->st, h->Ht[L - 2], 0, 0, h->dYt, 0, 0, Ly.in, kOutPad, cap, e, h->err);
+    rc = launch_gemm(h->st, h->Ht[L - 2], 0, 0, h->dYt, 0, 0, Ly.in, kOutPad, cap, e, h->err, h->wait_ns);
     if (rc) return rc;
     jobs.j[L - 1] = BiasJob{h->dYt.p, cap, h->g + Ly.b_off, kOutPad};
     // dH = dY W, then dZ = dH (1 - H^2) of the last hidden layer
@@ -1080,7 +1087,7 @@ int train_step(mlp_handle *h, const Mat &X, const Mat &Xt, int row0, const float
     d.ld_b = h->dZ[L - 2].cols;
     d.out_bt = h->dZt[L - 2].p;
     d.ld_bt = h->dZt[L - 2].cols;
-    rc = launch_gemm(h->st, h->dY, 0, 0, Ly.wtb, 0, 0, cap, Ly.in, kOutPad, d, h->err);
+    rc = launch_gemm(h->st, h->dY, 0, 0, Ly.wtb, 0, 0, cap, Ly.in, kOutPad, d, h->err, h->wait_ns);
     if (rc) return rc;
   }
   for (int l = L - 2; l >= 0; --l) {
@@ -1092,7 +1099,7 @@ int train_step(mlp_handle *h, const Mat &X, const Mat &Xt, int row0, const float
     e.out_f = h->g + Ly.w_off;
     e.ld_f = Ly.in_k;
     const Mat &Bm = (l == 0) ? Xt : h->Ht[l - 1];
-    rc = launch_gemm(h->st, h->dZt[l], 0, 0, Bm, 0, l == 0 ? row0 : 0, Ly.out, Ly.in_k, cap, e, h->err);
+    rc = launch_gemm(h->st, h->dZt[l], 0, 0, Bm, 0, l == 0 ? row0 : 0, Ly.out, Ly.in_k, cap, e, h->err, h->wait_ns);
     if (rc) return rc;
     jobs.j[l] = BiasJob{h->dZt[l].p, cap, h->g + Ly.b_off, Ly.out};
     if (l > 0) {
@@ -1105,7 +1112,7 @@ int train_step(mlp_handle *h, const Mat &X, const Mat &Xt, int row0, const float
       d.ld_b = h->dZ[l - 1].cols;
       d.out_bt = h->dZt[l - 1].p;
       d.ld_bt = h->dZt[l - 1].cols;
-      rc = launch_gemm(h->st, h->dZ[l], 0, 0, Ly.wtb, 0, 0, cap, Ly.in, Ly.out, d, h->err);
+      rc = launch_gemm(h->st, h->dZ[l], 0, 0, Ly.wtb, 0, 0, cap, Ly.in, Ly.out, d, h->err, h->wait_ns);
       if (rc) return rc;
     }
   }
@@ -1683,6 +1690,16 @@ int mlp_train(mlp_handle *h, const float *X, const float *T, int64_t rows, int32
   for (void *q : {(void *)Tall, (void *)Ts, (void *)ox, (void *)ot, (void *)dperm, (void *)dloss})
     if (q) cudaFree(q);
   return rc;
+}
+
+int mlp_set_wait_limit(mlp_handle *h, int64_t ns) {
+  clear_error();
+  if (!h || ns < 0) {
+    set_error("mlp_set_wait_limit: null handle or negative limit");
+    return MD_EINVAL;
+  }
+  h->wait_ns = (uint64_t)ns;
+  return MD_OK;
 }
 
 void mlp_free(mlp_handle *h) { destroy(h); }

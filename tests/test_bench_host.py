@@ -37,5 +37,12 @@ def test_timed_bytes_count_whole_blocks(bench):
     class A:
         warmup, steps = 5, 1003
 
+    # pushes 1..5 wait after the warm-up call; the timed call's passes apply
+    # pushes 1..1008 (126 whole blocks) and leave 1009 and 1010 waiting
     got = bench.vacf_timed_bytes(A, 8, 16, 2, 100)
-    assert got == bench.vacf_bytes_blocked(5, 5 + 1000, 8, 16, 2, 300, 4, 8)
+    assert got == bench.vacf_bytes_blocked(0, 1008, 8, 16, 2, 300, 4, 8)
+
+    class B:
+        warmup, steps = 5, 20
+
+    assert bench.vacf_timed_bytes(B, 8, 16, 2, 100) == bench.vacf_bytes_blocked(0, 24, 8, 16, 2, 300, 4, 8)

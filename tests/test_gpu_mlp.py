@@ -203,3 +203,31 @@ def test_corr_read_rows_equals_corr_read(pkg):
         assert np.allclose(r3[i], want, rtol=1e-14, atol=0)
     with pytest.raises(pkg.MdError):
         c.read_rows(10, 1, 3)
+
+
+def test_pipeline_wait_timeout_is_an_error_status(pkg, omlp):
+    """A tensor-core pipeline wait that runs out ends the call with
+    MD_ETIMEOUT and leaves the handle usable.  The wait limit is set to 0,
+    so the first wait on a TMA panel or a stage's products that is not
+    already complete gives up (the copies and products already issued are
+    still waited for before the CTA exits); no wait is left unbounded and
+    nothing traps.  With the default limit restored the same call matches
+    the oracle again."""
+    B = 256
+    params = f32(synth.mlp_init(41, DIMS, bias_scale=0.2))
+    net = pkg.MLP(132, 2, batch=B)
+    net.set_params(params)
+    X = synth.normal(42, B * 132).reshape(B, 132).astype(np.float32)
+    T = synth.normal(43, B * 2).reshape(B, 2).astype(np.float32)
+    net.set_wait_limit(0)
+    with pytest.raises(pkg.MdError) as ei:
+        net.loss_grad(X, T)
+    assert ei.value.code == -5  # MD_ETIMEOUT
+    with pytest.raises(pkg.MdError):
+        net.set_wait_limit(-1)
+    net.set_wait_limit(2_000_000_000)
+    net.set_params(params)
+    loss, _ = net.loss_grad(X, T)
+    ye, _ = omlp.forward(params, X.astype(np.float64), True)
+    assert loss == pytest.approx(omlp.loss(ye, T.astype(np.float64)), rel=1e-5)
+    net.close()
