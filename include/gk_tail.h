@@ -114,6 +114,39 @@ OTF_API int gk_tail_features(const double *c_sigma, const double *c_q, int64_t l
                              const double *volume, const double *temperature, const double *density,
                              float *out);
 
+/* Where the learned tail is used (a project extension; the paper has no
+ * counterpart).  The network is trusted inside the temperature-density box
+ * of its training runs, and only where a run is short enough that its own
+ * Green-Kubo integral is expected to be less accurate than the network: the
+ * own integral's rms relative error is modelled as short_coeff / sqrt(steps)
+ * (it falls with the run length and, for the integral of one global flux,
+ * not with the number of atoms), the network's as net_error, its rms
+ * relative error on validation runs.  Index 0: viscosity, 1: conductivity. */
+typedef struct {
+  double T_min, T_max, rho_min, rho_max; /* the training runs' temperature and density box */
+  double net_error[2];                   /* the network's rms relative error on validation runs */
+  double short_coeff[2];                 /* own integral: rms relative error x sqrt(correlated steps) */
+} gk_tail_rule;
+
+/* The box of n runs' temperatures and densities (host arrays) into rule.
+ * MD_EINVAL for a null argument or n < 1. */
+OTF_API int gk_tail_box(const double *temperature, const double *density, int64_t n, gk_tail_rule *rule);
+
+/* sqrt(mean_r (((a_r - b_r) / b_r)^2 w_r)) over n host values, w = NULL
+ * meaning all weights 1: the network's validation error (w = NULL), or, with
+ * a = the short runs' integrals, b = the long runs' and w = the short runs'
+ * correlated steps, short_coeff.  MD_EINVAL for a null argument, n < 1 or a
+ * zero b_r. */
+OTF_API int gk_tail_rms_rel(const double *a, const double *b, const double *w, int64_t n, double *out);
+
+/* Per run r and output k (host arrays; net, own, out, used [nruns][2]):
+ * out = net where (T_r, rho_r) lies in the rule's box and
+ * short_coeff[k] / sqrt(steps_r) > net_error[k], else own; used (nullable)
+ * records the choice.  MD_EINVAL for a null argument or steps_r <= 0. */
+OTF_API int gk_tail_choose(const gk_tail_rule *rule, const double *temperature, const double *density,
+                           const double *steps, const double *net, const double *own, int64_t nruns, double *out,
+                           int32_t *used);
+
 /* Reads `rows` rows of a correlator at once: row i is the mean of groups
  * g0 + i*avg .. g0 + i*avg + avg - 1 on the Algorithm 2 readout grid.
  * times [npts] and values [rows][cap] (host); *n = points per row.

@@ -97,7 +97,7 @@ typedef struct {
 } corr_spec;
 
 typedef struct {
-  int64_t n;          /* atoms, >= 2 */
+  int64_t n;          /* atoms, 2 .. 2^26 - 1 (over all replicas of a batch too) */
   double box;         /* edge of the periodic cubic box */
   double eps, sigma;  /* Lennard-Jones parameters */
   double rc;          /* cutoff radius; box >= 3 (rc + skin) */

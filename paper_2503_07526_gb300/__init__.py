@@ -29,7 +29,10 @@ from ._lib import (  # noqa: F401
     MdError,
     System,
     gk_integrate,
+    gk_tail_box,
+    gk_tail_choose,
     gk_tail_features,
+    gk_tail_rms_rel,
     lib,
     fp32_peak,
     make_params,

@@ -63,6 +63,11 @@ class md_config(C.Structure):
                 ("build_kind", C.c_int32), ("vacf_input_bytes", C.c_int64)]
 
 
+class gk_tail_rule(C.Structure):
+    _fields_ = [("T_min", C.c_double), ("T_max", C.c_double), ("rho_min", C.c_double), ("rho_max", C.c_double),
+                ("net_error", C.c_double * 2), ("short_coeff", C.c_double * 2)]
+
+
 class md_obs(C.Structure):
     _fields_ = [("step", C.c_int64), ("U", C.c_double), ("K", C.c_double), ("T", C.c_double),
                 ("sigma", C.c_double * 6), ("q", C.c_double * 3), ("T_mean", C.c_double),
@@ -120,6 +125,9 @@ def lib(build: bool = False):
         "md_observables_noalloc": [i64, C.c_double, vp, vp, vp, vp, vp, vp],
         "md_fp32_peak": [i32, i64, i32, vp, dp, dp, C.POINTER(C.c_int32)],
         "mlp_set_wait_limit": [vp, i64],
+        "gk_tail_box": [dp, dp, i64, C.POINTER(gk_tail_rule)],
+        "gk_tail_rms_rel": [dp, dp, dp, i64, dp],
+        "gk_tail_choose": [C.POINTER(gk_tail_rule), dp, dp, dp, dp, dp, i64, dp, vp],
         "mlp_create": [C.POINTER(mlp_params), vp, C.POINTER(vp)],
         "mlp_param_count": [vp, C.POINTER(C.c_int64)],
         "mlp_get_params": [vp, vp, i64, i32],
@@ -155,7 +163,8 @@ EXPORTS = ("md_init", "md_step", "md_observables", "md_get_particles", "md_scale
            "md_observables_noalloc", "md_init_replicas", "md_replica_observables", "md_replica_scale_velocities",
            "md_get_config", "md_replica_observables_all", "mlp_create", "mlp_param_count", "mlp_get_params",
            "mlp_set_params", "mlp_set_scaler", "mlp_fit_scaler", "mlp_forward", "mlp_loss_grad", "mlp_adam_step",
-           "mlp_train", "mlp_free", "gk_tail_features", "corr_read_rows", "md_fp32_peak", "mlp_set_wait_limit")
+           "mlp_train", "mlp_free", "gk_tail_features", "corr_read_rows", "md_fp32_peak", "mlp_set_wait_limit", "gk_tail_box", "gk_tail_rms_rel",
+           "gk_tail_choose")
 
 
 def _check(rc):
@@ -587,6 +596,47 @@ class MLP:
             _lib.mlp_free(h)
 
     __del__ = close
+
+
+def _f64c(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a if n is None else np.ascontiguousarray(np.broadcast_to(a, (n,)))
+
+
+def gk_tail_box(temperature, density):
+    """The temperature-density box of training runs (a gk_tail_rule with
+    only the box set)."""
+    T, rho = _f64c(temperature), _f64c(density)
+    rule = gk_tail_rule()
+    dp = C.POINTER(C.c_double)
+    _check(lib().gk_tail_box(T.ctypes.data_as(dp), rho.ctypes.data_as(dp), T.size, C.byref(rule)))
+    return rule
+
+
+def gk_tail_rms_rel(a, b, w=None):
+    """sqrt(mean(((a - b) / b)^2 w)) (w = None: weights 1)."""
+    a, b = _f64c(a).ravel(), _f64c(b).ravel()
+    dp = C.POINTER(C.c_double)
+    wp = None if w is None else _f64c(w).ravel()
+    out = C.c_double(0.0)
+    _check(lib().gk_tail_rms_rel(a.ctypes.data_as(dp), b.ctypes.data_as(dp),
+                                 None if wp is None else wp.ctypes.data_as(dp), a.size, C.byref(out)))
+    return out.value
+
+
+def gk_tail_choose(rule, temperature, density, steps, net, own):
+    """(out [nruns, 2], used [nruns, 2] bool): the network's (eta, kappa)
+    or the runs' own integrals, per the rule."""
+    net, own = _f64c(net).reshape(-1, 2), _f64c(own).reshape(-1, 2)
+    nr = net.shape[0]
+    T, rho, st = _f64c(temperature, nr), _f64c(density, nr), _f64c(steps, nr)
+    out = np.zeros((nr, 2))
+    used = np.zeros((nr, 2), dtype=np.int32)
+    dp = C.POINTER(C.c_double)
+    _check(lib().gk_tail_choose(C.byref(rule), T.ctypes.data_as(dp), rho.ctypes.data_as(dp), st.ctypes.data_as(dp),
+                                net.ctypes.data_as(dp), own.ctypes.data_as(dp), nr, out.ctypes.data_as(dp),
+                                used.ctypes.data))
+    return out, used.astype(bool)
 
 
 def gk_tail_features(c_sigma, c_q, volume, temperature, density):

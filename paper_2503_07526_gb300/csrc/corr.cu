@@ -260,7 +260,7 @@ int launch_grouped(const CorrDev &c, const Tin *x, const Tin *y, PushIdx pi, cud
 // those of Algorithm 1; only the order of the additions within a lag sum
 // differs.  k_push_higher then applies the higher blocks.
 template <typename T, typename Tin, int V, bool VIN, int U>
-__global__ void __launch_bounds__(kPushThreads, 2)
+__global__ void __launch_bounds__(kPushThreads, sizeof(T) == 4 ? 2 : 1)
     k_push_block0(CorrDev c, const Tin *__restrict__ xh, BlockIdx bi) {
   constexpr int P1 = 15;  // older samples kept for block 0 (p - 1 with p = 16)
   const int64_t st = *bi.d_step - *bi.d_base;

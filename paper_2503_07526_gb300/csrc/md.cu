@@ -52,6 +52,7 @@ constexpr int kCellWarps = 4;  // warps (cells) per CTA in the link-cell kernels
 constexpr int kNRed = 14;      // K, U, V*sigma[6], V*q[3], V*j[3]
 constexpr int kNBanks = 4;     // stress, heat flux, velocity, mass flux
 constexpr int kMaxRedBlocks = 152 * 4;
+constexpr double kRClose = 1.05;  // close-pair radius of the mixed form, in sigma
 
 // Step counters shared by all replicas.
 struct StepDev {
@@ -102,7 +103,8 @@ struct Sys {
   const double *lam;         // [nrep] velocity scale factors (md_scale_velocities)
   // cell-sorted state
   double *r, *v;             // FP64 form: absolute positions, velocities [3][n]
-  float *offl, *vh, *vl;     // mixed form: offset low words, velocity words [3][n]
+  float4 *rlo;               // mixed form: offset low words (x, y, z, 0) [n]
+  float *vh, *vl;            // mixed form: velocity words [3][n]
   void *F, *epot, *W;        // [3][n], [n], [6][n] in the pair type
   void *rel, *relb;          // Vec4 of the pair type: current / at last rebuild
   void *vbuf;                // [vacf_slots][3][n] velocities in atom-id order, one slot per waiting
@@ -124,7 +126,9 @@ struct Sys {
 
 template <typename TF>
 struct LJ {
-  TF eps4, eps24, sig2, rc2, ushift, rlist2;
+  TF c12, c6, f12, f6;  // 4 eps sig^12, 4 eps sig^6, 12 c12, 6 c6
+  TF rc2, ushift, rlist2;
+  TF rclose2;           // mixed form: pairs closer than r_close get the rounded-once displacement
   // MD_POT_BUCK_EWALD: A exp(-r/rho) - C/r^6 + ke qq erfc(alpha r)/r
   TF A, inv_rho, C6, alpha, c2, ke;  // c2 = 2 alpha / sqrt(pi)
 };
@@ -220,16 +224,17 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift_df(Sys d) {
     // every load first (the stores below could alias them for the compiler)
     const float4 o = rel[i];
     const float4 b = relb[i];
-    float fa[3], vh[3], vl[3], ol[3];
+    const float4 lo = d.rlo[i];
+    const float ol[3] = {lo.x, lo.y, lo.z};
+    float fa[3], vh[3], vl[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       fa[a] = F[a * n + i];
       vh[a] = d.vh[a * n + i];
       vl[a] = d.vl[a * n + i];
-      ol[a] = d.offl[a * n + i];
     }
     const dfloat h{d.hdtm_h[t], d.hdtm_l[t]};
-    float oh[3] = {o.x, o.y, o.z};
+    float oh[3] = {o.x, o.y, o.z}, nl[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       dfloat v{vh[a], vl[a]};
@@ -239,9 +244,10 @@ __global__ void __launch_bounds__(kThreads) k_kick_drift_df(Sys d) {
       dfloat x{oh[a], ol[a]};
       x = df_add(x, df_mul(dt, v));
       oh[a] = x.h;
-      d.offl[a * n + i] = x.l;
+      nl[a] = x.l;
     }
     rel[i] = make_float4(oh[0], oh[1], oh[2], o.w);
+    d.rlo[i] = make_float4(nl[0], nl[1], nl[2], 0.f);
     const float dx = oh[0] - b.x, dy = oh[1] - b.y, dz = oh[2] - b.z;
     if ((dx * dx + dy * dy + dz * dz) > lim2) request_rebuild(d, d.rep_of_atom[i]);
     bad |= !(isfinite(oh[0]) && isfinite(oh[1]) && isfinite(oh[2]));
@@ -318,13 +324,14 @@ __global__ void __launch_bounds__(kThreads) k_rb_assign_df(Sys d) {
     const int nc = R.nc;
     const dfloat edge{R.edge_h, R.edge_l};
     const float4 o = rel[i];
-    const float oh[3] = {o.x, o.y, o.z};
+    const float4 lo = d.rlo[i];
+    const float oh[3] = {o.x, o.y, o.z}, ol[3] = {lo.x, lo.y, lo.z};
     int cc[3];
     unpack_cell(d.cpk[i], cc[0], cc[1], cc[2]);
     int ci[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      dfloat x{oh[a], d.offl[a * n + i]};
+      dfloat x{oh[a], ol[a]};
       int k = (int)rintf(x.h / R.edge_h);  // NaN converts to 0
       k = max(-nc, min(nc, k));
       if (k != 0) x = df_add(x, df_mul_f(edge, (float)(-k)));
@@ -464,14 +471,15 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_rb_rank(Sys d) {
         } else {
           const float *oB = reinterpret_cast<const float *>(d.rB);
           const float *wB = reinterpret_cast<const float *>(d.vB);
-          float oh[3];
+          float oh[3], ol[3];
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
             oh[q] = oB[q * n + a];
-            d.offl[q * n + dst] = oB[3 * n + q * n + a];
+            ol[q] = oB[3 * n + q * n + a];
             d.vh[q * n + dst] = wB[q * n + a];
             d.vl[q * n + dst] = wB[3 * n + q * n + a];
           }
+          d.rlo[dst] = make_float4(ol[0], ol[1], ol[2], 0.f);
           const float4 o = make_float4(oh[0], oh[1], oh[2], (float)d.charge[min(max(d.typeB[a], 0), 7)]);
           static_cast<float4 *>(d.rel)[dst] = o;
           static_cast<float4 *>(d.relb)[dst] = o;
@@ -483,12 +491,60 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_rb_rank(Sys d) {
 
 // ---------------------------------------------------------------- pairs
 
-// Shifted LJ pair terms for r2 < rc2 (Sec. 2.3): adds f_ij = fs d to f,
-// U(r) to e and d (x) f_ij to w (the 1/2 of the per-particle split is
+// Neighbour-list entries: j << 6 | (oz + 1) << 4 | (oy + 1) << 2 | (ox + 1).
+// (ox, oy, oz) in {-1, 0, 1}^3 is the cell of j relative to the cell of i,
+// so j's offset from its own cell centre moves into i's frame by (ox, oy, oz)
+// cell edges (the periodic image is implied).  26 bits of atom index.
+constexpr int kEntShift = 6;
+__device__ __forceinline__ uint32_t list_entry(int j, int ox, int oy, int oz) {
+  return ((uint32_t)j << kEntShift) | (uint32_t)((ox + 1) | ((oy + 1) << 2) | ((oz + 1) << 4));
+}
+__device__ __forceinline__ int entry_atom(uint32_t e) { return (int)(e >> kEntShift); }
+__device__ __forceinline__ void entry_image(uint32_t e, int &ox, int &oy, int &oz) {
+  ox = (int)(e & 3u) - 1;
+  oy = (int)((e >> 2) & 3u) - 1;
+  oz = (int)((e >> 4) & 3u) - 1;
+}
+
+// Final list length of a build, clamped to the capacity (an overflow is
+// reported through the error word).
+__device__ __forceinline__ int list_count(const Sys &d, int cnt) {
+  if (cnt > d.maxnb) atomicOr(d.err, ERR_NBR_OVERFLOW);
+  return min(cnt, d.maxnb);
+}
+
+// Pair terms at squared distance r2 < rc2 (Sec. 2.3's pair potential):
+// returns fs = -U'(r)/r, so that the force on i is fs d with d = r_i - r_j,
+// and sets u = U(r).  Lennard-Jones, energy-shifted: U = c12 / r^12 -
+// c6 / r^6 - U(rc), fs = (f12 / r^12 - f6 / r^6) / r^2 with c12 = 4 eps sig^12,
+// c6 = 4 eps sig^6, f12 = 12 c12, f6 = 6 c6.  qq is the product of the two
+// charges (the Buckingham + real-space Ewald form).
+template <typename TF, int POT>
+__device__ __forceinline__ TF pair_terms(const LJ<TF> &lj, TF r2, TF qq, TF &u) {
+  if constexpr (POT == kPotLJ) {
+    const TF ir2 = pair_rcp(r2);
+    const TF ir6 = ir2 * ir2 * ir2;
+    u = ir6 * (lj.c12 * ir6 - lj.c6) - lj.ushift;
+    return ir2 * ir6 * (lj.f12 * ir6 - lj.f6);
+  } else {
+    // Buckingham plus the real-space Ewald term (arXiv 2503.07526 Sec. 5.3;
+    // erfc screening of Essmann et al. 1995)
+    const TF r = sqrt(r2);
+    const TF ir = TF(1) / r;
+    const TF ir2 = ir * ir;
+    const TF ir6 = ir2 * ir2 * ir2;
+    const TF ex = lj.A * exp(-r * lj.inv_rho);
+    const TF ar = lj.alpha * r;
+    const TF ec = erfc(ar);
+    const TF qk = lj.ke * qq;
+    u = ex - lj.C6 * ir6 + qk * ec * ir;
+    const TF mdu = ex * lj.inv_rho - TF(6) * lj.C6 * ir6 * ir + qk * (ec * ir2 + lj.c2 * exp(-ar * ar) * ir);
+    return mdu * ir;
+  }
+}
+
+// f += fs d, e += u, w += d (x) (fs d) (the 1/2 of the per-particle split is
 // applied once at the end).
-// Pair force, energy and virial of one pair (r2 < rc2): f += fs d,
-// e += U, w += d (x) (fs d), with fs = -U'(r)/r.  POT selects the
-// interaction; qq is the product of the two charges (unused for LJ).
 template <typename TF>
 __device__ __forceinline__ void pair_add(TF dx, TF dy, TF dz, TF u, TF fs, TF f[3], TF &e, TF w[6]) {
   const TF fx = fs * dx, fy = fs * dy, fz = fs * dz;
@@ -507,28 +563,9 @@ __device__ __forceinline__ void pair_add(TF dx, TF dy, TF dz, TF u, TF fs, TF f[
 template <typename TF, int POT>
 __device__ __forceinline__ void lj_accumulate(const LJ<TF> &lj, TF dx, TF dy, TF dz, TF r2, TF qq, TF f[3],
                                               TF &e, TF w[6]) {
-  if constexpr (POT == kPotLJ) {
-    const TF ir2 = pair_rcp(r2);
-    const TF s2 = lj.sig2 * ir2;
-    const TF s6 = s2 * s2 * s2;
-    const TF u = lj.eps4 * s6 * (s6 - TF(1)) - lj.ushift;
-    const TF fs = lj.eps24 * s6 * (s6 + s6 - TF(1)) * ir2;
-    pair_add<TF>(dx, dy, dz, u, fs, f, e, w);
-  } else {
-    // Buckingham plus the real-space Ewald term (arXiv 2503.07526 Sec. 5.3;
-    // erfc screening of Essmann et al. 1995)
-    const TF r = sqrt(r2);
-    const TF ir = TF(1) / r;
-    const TF ir2 = ir * ir;
-    const TF ir6 = ir2 * ir2 * ir2;
-    const TF ex = lj.A * exp(-r * lj.inv_rho);
-    const TF ar = lj.alpha * r;
-    const TF ec = erfc(ar);
-    const TF qk = lj.ke * qq;
-    const TF u = ex - lj.C6 * ir6 + qk * ec * ir;
-    const TF mdu = ex * lj.inv_rho - TF(6) * lj.C6 * ir6 * ir + qk * (ec * ir2 + lj.c2 * exp(-ar * ar) * ir);
-    pair_add<TF>(dx, dy, dz, u, mdu * ir, f, e, w);
-  }
+  TF u;
+  const TF fs = pair_terms<TF, POT>(lj, r2, qq, u);
+  pair_add<TF>(dx, dy, dz, u, fs, f, e, w);
 }
 
 template <typename TF>
@@ -550,15 +587,33 @@ __device__ __forceinline__ void image_offset(int code, int &ox, int &oy, int &oz
   oz = code / 9 - 1;
 }
 
+// The displacement r_i - r_j along one axis from double-float offsets
+// (hi + lo) in cells o edges apart (edge eh + el), rounded to FP32 once: the
+// high words' difference is split into its rounded value and exact error
+// (TwoSum), the cell offset comes off the rounded value (exact for pairs
+// closer than half an edge, by Sterbenz's lemma), and the error, the low
+// words and the edge's low word are added before the final rounding.
+__device__ __forceinline__ float exact_disp(float hi_i, float lo_i, float hi_j, float lo_j, float o, float eh,
+                                            float el) {
+  const dfloat s = df_two_sum(hi_i, -hi_j);
+  const float t = fmaf(-o, eh, s.h);
+  const float c = fmaf(-o, el, s.l + (lo_i - lo_j));
+  return t + c;
+}
+
 // Direct link-cell forces (MD_PAIR_CELLS), one warp per cell (lanes = the
 // cell's atoms, 32 at a time; warps stride over the cells).  The 27
-// neighbour cells are staged through shared memory 32 atoms at a time,
-// already moved into the i cell's frame; every lane then sweeps the staged
-// atoms (broadcast reads).
+// neighbour cells are staged through shared memory 32 atoms at a time; every
+// lane then sweeps the staged atoms (broadcast reads), moving each into its
+// own cell's frame first (pj + o edge).  In the mixed form pairs closer than
+// r_close take the rounded-once displacement (exact_disp) from the offsets'
+// low words.
 template <typename TF, int POT>
 __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
   using V4 = typename Vec4<TF>::type;
+  constexpr bool kMixed = std::is_same<TF, float>::value;
   __shared__ V4 spos[kCellWarps][32];
+  __shared__ float4 slo[kCellWarps][32];
   __shared__ int sidx[kCellWarps][32];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const V4 *rel = static_cast<const V4 *>(d.rel);
@@ -573,7 +628,11 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
       const int i = ib + lane;
       const bool act = i < i1;
       V4 pi;
-      if (act) pi = Vec4<TF>::load(rel + i);
+      float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (act) {
+        pi = Vec4<TF>::load(rel + i);
+        if constexpr (kMixed) li = d.rlo[i];
+      }
       TF f[3] = {0, 0, 0}, e = 0, w[6] = {0, 0, 0, 0, 0, 0};
       for (int code = 0; code < 27; ++code) {
         int ox, oy, oz;
@@ -585,13 +644,8 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
         for (int jb = j0; jb < j1; jb += 32) {
           __syncwarp();
           if (jb + lane < j1) {
-            const V4 pj = Vec4<TF>::load(rel + jb + lane);
-            V4 t;
-            t.x = pj.x + offx;
-            t.y = pj.y + offy;
-            t.z = pj.z + offz;
-            t.w = pj.w;
-            spos[wl][lane] = t;
+            spos[wl][lane] = Vec4<TF>::load(rel + jb + lane);
+            if constexpr (kMixed) slo[wl][lane] = d.rlo[jb + lane];
             sidx[wl][lane] = jb + lane;
           }
           __syncwarp();
@@ -599,13 +653,24 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
           if (act) {
             for (int t = 0; t < nj; ++t) {
               const V4 pj = spos[wl][t];
-              // pj already holds j in i's cell frame: the same subtraction
-              // the list kernel performs
-              const TF dx = pi.x - pj.x;
-              const TF dy = pi.y - pj.y;
-              const TF dz = pi.z - pj.z;
-              const TF r2 = dx * dx + dy * dy + dz * dz;
-              if (r2 < lj.rc2 && sidx[wl][t] != i) lj_accumulate<TF, POT>(lj, dx, dy, dz, r2, pi.w * pj.w, f, e, w);
+              // j moved into i's cell frame first: for a close pair across a
+              // cell face pj + o lands next to pi, so the subtraction is exact
+              TF dx = pi.x - (pj.x + offx);
+              TF dy = pi.y - (pj.y + offy);
+              TF dz = pi.z - (pj.z + offz);
+              TF r2 = dx * dx + dy * dy + dz * dz;
+              if (r2 < lj.rc2 && sidx[wl][t] != i) {
+                if constexpr (kMixed) {
+                  if (r2 < lj.rclose2) {
+                    const float4 lj4 = slo[wl][t];
+                    dx = exact_disp(pi.x, li.x, pj.x, lj4.x, (float)ox, R.edge_h, R.edge_l);
+                    dy = exact_disp(pi.y, li.y, pj.y, lj4.y, (float)oy, R.edge_h, R.edge_l);
+                    dz = exact_disp(pi.z, li.z, pj.z, lj4.z, (float)oz, R.edge_h, R.edge_l);
+                    r2 = dx * dx + dy * dy + dz * dz;
+                  }
+                }
+                lj_accumulate<TF, POT>(lj, dx, dy, dz, r2, pi.w * pj.w, f, e, w);
+              }
             }
           }
         }
@@ -617,7 +682,7 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
 
 // Verlet-list build, one warp per chunk of 32 consecutive atoms of the
 // cell-sorted order; the lists of a chunk fill one block of maxnb rows x 32
-// lanes (entry k of atom i at block(i / 32) + 32 k + i % 32), so the pair
+// lanes (slot k of atom i at block(i / 32) + 32 k + i % 32), so the pair
 // kernel reads a row of 128 bytes per step of its loop and the rows being
 // written stay together in L2.  The chunk's atoms fall into one or a few
 // cells ("segments").  For each segment, j-parallel: the chunk's i
@@ -625,8 +690,7 @@ __global__ void __launch_bounds__(kCellWarps * 32) k_cells(Sys d, LJ<TF> lj) {
 // time from a row of three x-adjacent neighbour cells (one contiguous range
 // of the sorted order unless the row wraps), move them into the i cell's
 // frame and, for each i of the segment, test all 32 at once; a ballot and a
-// population count give every accepted j its list slot.  Entries are
-// j | (image code << 27).
+// population count give every accepted j its list slot.
 template <typename TF, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_build(Sys d, LJ<TF> lj) {
   using V4 = typename Vec4<TF>::type;
@@ -689,7 +753,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_build(Sys d, LJ<TF> lj) {
               t.y = pj.y + oy * edge;
               t.z = pj.z + oz * edge;
             }
-            const uint32_t tag = (uint32_t)j | ((uint32_t)((ox + 1) + 3 * row) << 27);
+            const uint32_t tag = list_entry(j, ox, oy, oz);
             for (int ii = s; ii < e; ++ii) {
               const int li = ii - a0;  // lane that owns atom ii
               const V4 pi = spi[wl][li];
@@ -709,58 +773,39 @@ __global__ void __launch_bounds__(WARPS * 32) k_build(Sys d, LJ<TF> lj) {
       }
       s = e;
     }
-    if (a0 + lane < a1 && rebuilds(d, d.rep_of_atom[a0 + lane])) {
-      d.nnb[a0 + lane] = min(cnt, d.maxnb);
-      if (cnt > d.maxnb) atomicOr(d.err, ERR_NBR_OVERFLOW);
-    }
+    if (a0 + lane < a1 && rebuilds(d, d.rep_of_atom[a0 + lane])) d.nnb[a0 + lane] = list_count(d, cnt);
   }
 }
 
-// Verlet-list pair kernel: one thread per atom (cell-sorted, so a warp's
-// neighbours overlap and their coordinates come from L1), full neighbour
-// shell, no atomics; FP32 FMA work on the CUDA cores in the mixed form.  The
-// list is streamed with evict-first loads; the loop is unrolled by kUnroll
-// so that kUnroll index loads and then kUnroll coordinate gathers are in
-// flight before the arithmetic that needs them.
+// FP64 Verlet-list pair kernel (the comparison form and the FP64 ionic
+// path): one thread per atom (cell-sorted, so a warp's neighbours overlap
+// and their coordinates come from L1), full neighbour shell, no atomics.
+// The list is streamed with evict-first loads; the loop is unrolled by
+// kUnroll so that kUnroll index loads and then kUnroll coordinate gathers
+// are in flight before the arithmetic that needs them.
 constexpr int kUnroll = 4;
 
 template <typename TF, int POT>
-__device__ __forceinline__ void pair_from_entry(const LJ<TF> &lj, const typename Vec4<TF>::type *off,
-                                                uint32_t ent, const typename Vec4<TF>::type &pi,
+__device__ __forceinline__ void pair_from_entry(const LJ<TF> &lj, TF edge, uint32_t ent,
+                                                const typename Vec4<TF>::type &pi,
                                                 const typename Vec4<TF>::type &pj, TF f[3], TF &e, TF w[6]) {
-  const typename Vec4<TF>::type o = off[ent >> 27];
+  int ox, oy, oz;
+  entry_image(ent, ox, oy, oz);
   // j moved into i's cell frame first: for a close pair across a cell face
-  // pj + off lands next to pi, so the final subtraction is exact.
-  const TF dx = pi.x - (pj.x + o.x);
-  const TF dy = pi.y - (pj.y + o.y);
-  const TF dz = pi.z - (pj.z + o.z);
+  // pj + o lands next to pi, so the final subtraction is exact.
+  const TF dx = pi.x - (pj.x + ox * edge);
+  const TF dy = pi.y - (pj.y + oy * edge);
+  const TF dz = pi.z - (pj.z + oz * edge);
   const TF r2 = dx * dx + dy * dy + dz * dz;
   if (r2 < lj.rc2) lj_accumulate<TF, POT>(lj, dx, dy, dz, r2, pi.w * pj.w, f, e, w);
 }
 
-// A CTA spans at most two replicas (replicas hold at least kMaxPairThreads
-// atoms), so it keeps the image offsets of both in shared memory.
 template <typename TF, int POT>
 __global__ void __launch_bounds__(kMaxPairThreads) k_pair_list(Sys d, LJ<TF> lj) {
   using V4 = typename Vec4<TF>::type;
-  __shared__ V4 offs[2][27];  // image offsets, one vector load per pair
-  const int64_t blk0 = blockIdx.x * (int64_t)blockDim.x;
-  const int r0 = d.rep_of_atom[blk0];
-  const int r1 = d.rep_of_atom[min(blk0 + blockDim.x, d.n) - 1];
-  if (threadIdx.x < 54) {
-    const int which = threadIdx.x / 27, code = threadIdx.x % 27;
-    const TF edge = (TF)d.rep[which ? r1 : r0].edge;
-    int ox, oy, oz;
-    image_offset(code, ox, oy, oz);
-    offs[which][code].x = ox * edge;
-    offs[which][code].y = oy * edge;
-    offs[which][code].z = oz * edge;
-    offs[which][code].w = TF(0);
-  }
-  __syncthreads();
-  const int64_t i = blk0 + threadIdx.x;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= d.n) return;
-  const V4 *off = offs[d.rep_of_atom[i] == r0 ? 0 : 1];
+  const TF edge = (TF)rep_of(d, i).edge;
   const V4 *rel = static_cast<const V4 *>(d.rel);
   const V4 pi = Vec4<TF>::load(rel + i);
   TF f[3] = {0, 0, 0}, e = 0, w[6] = {0, 0, 0, 0, 0, 0};
@@ -773,16 +818,121 @@ __global__ void __launch_bounds__(kMaxPairThreads) k_pair_list(Sys d, LJ<TF> lj)
     for (int u = 0; u < kUnroll; ++u) ent[u] = __ldcs(nb + (k + u) * 32);
     V4 pj[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) pj[u] = Vec4<TF>::load(rel + (ent[u] & 0x07ffffffu));
+    for (int u = 0; u < kUnroll; ++u) pj[u] = Vec4<TF>::load(rel + entry_atom(ent[u]));
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) pair_from_entry<TF, POT>(lj, off, ent[u], pi, pj[u], f, e, w);
+    for (int u = 0; u < kUnroll; ++u) pair_from_entry<TF, POT>(lj, edge, ent[u], pi, pj[u], f, e, w);
   }
   for (; k < nn; ++k) {
     const uint32_t ent = __ldcs(nb + k * 32);
-    const V4 pj = Vec4<TF>::load(rel + (ent & 0x07ffffffu));
-    pair_from_entry<TF, POT>(lj, off, ent, pi, pj, f, e, w);
+    const V4 pj = Vec4<TF>::load(rel + entry_atom(ent));
+    pair_from_entry<TF, POT>(lj, edge, ent, pi, pj, f, e, w);
   }
   store_pair_out<TF>(d, i, f, e, w);
+}
+
+// Mixed-form Verlet-list pair kernel: one thread per atom (cell-sorted, so
+// a warp's neighbours overlap and their coordinates come from L1), full
+// neighbour shell, no atomics (deterministic sums), FP32 FMA work on the CUDA
+// cores.  The list is streamed with evict-first loads; the loop is unrolled
+// by kUnroll so that kUnroll index loads and then kUnroll coordinate gathers
+// are in flight before the arithmetic.  The image offsets of the at most two
+// replicas a CTA spans sit in shared memory, one vector per image code.
+//
+// Close pairs (closer than r_close, where |dF/dr| is largest and the FP32
+// rounding of the displacement dominates the force error): the main loop
+// keeps their list entries (up to kMaxClose) in a per-thread array, and
+// afterwards each such pair's term is replaced by the one of the
+// displacement rounded once from the double-float offsets (exact_disp): the
+// thread subtracts the main loop's term, recomputed by the same code, and
+// adds the exact one.
+constexpr int kMaxClose = 16;
+
+template <int POT>
+__device__ __forceinline__ bool mixed_term(const LJ<float> &lj, float dx, float dy, float dz, float qq, float sign,
+                                           float f[3], float &e, float w[6]) {
+  const float r2 = dx * dx + dy * dy + dz * dz;
+  if (r2 < lj.rc2) {
+    float u;
+    const float fs = pair_terms<float, POT>(lj, r2, qq, u);
+    pair_add<float>(dx, dy, dz, sign * u, sign * fs, f, e, w);
+  }
+  return r2 < lj.rclose2;
+}
+
+template <int POT>
+__global__ void __launch_bounds__(kMaxPairThreads) k_pair_mixed(Sys d, LJ<float> lj) {
+  __shared__ float4 offs[2][64];  // by image code (entry bits 0..5)
+  const int64_t blk0 = blockIdx.x * (int64_t)blockDim.x;
+  const int r0 = d.rep_of_atom[blk0];
+  const int r1 = d.rep_of_atom[min(blk0 + blockDim.x, d.n) - 1];
+  for (int t = threadIdx.x; t < 128; t += blockDim.x) {
+    const int which = t >> 6, code = t & 63;
+    const float edge = d.rep[which ? r1 : r0].edge_h;
+    const int ox = (code & 3) - 1, oy = ((code >> 2) & 3) - 1, oz = ((code >> 4) & 3) - 1;
+    offs[which][code] = make_float4(ox * edge, oy * edge, oz * edge, 0.f);
+  }
+  __syncthreads();
+  const int64_t i = blk0 + threadIdx.x;
+  if (i >= d.n) return;
+  const int ri = d.rep_of_atom[i];
+  const float4 *off = offs[ri == r0 ? 0 : 1];
+  const float4 *rel = static_cast<const float4 *>(d.rel);
+  const float4 pi = rel[i];
+  float f[3] = {0.f, 0.f, 0.f}, e = 0.f, w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const int nn = d.nnb[i];
+  const uint32_t *nb = d.nbr + (i >> 5) * d.maxnb * 32 + (i & 31);
+  // j moved into i's cell frame first: for a close pair across a cell face
+  // pj + o lands next to pi, so the final subtraction is exact
+  auto disp = [&](uint32_t ent, const float4 &pj, float &dx, float &dy, float &dz) {
+    const float4 o = off[ent & 63u];
+    dx = pi.x - (pj.x + o.x);
+    dy = pi.y - (pj.y + o.y);
+    dz = pi.z - (pj.z + o.z);
+  };
+  uint32_t close[kMaxClose];
+  int ncl = 0;
+  int k = 0;
+  for (; k + kUnroll <= nn; k += kUnroll) {
+    uint32_t ent[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) ent[u] = __ldcs(nb + (k + u) * 32);
+    float4 pj[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) pj[u] = rel[entry_atom(ent[u])];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      float dx, dy, dz;
+      disp(ent[u], pj[u], dx, dy, dz);
+      if (mixed_term<POT>(lj, dx, dy, dz, pi.w * pj[u].w, 1.f, f, e, w) && ncl < kMaxClose) close[ncl++] = ent[u];
+    }
+  }
+  for (; k < nn; ++k) {
+    const uint32_t ent = __ldcs(nb + k * 32);
+    const float4 pj = rel[entry_atom(ent)];
+    float dx, dy, dz;
+    disp(ent, pj, dx, dy, dz);
+    if (mixed_term<POT>(lj, dx, dy, dz, pi.w * pj.w, 1.f, f, e, w) && ncl < kMaxClose) close[ncl++] = ent;
+  }
+  if (ncl > 0) {
+    const Rep &R = d.rep[ri];
+    const float4 li = d.rlo[i];
+    for (int c = 0; c < ncl; ++c) {
+      const uint32_t ent = close[c];
+      const int j = entry_atom(ent);
+      const float4 pj = rel[j];
+      const float4 lj4 = d.rlo[j];
+      float dx, dy, dz;
+      disp(ent, pj, dx, dy, dz);
+      mixed_term<POT>(lj, dx, dy, dz, pi.w * pj.w, -1.f, f, e, w);
+      int ox, oy, oz;
+      entry_image(ent, ox, oy, oz);
+      dx = exact_disp(pi.x, li.x, pj.x, lj4.x, (float)ox, R.edge_h, R.edge_l);
+      dy = exact_disp(pi.y, li.y, pj.y, lj4.y, (float)oy, R.edge_h, R.edge_l);
+      dz = exact_disp(pi.z, li.z, pj.z, lj4.z, (float)oz, R.edge_h, R.edge_l);
+      mixed_term<POT>(lj, dx, dy, dz, pi.w * pj.w, 1.f, f, e, w);
+    }
+  }
+  store_pair_out<float>(d, i, f, e, w);
 }
 
 // ---------------------------------------------------- reduce and sample
@@ -1082,7 +1232,7 @@ __global__ void k_init_df(Sys d) {
     const Rep &R = rep_of(d, i);
     const int nc = R.nc;
     int ci[3];
-    float oh[3];
+    float oh[3], ol[3];
     for (int a = 0; a < 3; ++a) {
       double x = d.rB[a * n + i];
       x -= R.L * floor(x / R.L);
@@ -1093,12 +1243,13 @@ __global__ void k_init_df(Sys d) {
       ci[a] = c;
       const dfloat off = df_from_double(x - (c + 0.5) * R.edge);
       oh[a] = off.h;
-      d.offl[a * n + i] = off.l;
+      ol[a] = off.l;
       const dfloat v = df_from_double(d.vB[a * n + i]);
       d.vh[a * n + i] = v.h;
       d.vl[a * n + i] = v.l;
     }
     rel[i] = make_float4(oh[0], oh[1], oh[2], (float)d.charge[type_of(d, i)]);
+    d.rlo[i] = make_float4(ol[0], ol[1], ol[2], 0.f);
     d.cpk[i] = pack_cell(ci[0], ci[1], ci[2]);
   }
 }
@@ -1124,8 +1275,10 @@ __global__ void k_unsort(Sys d, double *r, double *v, double *F, double *epot, d
           x = d.r[a * n + i];
         } else {
           const float4 o = static_cast<const float4 *>(d.rel)[i];
+          const float4 lo = d.rlo[i];
           const float oh = a == 0 ? o.x : (a == 1 ? o.y : o.z);
-          x = (cc[a] + 0.5) * R.edge + df_to_double(dfloat{oh, d.offl[a * n + i]});
+          const float ol = a == 0 ? lo.x : (a == 1 ? lo.y : lo.z);
+          x = (cc[a] + 0.5) * R.edge + df_to_double(dfloat{oh, ol});
         }
         x -= R.L * floor(x / R.L);
         if (x >= R.L) x -= R.L;
@@ -1204,7 +1357,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_build_staged(Sys d, LJ<TF> lj) {
               tag = stag[wl][k];
               const TF dx = pi.x - t.x, dy = pi.y - t.y, dz = pi.z - t.z;
               const TF r2 = dx * dx + dy * dy + dz * dz;
-              acc = r2 < lj.rlist2 && (int)(tag & 0x07ffffffu) != ii;
+              acc = r2 < lj.rlist2 && entry_atom(tag) != ii;
             }
             const unsigned m = __ballot_sync(0xffffffffu, acc);
             const int pos = c0 + __popc(m & below);
@@ -1249,7 +1402,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_build_staged(Sys d, LJ<TF> lj) {
                 t.z = pj.z + oz * edge;
                 t.w = TF(0);
                 sxyz[wl][fill + u] = t;
-                stag[wl][fill + u] = (uint32_t)j | ((uint32_t)((ox + 1) + 3 * row) << 27);
+                stag[wl][fill + u] = list_entry(j, ox, oy, oz);
               }
             }
             fill += take;
@@ -1261,10 +1414,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_build_staged(Sys d, LJ<TF> lj) {
       if (fill > 0) flush();
       s = e;
     }
-    if (a0 + lane < a1 && rebuilds(d, d.rep_of_atom[a0 + lane])) {
-      d.nnb[a0 + lane] = min(cnt, d.maxnb);
-      if (cnt > d.maxnb) atomicOr(d.err, ERR_NBR_OVERFLOW);
-    }
+    if (a0 + lane < a1 && rebuilds(d, d.rep_of_atom[a0 + lane])) d.nnb[a0 + lane] = list_count(d, cnt);
   }
 }
 
@@ -1324,7 +1474,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_build_ip(Sys d, LJ<TF> lj) {
           const int j0 = d.cellstart[rb + jx], j1 = d.cellstart[rb + jx + 1];
           const int ox = ux - cx;  // this lane's image offset (|ox| <= 1 for an accepted j)
           const TF offx = ox * edge;
-          const uint32_t code = (uint32_t)((ox + 1) + 3 * row) << 27;
+          const int oxe = max(-1, min(1, ox));
           for (int j = j0; j < j1; ++j) {
             const V4 pj = Vec4<TF>::load(rel + j);
             V4 t;
@@ -1334,17 +1484,14 @@ __global__ void __launch_bounds__(WARPS * 32) k_build_ip(Sys d, LJ<TF> lj) {
             const TF dx = pi.x - t.x, dy = pi.y - t.y, dz = pi.z - t.z;
             const TF r2 = dx * dx + dy * dy + dz * dz;
             if (in && r2 < lj.rlist2 && (int64_t)j != i) {
-              if (cnt < d.maxnb) col[(int64_t)cnt * 32] = (uint32_t)j | code;
+              if (cnt < d.maxnb) col[(int64_t)cnt * 32] = list_entry(j, oxe, oy, oz);
               ++cnt;
             }
           }
         }
       }
     }
-    if (mine) {
-      d.nnb[i] = min(cnt, d.maxnb);
-      if (cnt > d.maxnb) atomicOr(d.err, ERR_NBR_OVERFLOW);
-    }
+    if (mine) d.nnb[i] = list_count(d, cnt);
   }
 }
 
@@ -1414,13 +1561,20 @@ LJ<TF> lj_of(const md_params &p) {
   LJ<TF> lj;
   const double sr = p.sigma / p.rc;
   const double sr6 = sr * sr * sr * sr * sr * sr;
-  lj.eps4 = (TF)(4.0 * p.eps);
-  lj.eps24 = (TF)(24.0 * p.eps);
-  lj.sig2 = (TF)(p.sigma * p.sigma);
+  const double s6 = p.sigma * p.sigma * p.sigma * p.sigma * p.sigma * p.sigma;
+  lj.c12 = (TF)(4.0 * p.eps * s6 * s6);
+  lj.c6 = (TF)(4.0 * p.eps * s6);
+  lj.f12 = (TF)(48.0 * p.eps * s6 * s6);
+  lj.f6 = (TF)(24.0 * p.eps * s6);
   lj.rc2 = (TF)(p.rc * p.rc);
   lj.ushift = (TF)(p.shift ? 4.0 * p.eps * (sr6 * sr6 - sr6) : 0.0);
   const double rl = p.rc + (p.pair_mode == MD_PAIR_VERLET ? p.skin : 0.0);
   lj.rlist2 = (TF)(rl * rl);
+  // mixed-form Lennard-Jones: pairs closer than 1.05 sigma (|dF/dr| > 200
+  // eps/sigma^2) get the displacement rounded once from the double-float
+  // offsets; none in FP64 or for the ionic potential
+  const double rclose = (std::is_same<TF, float>::value && p.potential == MD_POT_LJ) ? kRClose * p.sigma : 0.0;
+  lj.rclose2 = (TF)(rclose * rclose);
   lj.A = (TF)p.buck_A;
   lj.inv_rho = (TF)(p.buck_rho > 0 ? 1.0 / p.buck_rho : 0.0);
   lj.C6 = (TF)p.buck_C;
@@ -1509,9 +1663,12 @@ int launch_rebuild(md_handle *h, cudaStream_t s) {
 template <typename TF, int POT>
 void launch_pair_pot(const md_handle *h, cudaStream_t s) {
   const Sys &d = h->d;
-  if (h->prm.pair_mode == MD_PAIR_VERLET)
-    k_pair_list<TF, POT><<<ceil_div(d.n, h->pair_threads), h->pair_threads, 0, s>>>(d, lj_of<TF>(h->prm));
-  else
+  if (h->prm.pair_mode == MD_PAIR_VERLET) {
+    if constexpr (std::is_same<TF, float>::value)
+      k_pair_mixed<POT><<<ceil_div(d.n, h->pair_threads), h->pair_threads, 0, s>>>(d, lj_of<float>(h->prm));
+    else
+      k_pair_list<TF, POT><<<ceil_div(d.n, h->pair_threads), h->pair_threads, 0, s>>>(d, lj_of<TF>(h->prm));
+  } else
     k_cells<TF, POT><<<std::min(ceil_div(d.ncell, kCellWarps), 152 * 16), kCellWarps * 32, 0, s>>>(
         d, lj_of<TF>(h->prm));
 }
@@ -1535,7 +1692,7 @@ int launch_pair(md_handle *h, cudaStream_t s) {
     a.n = d.n;
     a.cpk = d.cpk;
     a.rel = d.rel;
-    a.offl = d.offl;
+    a.rlo = d.rlo;
     a.edge = h->reps[0].edge;
     a.cellstart = d.cellstart;
     a.nc = h->reps[0].nc;
@@ -1869,8 +2026,8 @@ int validate_replicas(const md_params *p, const md_replica *reps, int count, int
           }
     }
   }
-  if (total >= (int64_t(1) << 27)) {
-    set_error("md_init: %lld atoms in total; at most 2^27 - 1", (long long)total);
+  if (total >= (int64_t(1) << 26)) {  // 26 bits of atom index per neighbour-list entry
+    set_error("md_init: %lld atoms in total; at most 2^26 - 1", (long long)total);
     return MD_EINVAL;
   }
   return MD_OK;
@@ -1893,7 +2050,7 @@ void release(md_handle *h) {
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   Sys &d = h->d;
-  void *ptrs[] = {d.r, d.v, d.offl, d.vh, d.vl, d.F, d.epot, d.W, d.rel, d.relb, d.vbuf, d.id, d.type,
+  void *ptrs[] = {d.r, d.v, d.rlo, d.vh, d.vl, d.F, d.epot, d.W, d.rel, d.relb, d.vbuf, d.id, d.type,
                   d.cpk, d.rB, d.vB, d.idB, d.typeB, d.cellB, d.slot, d.perm, d.cellcount, d.cellstart,
                   d.nbr, d.nnb, d.partials, d.counter, d.obs, d.st, d.rebuild, d.err, h->d_out, h->d_rep,
                   h->d_rep_of_atom, h->d_rep_of_cell, h->d_rep_of_block, h->d_lam};
@@ -2046,7 +2203,7 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
     OTF_CUDA(cudaMalloc(&d.r, 3 * n * sizeof(double)));
     OTF_CUDA(cudaMalloc(&d.v, 3 * n * sizeof(double)));
   } else {
-    OTF_CUDA(cudaMalloc(&d.offl, 3 * n * sizeof(float)));
+    OTF_CUDA(cudaMalloc(&d.rlo, n * sizeof(float4)));
     OTF_CUDA(cudaMalloc(&d.vh, 3 * n * sizeof(float)));
     OTF_CUDA(cudaMalloc(&d.vl, 3 * n * sizeof(float)));
   }
@@ -2247,8 +2404,8 @@ int md_init(const md_params *p, const md_system *s, void *cuda_stream, md_handle
     return MD_EINVAL;
   }
   *out = nullptr;
-  if (p->n < 2 || p->n >= (1 << 27) || !(p->box > 0)) {
-    set_error("md_init: n must be in [2, 2^27) and box positive");
+  if (p->n < 2 || p->n >= (1 << 26) || !(p->box > 0)) {
+    set_error("md_init: n must be in [2, 2^26) and box positive");
     return MD_EINVAL;
   }
   if (!s->r || !s->v) {

@@ -1730,4 +1730,64 @@ int gk_tail_features(const double *c_sigma, const double *c_q, int64_t ld, int64
   return MD_OK;
 }
 
+int gk_tail_box(const double *temperature, const double *density, int64_t n, gk_tail_rule *rule) {
+  clear_error();
+  if (!temperature || !density || !rule || n < 1) {
+    set_error("gk_tail_box: null argument or no runs");
+    return MD_EINVAL;
+  }
+  rule->T_min = rule->T_max = temperature[0];
+  rule->rho_min = rule->rho_max = density[0];
+  for (int64_t r = 1; r < n; ++r) {
+    rule->T_min = std::min(rule->T_min, temperature[r]);
+    rule->T_max = std::max(rule->T_max, temperature[r]);
+    rule->rho_min = std::min(rule->rho_min, density[r]);
+    rule->rho_max = std::max(rule->rho_max, density[r]);
+  }
+  return MD_OK;
+}
+
+int gk_tail_rms_rel(const double *a, const double *b, const double *w, int64_t n, double *out) {
+  clear_error();
+  if (!a || !b || !out || n < 1) {
+    set_error("gk_tail_rms_rel: null argument or no values");
+    return MD_EINVAL;
+  }
+  double s = 0.0;
+  for (int64_t r = 0; r < n; ++r) {
+    if (!(b[r] != 0.0)) {
+      set_error("gk_tail_rms_rel: reference value %lld is zero", (long long)r);
+      return MD_EINVAL;
+    }
+    const double e = (a[r] - b[r]) / b[r];
+    s += e * e * (w ? w[r] : 1.0);
+  }
+  *out = std::sqrt(s / (double)n);
+  return MD_OK;
+}
+
+int gk_tail_choose(const gk_tail_rule *rule, const double *temperature, const double *density, const double *steps,
+                   const double *net, const double *own, int64_t nruns, double *out, int32_t *used) {
+  clear_error();
+  if (!rule || !temperature || !density || !steps || !net || !own || !out || nruns < 0) {
+    set_error("gk_tail_choose: null argument");
+    return MD_EINVAL;
+  }
+  for (int64_t r = 0; r < nruns; ++r) {
+    if (!(steps[r] > 0.0)) {
+      set_error("gk_tail_choose: run %lld has no correlated steps", (long long)r);
+      return MD_EINVAL;
+    }
+    const bool inside = temperature[r] >= rule->T_min && temperature[r] <= rule->T_max &&
+                        density[r] >= rule->rho_min && density[r] <= rule->rho_max;
+    const double root = std::sqrt(steps[r]);
+    for (int k = 0; k < 2; ++k) {
+      const bool use = inside && rule->short_coeff[k] / root > rule->net_error[k];
+      out[2 * r + k] = use ? net[2 * r + k] : own[2 * r + k];
+      if (used) used[2 * r + k] = use ? 1 : 0;
+    }
+  }
+  return MD_OK;
+}
+
 }  // extern "C"

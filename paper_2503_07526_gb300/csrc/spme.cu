@@ -1,8 +1,9 @@
 // Smooth particle-mesh Ewald (Essmann et al. 1995; arXiv 2503.07526
 // Sec. 5.3 and Appendix B) for the ionic-melt path.  Per step:
 //   1. spread: every atom adds q M_n(u_x - k_x) M_n(u_y - k_y) M_n(u_z - k_z)
-//      to the n^3 mesh points around it (fixed-point 64-bit integer atomics,
-//      so the sums do not depend on the order of the atoms);
+//      to the n^3 mesh points around it (fixed-point integer atomics, so
+//      the sums do not depend on the order of the atoms: 64-bit words at a
+//      scale of 2^40 in the mixed form, 128-bit words at 2^80 in FP64);
 //   2. forward real-to-complex FFT of the mesh (cuFFT);
 //   3. multiply by B(m) C(m) (phi mesh) and by B(m) C(m) h(m) (psi mesh),
 //      C(m) = exp(-pi^2 m^2 / alpha^2) / (pi V m^2),
@@ -26,7 +27,11 @@
 namespace otf {
 namespace {
 
-constexpr double kFix = 1099511627776.0;  // 2^40: fixed-point scale of the charge mesh
+constexpr double kFix = 1099511627776.0;  // 2^40: fixed-point scale of the mixed form's charge mesh
+// FP64 form: each mesh point is a 128-bit two's-complement integer (a low
+// and a high 64-bit word) counting units of 2^-80 of a charge, so the
+// quantisation (2^-81 per added value) is far below FP64 rounding and the
+// range (2^47 charges) cannot be reached.
 constexpr double kPi = 3.14159265358979323846;
 
 template <typename T>
@@ -51,7 +56,31 @@ struct Cplx<double> {
 };
 
 __device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * (float)kFix); }
-__device__ __forceinline__ long long to_fix(double v) { return __double2ll_rn(v * kFix); }
+
+// Adds v to mesh point idx of a mesh of K3 points: one 64-bit word per point
+// (mixed form) or 128 bits per point, low words [0, K3) and high words
+// [K3, 2 K3) (FP64).  The 128-bit addend is round(v 2^80) split as
+// hi 2^64 + lo with lo in [0, 2^64); the carry out of the low word is the
+// unsigned wrap of that add, so every order of the adds gives the same
+// integer.
+__device__ __forceinline__ void mesh_add(unsigned long long *Q, int64_t idx, int64_t K3, float v) {
+  const long long f = to_fix(v);
+  if (f != 0) atomicAdd(Q + idx, (unsigned long long)f);
+}
+__device__ __forceinline__ void mesh_add(unsigned long long *Q, int64_t idx, int64_t K3, double v) {
+  if (v == 0.0) return;
+  const double t = v * 65536.0;  // v 2^16: the high word's units (exact)
+  const double fh = floor(t);
+  // t - fh is exact and at most 1 - 2^-53, so its product with 2^64 is at
+  // most 2^64 - 2^11 and rounds to an integer below 2^64
+  const unsigned long long l = __double2ull_rn((t - fh) * 18446744073709551616.0);
+  long long hi = (long long)fh;
+  if (l != 0ull) {
+    const unsigned long long old = atomicAdd(Q + idx, l);
+    if (old + l < old) hi += 1;  // carry
+  }
+  if (hi != 0) atomicAdd(Q + K3 + idx, (unsigned long long)hi);
+}
 
 // Mesh coordinates of atom i: base mesh point and fraction per axis, from
 // the cell index and the offset from the cell centre (FP64).  The base is
@@ -65,10 +94,15 @@ __device__ __forceinline__ void mesh_coords(const SpmeAtoms &a, int64_t i, doubl
   const int c = a.cpk[i];
   const int cc[3] = {c & 1023, (c >> 10) & 1023, c >> 20};
   const double off[3] = {(double)r.x, (double)r.y, (double)r.z};
+  float lo[3] = {0.f, 0.f, 0.f};
+  if constexpr (std::is_same<T, float>::value) {
+    const float4 l4 = a.rlo[i];
+    lo[0] = l4.x, lo[1] = l4.y, lo[2] = l4.z;
+  }
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
     double x = (cc[ax] + 0.5) * a.edge + off[ax];
-    if constexpr (std::is_same<T, float>::value) x += (double)a.offl[ax * a.n + i];
+    if constexpr (std::is_same<T, float>::value) x += (double)lo[ax];
     const double u = x * kl;
     const int b = (int)floor(u);
     base[ax] = b;
@@ -153,6 +187,7 @@ struct Two<double> {
 template <typename T, int N, bool TILE>
 __device__ __forceinline__ void spread_atom(const int (&base)[3], const T (&frac)[3], T q, unsigned long long *dst,
                                             int *hi, int *lo, int K, int ox, int oy, int oz, int ey, int ez) {
+  const int64_t K3 = (int64_t)K * K * K;
   T wx[N], wy[N], wz[N], d1[N], d2[N];
   spline<T, N, false>(frac[0], wx, d1, d2);
   spline<T, N, false>(frac[1], wy, d1, d2);
@@ -169,14 +204,14 @@ __device__ __forceinline__ void spread_atom(const int (&base)[3], const T (&frac
       const int64_t row = TILE ? ((int64_t)ix * ey + iy) * ez : ((int64_t)ix * K + iy) * K;
 #pragma unroll
       for (int t2 = 0; t2 < N; ++t2) {
-        const long long v = to_fix(qxy * wz[t2]);
         if (TILE) {
           // two native 32-bit shared adds: the high part (arithmetic shift)
           // and the low 20 bits; neither can overflow over one chunk
+          const long long v = to_fix((float)(qxy * wz[t2]));
           atomicAdd(hi + row + iz[t2], (int)(v >> kLoBits));
           atomicAdd(lo + row + iz[t2], (int)(v & ((1ll << kLoBits) - 1)));
         } else {
-          atomicAdd(dst + row + iz[t2], (unsigned long long)v);
+          mesh_add(dst, row + iz[t2], K3, qxy * wz[t2]);
         }
       }
     }
@@ -287,10 +322,7 @@ __global__ void __launch_bounds__(kRowThreads) k_spme_spread(SpmeAtoms a, int K,
           const int lx = col / tl.ey, ly = col % tl.ey;
           const int64_t g0 = ((int64_t)wrap_near(tl.ox + lx, K) * K + wrap_near(tl.oy + ly, K)) * K;
           const T *cz = tile + (int64_t)col * ezp;
-          for (int z = 0; z < tl.ez; ++z) {
-            const long long v = to_fix(cz[z]);
-            if (v != 0) atomicAdd(Qi + g0 + wrap_near(tl.oz + z, K), (unsigned long long)v);
-          }
+          for (int z = 0; z < tl.ez; ++z) mesh_add(Qi, g0 + wrap_near(tl.oz + z, K), (int64_t)K * K * K, cz[z]);
         }
       } else if (live) {
         spread_atom<T, N, false>(base, frac, q, Qi, nullptr, nullptr, K, 0, 0, 0, 0, 0);
@@ -302,8 +334,12 @@ __global__ void __launch_bounds__(kRowThreads) k_spme_spread(SpmeAtoms a, int K,
 
 template <typename T>
 __global__ void k_spme_unfix(const unsigned long long *Qi, T *Qr, int64_t total) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x)
-    Qr[k] = (T)((double)(long long)Qi[k] * (1.0 / kFix));
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (std::is_same<T, double>::value)  // hi 2^-16 + lo 2^-80
+      Qr[k] = (double)(long long)Qi[total + k] * (1.0 / 65536.0) + (double)Qi[k] * 8.271806125530277e-25;
+    else
+      Qr[k] = (T)((double)(long long)Qi[k] * (1.0 / kFix));
+  }
 }
 
 // The two convolutions on the half spectrum [K][K][K/2+1].
@@ -509,7 +545,7 @@ int Spme::create(const SpmeParams &p, bool fp64, cudaStream_t st) {
     for (int k = 0; k <= p.order - 2; ++k) s += Mk[k + 1] * std::polar(1.0, 2.0 * kPi * m * k / K);
     bm[m] = 1.0 / std::norm(s);
   }
-  OTF_CUDA(cudaMalloc(&Qi_, sizeof(unsigned long long) * K3));
+  OTF_CUDA(cudaMalloc(&Qi_, sizeof(unsigned long long) * K3 * (fp64 ? 2 : 1)));  // 128-bit points in FP64
   OTF_CUDA(cudaMalloc(&Qr_, ts * K3));
   OTF_CUDA(cudaMalloc(&phi_, ts * K3));
   OTF_CUDA(cudaMalloc(&psi_, ts * K3));
@@ -552,7 +588,7 @@ int Spme::run_t(const SpmeAtoms &a, T *F, T *epot, T *W, cudaStream_t st) {
   int rs = cufft_ok(cufftSetStream(fwd_, st), "cufftSetStream");
   if (!rs) rs = cufft_ok(cufftSetStream(inv_, st), "cufftSetStream");
   if (rs) return rs;
-  OTF_CUDA(cudaMemsetAsync(Qi_, 0, sizeof(unsigned long long) * K3, st));
+  OTF_CUDA(cudaMemsetAsync(Qi_, 0, sizeof(unsigned long long) * K3 * (fp64_ ? 2 : 1), st));
   if (!a.cellstart || a.nc < 1) {
     set_error("spme: the cell list is missing");
     return MD_EINVAL;

@@ -21,12 +21,12 @@ struct SpmeParams {
 // Atoms as the MD engine holds them: cell-sorted, each with a packed cell
 // index (x | y << 10 | z << 20), its offset from the cell centre (the Vec4
 // record of the pair type, whose w holds the charge; in the mixed form the
-// offset's low words are in offl [3][n]) and a cell edge.
+// offset's low words are in rlo [n]) and a cell edge.
 struct SpmeAtoms {
   int64_t n = 0;
   const int *cpk = nullptr;
   const void *rel = nullptr;
-  const float *offl = nullptr;
+  const float4 *rlo = nullptr;
   double edge = 0.0;
   const int *cellstart = nullptr;  // [nc^3 + 1]: atoms of cell c are [cellstart[c], cellstart[c+1])
   int nc = 0;                      // cells per side

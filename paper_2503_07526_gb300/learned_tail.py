@@ -138,17 +138,24 @@ def generate(specs, short, long, *, precision=_lib.MD_PREC_MIXED, melt_steps=(60
 
 
 class LearnedTail:
-    """The network (3 x 128 tanh, bfloat16 tensor-core products) with what
-    decides where it is used: the temperature-density box of its training
-    set, its error on validation replicas, and a fit of the short-run
-    integral's error against atoms x steps.  Outputs (eta, kappa)."""
+    """The network (3 x 128 tanh, bfloat16 tensor-core products) with the
+    rule that decides where it is used (gk_tail_rule of the C ABI: the
+    temperature-density box of its training set, its error on validation
+    replicas, and the short-run integral's error coefficient).  Outputs
+    (eta, kappa)."""
 
     def __init__(self, *, depth=3, batch=128, lr=1e-3, weight_decay=1e-3, seed=1, stream=None):
         self.net = _lib.MLP(N_FEATURES, 2, depth=depth, batch=batch, lr=lr, weight_decay=weight_decay, seed=seed,
                             stream=stream)
-        self.box = None
-        self.val_error = None    # rms relative error of (eta, kappa) on the validation replicas
-        self.short_coeff = None  # short-run rms relative error ~ coeff / sqrt(steps)
+        self.rule = None
+
+    @property
+    def val_error(self):
+        return tuple(self.rule.net_error)
+
+    @property
+    def short_coeff(self):
+        return tuple(self.rule.short_coeff)
 
     def fit(self, train, val, epochs, shuffle_seed=1):
         """train, val: dicts as returned by generate() (rows with a
@@ -158,17 +165,18 @@ class LearnedTail:
         X = np.ascontiguousarray(train["X"][tr], dtype=np.float32)
         Y = np.stack([np.log(train["eta_long"][tr]), np.log(train["kappa_long"][tr])], 1).astype(np.float32)
         self.net.fit_scaler(X, Y)
-        self.box = (float(X[:, 130].min()), float(X[:, 130].max()), float(X[:, 131].min()), float(X[:, 131].max()))
+        rule = _lib.gk_tail_box(X[:, 130], X[:, 131])
         hist = self.net.train(X, Y, epochs, shuffle_seed=shuffle_seed)
         va = _usable(val)
         eta, kappa = self._net(val["X"][va])
-        self.val_error = (_rms_rel(eta, val["eta_long"][va]), _rms_rel(kappa, val["kappa_long"][va]))
+        rule.net_error[0] = _lib.gk_tail_rms_rel(eta, val["eta_long"][va])
+        rule.net_error[1] = _lib.gk_tail_rms_rel(kappa, val["kappa_long"][va])
         # the short-run integral's error falls as 1/sqrt(steps), whatever the size
         both = {k: np.concatenate([train[k][tr], val[k][va]])
                 for k in ("eta_short", "kappa_short", "eta_long", "kappa_long", "steps_short")}
-        w = np.sqrt(both["steps_short"])
-        self.short_coeff = tuple(float(np.sqrt(np.mean(((both[k + "_short"] - both[k + "_long"]) /
-                                                        both[k + "_long"] * w) ** 2))) for k in ("eta", "kappa"))
+        for i, k in enumerate(("eta", "kappa")):
+            rule.short_coeff[i] = _lib.gk_tail_rms_rel(both[k + "_short"], both[k + "_long"], both["steps_short"])
+        self.rule = rule
         return hist
 
     def _net(self, X):
@@ -177,17 +185,13 @@ class LearnedTail:
 
     def predict(self, X, eta_short, kappa_short, steps):
         """(eta, kappa, used_eta, used_kappa): per output, the network's value
-        where the run lies in the training box and its own integral (after
-        `steps` correlated steps) is expected to be less accurate than the
-        network; elsewhere the run's own integral."""
+        or the run's own integral, as gk_tail_choose decides."""
         X = np.ascontiguousarray(X, dtype=np.float32)
         eta, kappa = self._net(X)
-        T0, T1, r0, r1 = self.box
-        inside = (X[:, 130] >= T0) & (X[:, 130] <= T1) & (X[:, 131] >= r0) & (X[:, 131] <= r1)
-        w = np.sqrt(np.asarray(steps, dtype=np.float64))
-        use_e = inside & (self.short_coeff[0] / w > self.val_error[0])
-        use_k = inside & (self.short_coeff[1] / w > self.val_error[1])
-        return (np.where(use_e, eta, eta_short), np.where(use_k, kappa, kappa_short), use_e, use_k)
+        out, used = _lib.gk_tail_choose(self.rule, X[:, 130], X[:, 131], steps, np.stack([eta, kappa], 1),
+                                        np.stack([np.asarray(eta_short, dtype=np.float64),
+                                                  np.asarray(kappa_short, dtype=np.float64)], 1))
+        return out[:, 0], out[:, 1], used[:, 0], used[:, 1]
 
 
 def _usable(d):

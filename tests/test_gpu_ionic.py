@@ -10,10 +10,10 @@ alpha = 0.3 / A, order-8 splines on a 16^3 mesh (the chunks of a cell row fit
 the kernels' shared tiles) and on a 32^3 mesh (they do not: the kernels take
 the global mesh directly); units eV, A, amu, e.
 
-Tolerances.  FP64: the charge mesh is summed in 64-bit fixed point with 2^-40
-resolution per contribution (so that the sums do not depend on the order of
-the atomic adds), which leaves ~1e-12 relative in the mesh; 1e-10 normwise
-per array is allowed.  Mixed: FP32 pair terms, FP32 spreading, FFTs and
+Tolerances.  FP64: the charge mesh is summed in 128-bit fixed point with
+2^-80 resolution per contribution (so that the sums do not depend on the
+order of the atomic adds), far below FP64 rounding; 1e-11 normwise per
+array, as for Lennard-Jones.  Mixed: FP32 pair terms, FP32 spreading, FFTs and
 gathers; 2e-5 normwise per force component, as for Lennard-Jones, and 1e-4
 for the per-particle energies and virials (sums of large cancelling
 terms)."""
@@ -82,7 +82,7 @@ def test_forces_energies_virials_match_oracle(pkg, system, precision, mesh):
     g = pkg.System(params(pkg, s, precision, mesh=mesh), s["r"], s["v"], types=s["types"])
     got = g.particles()
     g.close()
-    tol = {0: (1e-10, 1e-10), 1: (2e-5, 1e-4)}[precision]
+    tol = {0: (1e-11, 1e-11), 1: (2e-5, 1e-4)}[precision]
     for key, t in (("F", tol[0]), ("epot", tol[1]), ("W", tol[1])):
         e = rel(got[key], ref[key])
         print(f"precision {precision} mesh {mesh}: {key} {e:.2e}")
@@ -105,7 +105,7 @@ def test_observables_match_oracle(pkg, system, precision, oracle_mod):
     mass_of = np.asarray(MASSES)[s["types"]]
     ref = reference(s, K)
     want = oracle_mod.observables(s["L"] ** 3, mass_of, s["v"], ref["epot"], ref["W"])
-    tol = 1e-10 if precision == 0 else 1e-4
+    tol = 1e-11 if precision == 0 else 1e-4
     assert o["U"] == pytest.approx(want[0], rel=tol)
     assert o["K"] == pytest.approx(want[1], rel=1e-12 if precision == 0 else 1e-6)
     assert rel(o["sigma"], want[3:9]) <= tol
