@@ -831,9 +831,9 @@ def cpu_baseline(st, s, budget_s=20.0):
         if el > budget_s or steps >= 50:
             break
     return {"value": n * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} whole steps of the {n:,}-atom workload (link-cell forces, integration, "
-                      f"observables, stress/heat-flux and per-atom VACF correlators) after 1 warm-up step, "
-                      f"{el:.1f} s"}
+            "sample": f"{steps} whole steps of the {n:,}-atom workload from the melted state the GPU runs "
+                      f"(link-cell forces, integration, observables, stress/heat-flux and per-atom VACF "
+                      f"correlators) after 1 warm-up step, {el:.1f} s"}
 
 
 def run_reference(args):
@@ -865,7 +865,8 @@ def run_reference(args):
            "impl": "reference",
            "config": {"workload": workload_name(n) + " (fcc start, not melted)", "n_atoms": n, "precision": "fp64"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": f"{args.steps} timed steps of the full workload after {args.warmup} warm-up"},
+                            "sample": f"{args.steps} timed steps of the full workload from the fcc start (not melted) "
+                                      f"after {args.warmup} warm-up"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
