@@ -229,7 +229,8 @@ def run_ours(args):
     s, st = prepare_state(pkg, synth, seed=replicas.replica_seed(1, rank), cells=args.cells,
                           melt_steps=100 if args.quick else 600)
     n, L = s["n"], s["L"]
-    p = pkg.make_params(n, L, rc=RC, dt=DT, skin=args.skin, precision=pkg.MD_PREC_MIXED,
+    pair_mode = pkg.MD_PAIR_TILES if args.pair == "tiles" else pkg.MD_PAIR_VERLET
+    p = pkg.make_params(n, L, rc=RC, dt=DT, skin=args.skin, precision=pkg.MD_PREC_MIXED, pair_mode=pair_mode,
                         list_build=args.list_build, **SPEC)
     g = pkg.System(p, st["r"], st["v"])
     g.step(args.warmup)
@@ -325,7 +326,8 @@ def run_ours(args):
     else:
         flops = PAIR_FLOP_PER_ATOM * n * ktimes["pair"][1]
         achieved = flops / (ktimes["pair"][0] / 1e3) / 1e12
-        roof = {"kernel": "k_pair_mixed (LJ forces + per-particle energy and virial, mixed form)", "bound": "alu",
+        kname = "k_pair_tile" if args.pair == "tiles" else "k_pair_mixed"
+        roof = {"kernel": f"{kname} (LJ forces + per-particle energy and virial, mixed form)", "bound": "alu",
                 "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak_tflops,
                 "peak_source": f"measured in this run: md_fp32_peak ({fp32['from']}), median SM clock "
@@ -882,6 +884,8 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the replica ensemble and time-to-viscosity")
     ap.add_argument("--cells", type=int, default=CELLS, help="fcc cells per side (4 cells^3 atoms)")
     ap.add_argument("--skin", type=float, default=SKIN, help="Verlet skin of the timed system (sigma)")
+    ap.add_argument("--pair", default="tiles", choices=["tiles", "verlet"],
+                    help="mixed-form pair path of the timed system: tile windows or global Verlet lists")
     ap.add_argument("--list-build", type=int, default=0,
                     help="neighbour-list build of the timed system: 0 default, 1 j-parallel, 2 i-parallel, 3 staged")
     ap.add_argument("--quick", action="store_true", help="short melt, timed region only (for profilers)")

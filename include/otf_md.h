@@ -87,6 +87,15 @@ extern "C" {
 #define MD_PAIR_VERLET 0 /* Verlet neighbour lists built from link cells,
                             rebuilt when an atom has moved skin/2 */
 #define MD_PAIR_CELLS 1  /* direct link-cell evaluation every step */
+#define MD_PAIR_TILES 2  /* mixed-precision Lennard-Jones only: Verlet lists
+                            (same skin rule) over tiles of at most 3 x 2 x 2
+                            cells; each tile's CTA stages the tile and its
+                            one-cell shell in shared memory, in the tile's own
+                            frame, and the lists hold 16-bit offsets into that
+                            window.  md_init returns MD_EINVAL when the
+                            expected window exceeds the shared-memory capacity
+                            (4,095 atoms); a window that outgrows it during a
+                            run stops md_step with MD_ESTATE. */
 
 /* Multiple-tau parameters of one correlator (Sec. 2.2: b blocks of p points
  * with block averages of m samples; u = update interval in MD steps).
@@ -162,9 +171,13 @@ typedef struct {
   int32_t build_warps;    /* warps per CTA of the neighbour-list build */
   int32_t max_neighbors;  /* neighbour-list capacity per atom */
   int64_t atoms, cells;   /* totals over all replicas */
-  int32_t build_kind;     /* 0: j-parallel list build, 1: i-parallel, 2: staged */
+  int32_t build_kind;     /* 0: j-parallel list build, 1: i-parallel, 2: staged,
+                             3: tile windows (MD_PAIR_TILES) */
   int64_t vacf_input_bytes; /* device bytes of the per-atom velocity correlator's
                                input slots (0 when that correlator is off) */
+  int64_t tiles;            /* MD_PAIR_TILES: tiles (CTAs of the pair kernel); else 0 */
+  int32_t window_capacity;  /* MD_PAIR_TILES: shared-memory window slots per tile */
+  int32_t tile_threads;     /* MD_PAIR_TILES: threads per tile CTA */
 } md_config;
 
 /* Observables of the last completed step (Sec. 2.3). */

@@ -18,6 +18,7 @@ from ._lib import (  # noqa: F401
     MD_MEM_DEVICE,
     MD_MEM_HOST,
     MD_PAIR_CELLS,
+    MD_PAIR_TILES,
     MD_PAIR_VERLET,
     MD_POT_BUCK_EWALD,
     MD_POT_LJ,

@@ -18,7 +18,7 @@ MD_OK, MD_EINVAL, MD_ENOMEM, MD_ECUDA, MD_ESTATE, MD_ETIMEOUT, MD_ECAP = 0, -1, 
 MD_PREC_FP64, MD_PREC_MIXED = 0, 1
 MD_MEM_HOST, MD_MEM_DEVICE = 0, 1
 MD_CORR_STRESS, MD_CORR_HEATFLUX, MD_CORR_VACF, MD_CORR_MASSFLUX = 0, 1, 2, 3
-MD_PAIR_VERLET, MD_PAIR_CELLS = 0, 1
+MD_PAIR_VERLET, MD_PAIR_CELLS, MD_PAIR_TILES = 0, 1, 2
 MD_POT_LJ, MD_POT_BUCK_EWALD = 0, 1
 MD_K_NAMES = ("integrate", "rebuild", "pair", "reduce", "vacf", "spme")
 MD_NKCLASS = 6
@@ -60,7 +60,8 @@ class md_replica(C.Structure):
 class md_config(C.Structure):
     _fields_ = [("replicas", C.c_int32), ("pair_threads", C.c_int32), ("build_warps", C.c_int32),
                 ("max_neighbors", C.c_int32), ("atoms", C.c_int64), ("cells", C.c_int64),
-                ("build_kind", C.c_int32), ("vacf_input_bytes", C.c_int64)]
+                ("build_kind", C.c_int32), ("vacf_input_bytes", C.c_int64), ("tiles", C.c_int64),
+                ("window_capacity", C.c_int32), ("tile_threads", C.c_int32)]
 
 
 class gk_tail_rule(C.Structure):
@@ -394,7 +395,8 @@ class System:
         return dict(replicas=c.replicas, pair_threads=c.pair_threads, build_warps=c.build_warps,
                     build_kind=c.build_kind,
                     max_neighbors=c.max_neighbors, atoms=c.atoms, cells=c.cells,
-                    vacf_input_bytes=c.vacf_input_bytes)
+                    vacf_input_bytes=c.vacf_input_bytes, tiles=c.tiles, window_capacity=c.window_capacity,
+                    tile_threads=c.tile_threads)
 
     def step(self, nsteps):
         _check(lib().md_step(self._h, int(nsteps)))

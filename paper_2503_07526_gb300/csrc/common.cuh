@@ -21,6 +21,7 @@ enum : unsigned {
   ERR_NBR_OVERFLOW = 2u,   // an atom has more neighbours than the list holds
   ERR_BAD_TYPE = 4u,       // an atom type outside [0, ntypes)
   ERR_PUSH_BACKLOG = 8u,   // more velocity pushes waiting than one blocked pass applies
+  ERR_WINDOW = 16u,        // a tile's shared-memory window outgrew its capacity (MD_PAIR_TILES)
 };
 
 #define OTF_CUDA(call)                                                                       \

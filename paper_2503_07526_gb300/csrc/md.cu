@@ -37,6 +37,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "corr.cuh"
 #include "spme.cuh"
 
@@ -85,6 +87,14 @@ struct Rep {
   float edge_h, edge_l;  // double-float edge (mixed form)
 };
 
+// One tile of the MD_PAIR_TILES path: cells [x0, x0 + bx) x [y0, y0 + by) x
+// [z0, z0 + bz) of replica rep (a tile never wraps around the box).
+struct Tile {
+  int rep;
+  unsigned short x0, y0, z0;
+  unsigned char bx, by, bz, pad;
+};
+
 struct Sys {
   int64_t n, ncell, maxchunks;  // totals over all replicas
   int nrep, ntypes, maxnb, always_rebuild, vacf_u;
@@ -114,8 +124,15 @@ struct Sys {
   // rebuild scratch (24 bytes per atom each)
   double *rB, *vB;
   int *idB, *typeB, *cellB, *slot, *perm, *cellcount, *cellstart;
-  uint32_t *nbr;             // [n/32 chunks][maxnb][32]: j | (image code << 27)
-  int *nnb;                  // list length per atom
+  uint32_t *nbr;             // [n/32 chunks][maxnb][32]: j << 6 | image code
+  int *nnb;                  // list length per atom (MD_PAIR_TILES: far | close << 16)
+  // MD_PAIR_TILES
+  const Tile *tiles;         // [ntiles]
+  int ntiles, wcap;          // tiles; window slots per tile (slot 0: the far-away dummy)
+  uint4 *tnb;                // [maxnb / 8][n]: far entries, eight 16-bit window byte offsets per block
+  uint4 *tcl;                // [kMaxCloseT / 8][n]: close entries, the same way
+  struct TileWin *trec;      // [ntiles]: window layout of each tile at the last list build
+  unsigned char *tcell;      // [ntiles][wcap + kWinPad]: window cell of each slot, the same
   // reductions and flags
   double *partials;          // [reduction CTAs][kNRed]
   unsigned *counter;         // [nrep] finished CTAs per replica
@@ -130,6 +147,7 @@ struct LJ {
   TF c12, c6, f12, f6;  // 4 eps sig^12, 4 eps sig^6, 12 c12, 6 c6
   TF rc2, ushift, rlist2;
   TF rclose2;           // mixed form: pairs closer than r_close get the rounded-once displacement
+  TF rcb2;              // MD_PAIR_TILES: (r_close + skin)^2, the list build's close segment
   // MD_POT_BUCK_EWALD: A exp(-r/rho) - C/r^6 + ke qq erfc(alpha r)/r
   TF A, inv_rho, C6, alpha, c2, ke;  // c2 = 2 alpha / sqrt(pi)
 };
@@ -945,6 +963,474 @@ __global__ void __launch_bounds__(kMaxPairThreads, 5) k_pair_mixed(Sys d, LJ<flo
   store_pair_out<float>(d, i, f, e, w);
 }
 
+// ------------------------------------------ tile windows (MD_PAIR_TILES)
+//
+// Mixed-form Lennard-Jones pairs over shared-memory windows.  A replica's
+// cells are cut into tiles of at most kTileExt cells per axis (segments of
+// nearly equal length that never wrap); a tile's window is its cells plus
+// the one-cell shell around them, (bx+2)(by+2)(bz+2) cells enumerated
+// z-major, then y, then x, so the three x-neighbours of a cell are three
+// consecutive window cells whose atoms fill one contiguous slot range.  The
+// CTA of a tile stages every window atom in shared memory once per launch:
+// its coordinate in the tile's own frame (origin at the tile centre, so
+// |X| < 8 and the FP32 word keeps a resolution of 2^-21; the shell's
+// periodic images come out right by construction) as a float4 X_h, and the
+// double-float remainder X_l = x - X_h as three halves scaled by 2^20
+// (|X_l| < 2^-20, kept to ~2^-31 absolute).  Slot 0 holds a dummy atom 10^9
+// away, the padding entry of the lists.
+//
+// An atom's Verlet list holds the byte offsets (16 bits: slots < 4096) of
+// its neighbours' slots in two segments: close entries (within r_close +
+// skin at the build, so possibly within r_close before the next build),
+// evaluated from the double-float coordinates with the displacement rounded
+// once, and far entries, evaluated from X_h alone, two per 32-bit word and
+// padded with dummies to a multiple of four.  The pair loop reads its
+// neighbours from shared memory (no global gathers, no image offsets) and
+// streams its list words with one block of lookahead.
+constexpr int kTileExt[3] = {3, 2, 2};  // largest tile extent along x, y, z (cells)
+constexpr int kMaxWinCells = 128;       // (3+2)^3 = 125 for tiles up to 3 x 3 x 3
+constexpr int kMaxTileRows = 9;
+constexpr int kMaxCloseT = 16;  // two blocks of eight
+constexpr int kWinMaxSlots = 4096;
+constexpr int kWinPad = 32;  // slots past the capacity that the build's 32-slot test batches may read
+constexpr int kTileThreadsMax = 384;
+constexpr float kLoScale = 1048576.f;  // 2^20
+constexpr float kLoUnscale = 1.f / 1048576.f;
+
+// Dynamic shared memory of the tile kernels: X_h [wcap + kWinPad] float4,
+// then (pair kernel) X_l [wcap + kWinPad] uint2, then the window cell of
+// every slot [wcap + kWinPad] bytes.
+__host__ __device__ constexpr size_t tile_smem(int wcap, bool lo) {
+  return (size_t)(wcap + kWinPad) * (sizeof(float4) + (lo ? sizeof(uint2) : 0) + 1);
+}
+
+// Window of one tile (shared memory).
+struct TileWin {
+  int WX, WY, WZ, nwc;          // window extent in cells, window cells
+  int natoms, nrows, bx, by;    // atoms of the tile (-1: window over capacity), its (y, z) rows, extent
+  int wsum[kMaxWinCells / 32];  // scan scratch
+  int pre[kMaxWinCells + 1];    // first slot of each window cell (pre[nwc]: end)
+  int gs[kMaxWinCells];         // sorted index of each window cell's first atom
+  int cxyz[kMaxWinCells];       // window-cell coordinates wx | wy << 4 | wz << 8
+  float ch[3][5], cl[3][5];     // tile-frame centre of the k-th window cell along each axis (hi, lo)
+  int rpre[kMaxTileRows + 1];   // tile rows: prefix of their atom counts
+  int rslot[kMaxTileRows];      // first slot of each row
+  int rg[kMaxTileRows];         // sorted index of each row's first atom
+};
+
+__device__ __forceinline__ uint2 pack_lo(float x, float y, float z) {
+  const __half2 a = __floats2half2_rn(x * kLoScale, y * kLoScale);
+  const __half2 b = __floats2half2_rn(z * kLoScale, 0.f);
+  return make_uint2(*reinterpret_cast<const unsigned *>(&a), *reinterpret_cast<const unsigned *>(&b));
+}
+__device__ __forceinline__ float3 unpack_lo(uint2 u) {
+  const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+  return make_float3(a.x * kLoUnscale, a.y * kLoUnscale, b.x * kLoUnscale);
+}
+
+// 128- and 64-bit shared loads at a shared-window byte address (the
+// compiler would narrow a float4 whose w goes unused into two loads).
+__device__ __forceinline__ float4 lds4(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint2 lds2(uint32_t a) {
+  uint2 v;
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+  return v;
+}
+
+// Exact rounding error of s = fl(a + b) (Knuth's TwoSum).
+__device__ __forceinline__ float two_sum_err(float a, float b, float s) {
+  const float bb = s - a;
+  return (a - (s - bb)) + (b - bb);
+}
+
+// Window layout of tile tl (every thread of the CTA calls it): a prefix sum
+// over the window cells gives every cell its slot range, every slot learns
+// its cell in a byte map, and thread 0 lists the tile's rows.  False when
+// the window exceeds d.wcap slots (the error word is set, natoms = -1).
+// The layout depends only on the cell sort, so the list build computes it
+// and keeps it for the pair kernel until the next rebuild.
+__device__ bool window_layout(const Sys &d, const Tile &tl, TileWin &W, unsigned char *cellof) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const Rep &R = d.rep[tl.rep];
+  const int nc = R.nc;
+  const int WX = tl.bx + 2, WY = tl.by + 2, WZ = tl.bz + 2, nwc = WX * WY * WZ;
+  if (t < 15) {  // window-cell centres: axis t / 5, window index t % 5
+    const int a = t / 5, k = t % 5;
+    const int ext = a == 0 ? tl.bx : (a == 1 ? tl.by : tl.bz);
+    const float m = (float)(2 * k - 1 - ext);  // half edges from the tile centre
+    const float hh = 0.5f * R.edge_h;
+    const float c = m * hh;
+    W.ch[a][k] = c;
+    W.cl[a][k] = fmaf(m, hh, -c) + m * (0.5f * R.edge_l);
+  }
+  int cnt = 0, incl = 0;
+  if (t < kMaxWinCells) {
+    if (t < nwc) {
+      const int wx = t % WX, wy = (t / WX) % WY, wz = t / (WX * WY);
+      int gx = tl.x0 - 1 + wx, gy = tl.y0 - 1 + wy, gz = tl.z0 - 1 + wz;
+      gx += gx < 0 ? nc : (gx >= nc ? -nc : 0);
+      gy += gy < 0 ? nc : (gy >= nc ? -nc : 0);
+      gz += gz < 0 ? nc : (gz >= nc ? -nc : 0);
+      const int64_t g = R.cell0 + ((int64_t)gz * nc + gy) * nc + gx;
+      const int s0 = d.cellstart[g];
+      cnt = d.cellstart[g + 1] - s0;
+      W.gs[t] = s0;
+      W.cxyz[t] = wx | (wy << 4) | (wz << 8);
+    }
+    incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) W.wsum[warp] = incl;
+  }
+  __syncthreads();
+  if (t < kMaxWinCells) {
+    int off = 0;
+    for (int w = 0; w < warp; ++w) off += W.wsum[w];
+    if (t < nwc) W.pre[t] = 1 + off + incl - cnt;
+    if (t == nwc - 1) W.pre[nwc] = 1 + off + incl;
+  }
+  __syncthreads();
+  const bool fail = W.pre[nwc] > d.wcap;
+  if (t == 0) {
+    W.WX = WX;
+    W.WY = WY;
+    W.WZ = WZ;
+    W.nwc = nwc;
+    W.bx = tl.bx;
+    W.by = tl.by;
+    int acc = 0, q = 0;
+    for (int zq = 1; zq <= tl.bz; ++zq)
+      for (int yq = 1; yq <= tl.by; ++yq, ++q) {
+        const int c = (zq * WY + yq) * WX + 1;
+        W.rslot[q] = W.pre[c];
+        W.rg[q] = W.gs[c];
+        W.rpre[q] = acc;
+        acc += W.pre[c + tl.bx] - W.pre[c];
+      }
+    W.rpre[q] = acc;
+    W.nrows = q;
+    W.natoms = acc;
+    if (fail) {
+      atomicOr(d.err, ERR_WINDOW);
+      W.natoms = -1;
+    }
+  }
+  if (!fail && t < nwc)
+    for (int s = W.pre[t], e = W.pre[t + 1]; s < e; ++s) cellof[s] = (unsigned char)t;
+  __syncthreads();
+  return !fail;  // uniform: every thread read the same pre[nwc]
+}
+
+// Coordinates of every window slot in the tile frame (X_h, and with LO the
+// remainder X_l), from the layout in W and cellof; slot 0 gets the dummy.
+// Each thread handles its slots three at a time, so that their coordinate
+// loads are in flight together.
+template <bool LO>
+__device__ void stage_coords(const Sys &d, const TileWin &W, float4 *whi, uint2 *wlo, const unsigned char *cellof) {
+  const int t = threadIdx.x;
+  const float4 *rel = static_cast<const float4 *>(d.rel);
+  const int end = W.pre[W.nwc], T = blockDim.x;
+  constexpr int U = 3;
+  for (int s0 = 1 + t; s0 < end; s0 += U * T) {
+    int jj[U], xyz[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int s = s0 + u * T;
+      const int c = s < end ? cellof[s] : 0;
+      jj[u] = W.gs[c] + (s - W.pre[c]);
+      xyz[u] = W.cxyz[c];
+    }
+    float4 h[U], l[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (s0 + u * T < end) {
+        h[u] = rel[jj[u]];
+        if constexpr (LO) l[u] = d.rlo[jj[u]];
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int s = s0 + u * T;
+      if (s < end) {
+        const int kx = xyz[u] & 15, ky = (xyz[u] >> 4) & 15, kz = xyz[u] >> 8;
+        const float cx = W.ch[0][kx], cy = W.ch[1][ky], cz = W.ch[2][kz];
+        const float xh = cx + h[u].x, yh = cy + h[u].y, zh = cz + h[u].z;
+        whi[s] = make_float4(xh, yh, zh, 0.f);
+        if constexpr (LO)
+          wlo[s] = pack_lo(two_sum_err(cx, h[u].x, xh) + (W.cl[0][kx] + l[u].x),
+                           two_sum_err(cy, h[u].y, yh) + (W.cl[1][ky] + l[u].y),
+                           two_sum_err(cz, h[u].z, zh) + (W.cl[2][kz] + l[u].z));
+      }
+    }
+  }
+  if (t == 0) {
+    whi[0] = make_float4(1e9f, 1e9f, 1e9f, 0.f);
+    if constexpr (LO) wlo[0] = make_uint2(0u, 0u);
+  }
+  __syncthreads();
+}
+
+// The t-th atom of the tile: its sorted index i, its slot wi and its window
+// cell (wx, wy, wz).
+__device__ __forceinline__ void tile_atom(const TileWin &W, int t, int64_t &i, int &wi, int &wx, int &wy, int &wz) {
+  int q = 0;
+  while (q + 1 < W.nrows && W.rpre[q + 1] <= t) ++q;
+  const int k = t - W.rpre[q];
+  wi = W.rslot[q] + k;
+  i = W.rg[q] + k;
+  wy = q % W.by + 1;
+  wz = q / W.by + 1;
+  const int c = (wz * W.WY + wy) * W.WX;
+  wx = 1;
+  while (wx < W.bx && W.pre[c + wx + 1] <= wi) ++wx;
+}
+
+// Appends a 16-bit entry to four words that fill up as one block of eight
+// (entry k in bits 16k.. of the 128 bits): every word moves down by one
+// entry and the new one comes in at the top.
+__device__ __forceinline__ void push16(uint32_t (&w)[4], uint32_t off) {
+  w[0] = __funnelshift_r(w[0], w[1], 16);
+  w[1] = __funnelshift_r(w[1], w[2], 16);
+  w[2] = __funnelshift_r(w[2], w[3], 16);
+  w[3] = __funnelshift_r(w[3], off, 16);
+}
+
+// gm |= bit when r2 < lim (a predicated OR: no branch, so the lanes of a
+// warp never split over a distance test).
+__device__ __forceinline__ void or_if_less(uint32_t &gm, float r2, float lim, uint32_t bit) {
+  asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+      : "+r"(gm)
+      : "f"(r2), "f"(lim), "r"(bit));
+}
+
+__device__ __forceinline__ float dist2(const float4 &a, const float4 &b) {
+  const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  return dx * dx + dy * dy + dz * dz;
+}
+
+// List build of the tiles whose replica rebuilds: every atom of the tile
+// against the 27 window cells around its own (nine contiguous slot ranges
+// of three cells), 32 slots at a time.  The distance tests (groups of eight,
+// predicated) fill two bit masks, within r_list and within the close radius
+// r_close + skin, before anything is appended; the accepted slots are then
+// appended in warp-uniform loops (as many rounds as the lane with the most
+// entries needs), close entries first.  Entries leave as blocks of eight in
+// slot order, the last block of each segment padded with the dummy slot 0.
+__global__ void __launch_bounds__(kTileThreadsMax, 2) k_build_tile(Sys d, LJ<float> lj) {
+  if (!any_rebuild(d)) return;
+  const Tile tl = d.tiles[blockIdx.x];
+  if (!rebuilds(d, tl.rep)) return;
+  extern __shared__ float4 whi[];
+  unsigned char *cellof = reinterpret_cast<unsigned char *>(whi + d.wcap + kWinPad);
+  __shared__ TileWin W;
+  const bool ok = window_layout(d, tl, W, cellof);
+  {  // the layout, kept for the pair kernel until the next rebuild
+    const int *src = reinterpret_cast<const int *>(&W);
+    int *dst = reinterpret_cast<int *>(d.trec + blockIdx.x);
+    for (int k = threadIdx.x; k < (int)(sizeof(TileWin) / 4); k += blockDim.x) dst[k] = src[k];
+    const uint4 *cs = reinterpret_cast<const uint4 *>(cellof);
+    uint4 *cd = reinterpret_cast<uint4 *>(d.tcell + (int64_t)blockIdx.x * (d.wcap + kWinPad));
+    if (ok)
+      for (int k = threadIdx.x; k < (d.wcap + kWinPad) / 16; k += blockDim.x) cd[k] = cs[k];
+  }
+  if (!ok) return;
+  stage_coords<false>(d, W, whi, nullptr, cellof);
+  const uint32_t wbase = (uint32_t)__cvta_generic_to_shared(whi);
+  const int64_t n = d.n;
+  const int maxb = d.maxnb >> 3;
+  for (int t = threadIdx.x; t < W.natoms; t += blockDim.x) {
+    int64_t i;
+    int wi, wx, wy, wz;
+    tile_atom(W, t, i, wi, wx, wy, wz);
+    const float4 xi = whi[wi];
+    uint4 *far = d.tnb + i;
+    uint4 *cl = d.tcl + i;
+    uint32_t fw[4] = {0u, 0u, 0u, 0u}, cw[4] = {0u, 0u, 0u, 0u};
+    int nfar = 0, ncl = 0;
+    auto put_far = [&](uint32_t off) {
+      push16(fw, off);
+      if ((++nfar & 7) == 0 && (nfar >> 3) <= maxb)
+        far[(int64_t)((nfar >> 3) - 1) * n] = make_uint4(fw[0], fw[1], fw[2], fw[3]);
+    };
+    for (int row = 0; row < 9; ++row) {
+      const int c = ((wz + row / 3 - 1) * W.WY + (wy + row % 3 - 1)) * W.WX + wx - 1;
+      const int s1 = W.pre[c + 3];
+      for (int s = W.pre[c]; s < s1; s += 32) {
+        const uint32_t a0 = wbase + ((uint32_t)s << 4);
+        const int m = min(32, s1 - s);
+        uint32_t am = 0u, cm = 0u;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          if (8 * g < m) {
+            uint32_t ga = 0u, gc = 0u;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const float r2 = dist2(xi, lds4(a0 + 16u * (8 * g + u)));
+              or_if_less(ga, r2, lj.rlist2, 1u << u);
+              or_if_less(gc, r2, lj.rcb2, 1u << u);
+            }
+            am |= ga << (8 * g);
+            cm |= gc << (8 * g);
+          }
+        }
+        if (m < 32) am &= (1u << m) - 1u;
+        const int self = wi - s;
+        if (self >= 0 && self < 32) am &= ~(1u << self);
+        cm &= am;
+        uint32_t fm = am & ~cm;
+        const unsigned act = __activemask();
+        const int mc = __reduce_max_sync(act, __popc(cm));
+        for (int k = 0; k < mc; ++k) {
+          if (cm) {
+            const int b = __ffs(cm) - 1;
+            cm &= cm - 1u;
+            if (ncl < kMaxCloseT) {
+              push16(cw, (uint32_t)(s + b) << 4);
+              if ((++ncl & 7) == 0) cl[(int64_t)((ncl >> 3) - 1) * n] = make_uint4(cw[0], cw[1], cw[2], cw[3]);
+            } else {
+              fm |= 1u << b;  // beyond the close capacity: FP32 displacement
+            }
+          }
+        }
+        const int mf = __reduce_max_sync(act, __popc(fm));
+        for (int k = 0; k < mf; ++k) {
+          if (fm) {
+            const int b = __ffs(fm) - 1;
+            fm &= fm - 1u;
+            put_far((uint32_t)(s + b) << 4);
+          }
+        }
+      }
+    }
+    if (ncl & 7) {  // pad the last close block with the dummy
+      const int pad = 8 - (ncl & 7);
+      for (int k = 0; k < pad; ++k) push16(cw, 0u);
+      cl[(int64_t)(ncl >> 3) * n] = make_uint4(cw[0], cw[1], cw[2], cw[3]);
+    }
+    while (nfar & 7) put_far(0u);
+    d.nnb[i] = list_count(d, nfar) | (ncl << 16);
+  }
+}
+
+// One far or close term, branch-free (out of range: ir2 = 0, so every
+// accumulated product is 0); the energy shift is applied once per atom from
+// the count of pairs in range.
+__device__ __forceinline__ void tile_term(const LJ<float> &lj, float dx, float dy, float dz, float f[3], float &e,
+                                          float w[6], int &cnt) {
+  const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  const float rr = pair_rcp(r2);
+  float ir2;  // rr in range, else 0; cnt counts the pairs in range (predicated, no branch)
+  asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %2, %3;\n\tselp.f32 %0, %4, 0f00000000, p;\n\t@p add.s32 %1, %1, 1;\n\t}"
+      : "=f"(ir2), "+r"(cnt)
+      : "f"(r2), "f"(lj.rc2), "f"(rr));
+  const float ir6 = ir2 * ir2 * ir2;
+  e = fmaf(ir6, fmaf(lj.c12, ir6, -lj.c6), e);
+  const float fs = ir2 * ir6 * fmaf(lj.f12, ir6, -lj.f6);
+  const float fx = fs * dx, fy = fs * dy, fz = fs * dz;
+  f[0] += fx;
+  f[1] += fy;
+  f[2] += fz;
+  w[0] = fmaf(dx, fx, w[0]);
+  w[1] = fmaf(dy, fy, w[1]);
+  w[2] = fmaf(dz, fz, w[2]);
+  w[3] = fmaf(dx, fy, w[3]);
+  w[4] = fmaf(dx, fz, w[4]);
+  w[5] = fmaf(dy, fz, w[5]);
+}
+
+// The displacement a - b of two double-float coordinates, rounded once.
+__device__ __forceinline__ float df_disp(float ah, float al, float bh, float bl) {
+  const dfloat s = df_two_sum(ah, -bh);
+  return s.h + (s.l + (al - bl));
+}
+
+// Pair forces, per-particle energies and virials of one tile per CTA.  The
+// list blocks are streamed two ahead (the close block and the first two far
+// blocks are requested before any arithmetic).
+__global__ void __launch_bounds__(kTileThreadsMax, 3) k_pair_tile(Sys d, LJ<float> lj) {
+  extern __shared__ float4 whi[];
+  uint2 *wlo = reinterpret_cast<uint2 *>(whi + d.wcap + kWinPad);
+  unsigned char *cellof = reinterpret_cast<unsigned char *>(wlo + d.wcap + kWinPad);
+  __shared__ TileWin W;
+  {  // the layout the last list build kept (one coalesced load)
+    const int *src = reinterpret_cast<const int *>(d.trec + blockIdx.x);
+    int *dst = reinterpret_cast<int *>(&W);
+    for (int k = threadIdx.x; k < (int)(sizeof(TileWin) / 4); k += blockDim.x) dst[k] = src[k];
+    const uint4 *cs = reinterpret_cast<const uint4 *>(d.tcell + (int64_t)blockIdx.x * (d.wcap + kWinPad));
+    uint4 *cd = reinterpret_cast<uint4 *>(cellof);
+    for (int k = threadIdx.x; k < (d.wcap + kWinPad) / 16; k += blockDim.x) cd[k] = cs[k];
+  }
+  __syncthreads();
+  if (W.natoms < 0) return;  // the build found the window over capacity (error word set)
+  stage_coords<true>(d, W, whi, wlo, cellof);
+  const uint32_t wbase = (uint32_t)__cvta_generic_to_shared(whi);
+  const uint32_t lbase = (uint32_t)__cvta_generic_to_shared(wlo);
+  const int64_t n = d.n;
+  float *F = static_cast<float *>(d.F);
+  float *E = static_cast<float *>(d.epot);
+  float *Wv = static_cast<float *>(d.W);
+  const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+  for (int t = threadIdx.x; t < W.natoms; t += blockDim.x) {
+    int64_t i;
+    int wi, wx, wy, wz;
+    tile_atom(W, t, i, wi, wx, wy, wz);
+    const int nn = d.nnb[i];
+    const int nb = (nn & 0xffff) >> 3, ncl = nn >> 16;
+    const uint4 *lw = d.tnb + i;
+    const uint4 *lc = d.tcl + i;
+    const uint4 C0 = ncl > 0 ? __ldcs(lc) : zero;
+    uint4 A = nb > 0 ? __ldcs(lw) : zero;
+    uint4 B = nb > 1 ? __ldcs(lw + n) : zero;
+    const float4 xi = whi[wi];
+    const float3 li = unpack_lo(wlo[wi]);
+    float f[3] = {0.f, 0.f, 0.f}, e = 0.f, w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int cnt = 0;
+    auto close_term = [&](uint32_t off) {
+      const float4 pj = lds4(wbase + off);
+      const float3 lj3 = unpack_lo(lds2(lbase + (off >> 1)));
+      tile_term(lj, df_disp(xi.x, li.x, pj.x, lj3.x), df_disp(xi.y, li.y, pj.y, lj3.y),
+                df_disp(xi.z, li.z, pj.z, lj3.z), f, e, w, cnt);
+    };
+    auto close_block = [&](const uint4 &q, int m) {  // the first m entries of a block
+      const uint32_t v[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k < m) close_term(k & 1 ? v[k >> 1] >> 16 : v[k >> 1] & 0xffffu);
+    };
+    close_block(C0, ncl);
+    if (ncl > 8) close_block(__ldcs(lc + n), ncl - 8);
+    auto far_term = [&](uint32_t off) {
+      const float4 pj = lds4(wbase + off);
+      tile_term(lj, xi.x - pj.x, xi.y - pj.y, xi.z - pj.z, f, e, w, cnt);
+    };
+    for (int k = 0; k < nb; ++k) {
+      const uint4 C = k + 2 < nb ? __ldcs(lw + (int64_t)(k + 2) * n) : zero;
+      far_term(A.x & 0xffffu);
+      far_term(A.x >> 16);
+      far_term(A.y & 0xffffu);
+      far_term(A.y >> 16);
+      far_term(A.z & 0xffffu);
+      far_term(A.z >> 16);
+      far_term(A.w & 0xffffu);
+      far_term(A.w >> 16);
+      A = B;
+      B = C;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) F[a * n + i] = f[a];
+    E[i] = 0.5f * fmaf(-lj.ushift, (float)cnt, e);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) Wv[a * n + i] = 0.5f * w[a];
+  }
+}
+
 // ---------------------------------------------------- reduce and sample
 
 // Second half kick, then the per-step observables of every replica
@@ -1551,6 +2037,8 @@ struct md_handle_s {
   int pair_threads = kPairThreads;   // launch shapes (autotuned when asked)
   int build_warps = kCellWarps;
   int build_kind = 0;                // 0: j-parallel k_build, 1: i-parallel k_build_ip, 2: k_build_staged
+  int tile_threads = 0;              // MD_PAIR_TILES: threads per tile CTA
+  Tile *d_tiles = nullptr;
   std::vector<Rep> reps;             // host copy of the descriptor table
   Rep *d_rep = nullptr;
   int *d_rep_of_atom = nullptr, *d_rep_of_cell = nullptr, *d_rep_of_block = nullptr;
@@ -1580,6 +2068,9 @@ int grid_for(int64_t n, int threads, int max_blocks = 152 * 8) {
   return std::max(1, std::min(ceil_div(n, threads), max_blocks));
 }
 
+// Verlet lists (with the skin rule) in either list mode.
+bool uses_lists(const md_params &p) { return p.pair_mode == MD_PAIR_VERLET || p.pair_mode == MD_PAIR_TILES; }
+
 template <typename TF>
 LJ<TF> lj_of(const md_params &p) {
   LJ<TF> lj;
@@ -1592,13 +2083,14 @@ LJ<TF> lj_of(const md_params &p) {
   lj.f6 = (TF)(24.0 * p.eps * s6);
   lj.rc2 = (TF)(p.rc * p.rc);
   lj.ushift = (TF)(p.shift ? 4.0 * p.eps * (sr6 * sr6 - sr6) : 0.0);
-  const double rl = p.rc + (p.pair_mode == MD_PAIR_VERLET ? p.skin : 0.0);
+  const double rl = p.rc + (uses_lists(p) ? p.skin : 0.0);
   lj.rlist2 = (TF)(rl * rl);
   // mixed-form Lennard-Jones: pairs closer than 1.03 sigma (|dF/dr| > 280
   // eps/sigma^2) get the displacement rounded once from the double-float
   // offsets; none in FP64 or for the ionic potential
   const double rclose = (std::is_same<TF, float>::value && p.potential == MD_POT_LJ) ? kRClose * p.sigma : 0.0;
   lj.rclose2 = (TF)(rclose * rclose);
+  lj.rcb2 = (TF)((rclose + p.skin) * (rclose + p.skin));
   lj.A = (TF)p.buck_A;
   lj.inv_rho = (TF)(p.buck_rho > 0 ? 1.0 / p.buck_rho : 0.0);
   lj.C6 = (TF)p.buck_C;
@@ -1680,6 +2172,8 @@ int launch_rebuild(md_handle *h, cudaStream_t s) {
   k_rb_place<<<grid_for(d.n, kThreads), kThreads, 0, s>>>(d);
   k_rb_rank<TF><<<grid_for(d.ncell * 32, kCellWarps * 32), kCellWarps * 32, 0, s>>>(d);
   if (h->prm.pair_mode == MD_PAIR_VERLET) launch_build<TF>(h, s);
+  if (h->prm.pair_mode == MD_PAIR_TILES)
+    k_build_tile<<<d.ntiles, h->tile_threads, tile_smem(d.wcap, false), s>>>(d, lj_of<float>(h->prm));
   OTF_LAUNCH_CHECK();
   return MD_OK;
 }
@@ -1687,7 +2181,11 @@ int launch_rebuild(md_handle *h, cudaStream_t s) {
 template <typename TF, int POT>
 void launch_pair_pot(const md_handle *h, cudaStream_t s) {
   const Sys &d = h->d;
-  if (h->prm.pair_mode == MD_PAIR_VERLET) {
+  if (h->prm.pair_mode == MD_PAIR_TILES) {
+    if constexpr (std::is_same<TF, float>::value && POT == kPotLJ)
+      k_pair_tile<<<d.ntiles, h->tile_threads, tile_smem(d.wcap, true), s>>>(
+          d, lj_of<float>(h->prm));
+  } else if (h->prm.pair_mode == MD_PAIR_VERLET) {
     if constexpr (std::is_same<TF, float>::value)
       k_pair_mixed<POT><<<ceil_div(d.n, h->pair_threads), h->pair_threads, 0, s>>>(d, lj_of<float>(h->prm));
     else
@@ -1831,10 +2329,11 @@ int check_device(md_handle *h) {
   OTF_CUDA(cudaStreamSynchronize(h->stream));
   const unsigned e = *h->h_err;
   if (e) {
-    set_error("device check failed (flags 0x%x):%s%s%s%s", e, (e & ERR_NONFINITE) ? " non-finite coordinates;" : "",
+    set_error("device check failed (flags 0x%x):%s%s%s%s%s", e, (e & ERR_NONFINITE) ? " non-finite coordinates;" : "",
               (e & ERR_NBR_OVERFLOW) ? " neighbour list over capacity (raise max_neighbors);" : "",
               (e & ERR_BAD_TYPE) ? " atom type out of range;" : "",
-              (e & ERR_PUSH_BACKLOG) ? " velocity-correlator pushes left unapplied;" : "");
+              (e & ERR_PUSH_BACKLOG) ? " velocity-correlator pushes left unapplied;" : "",
+              (e & ERR_WINDOW) ? " a tile window outgrew its shared-memory capacity (use MD_PAIR_VERLET);" : "");
     return MD_ESTATE;
   }
   return MD_OK;
@@ -1951,8 +2450,12 @@ int validate_params(const md_params *p) {
     set_error("md_init: list_build must be 0, 1, 2 or 3");
     return MD_EINVAL;
   }
-  if (p->pair_mode != MD_PAIR_VERLET && p->pair_mode != MD_PAIR_CELLS) {
+  if (p->pair_mode != MD_PAIR_VERLET && p->pair_mode != MD_PAIR_CELLS && p->pair_mode != MD_PAIR_TILES) {
     set_error("md_init: unknown pair_mode");
+    return MD_EINVAL;
+  }
+  if (p->pair_mode == MD_PAIR_TILES && (p->precision != MD_PREC_MIXED || p->potential != MD_POT_LJ)) {
+    set_error("md_init: MD_PAIR_TILES is for the mixed-precision Lennard-Jones form");
     return MD_EINVAL;
   }
   if (p->potential == MD_POT_BUCK_EWALD) {
@@ -2012,7 +2515,7 @@ int validate_replicas(const md_params *p, const md_replica *reps, int count, int
     set_error("md_init: the per-atom velocity correlator is for a single system (set vacf.u = 0)");
     return MD_EINVAL;
   }
-  const double rl = p->rc + (p->pair_mode == MD_PAIR_VERLET ? p->skin : 0.0);
+  const double rl = p->rc + (uses_lists(*p) ? p->skin : 0.0);
   int64_t total = 0;
   for (int k = 0; k < count; ++k) {
     const md_replica &R = reps[k];
@@ -2076,7 +2579,8 @@ void release(md_handle *h) {
   Sys &d = h->d;
   void *ptrs[] = {d.r, d.v, d.rlo, d.vh, d.vl, d.F, d.epot, d.W, d.rel, d.relb, d.vbuf, d.id, d.type,
                   d.cpk, d.rB, d.vB, d.idB, d.typeB, d.cellB, d.slot, d.perm, d.cellcount, d.cellstart,
-                  d.nbr, d.nnb, d.partials, d.counter, d.obs, d.st, d.rebuild, d.err, h->d_out, h->d_rep,
+                  d.nbr, d.nnb, d.tnb, d.tcl, d.trec, d.tcell, h->d_tiles, d.partials, d.counter, d.obs, d.st, d.rebuild, d.err,
+                  h->d_out, h->d_rep,
                   h->d_rep_of_atom, h->d_rep_of_cell, h->d_rep_of_block, h->d_lam};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -2116,7 +2620,7 @@ float time_runs(md_handle *h, int reps, Fn fn) {
 // not touched) and keeps the fastest of each.
 template <typename TF>
 int autotune(md_handle *h) {
-  if (h->prm.pair_mode != MD_PAIR_VERLET) return MD_OK;
+  if (h->prm.pair_mode != MD_PAIR_VERLET) return MD_OK;  // nothing to choose for the other modes
   float best = 1e30f;
   int best_t = h->pair_threads;
   for (int t : {64, 128, 256}) {
@@ -2149,13 +2653,89 @@ int autotune(md_handle *h) {
   return MD_OK;
 }
 
+// Segments [start, start + len) of nearly equal length <= b covering 0..nc-1.
+std::vector<std::pair<int, int>> tile_segments(int nc, int b) {
+  const int nseg = (nc + b - 1) / b, base = nc / nseg, extra = nc % nseg;
+  std::vector<std::pair<int, int>> out;
+  for (int k = 0, x = 0; k < nseg; ++k) {
+    const int len = base + (k < extra ? 1 : 0);
+    out.emplace_back(x, len);
+    x += len;
+  }
+  return out;
+}
+
+// MD_PAIR_TILES: the tile table, the window capacity (the largest window
+// expected at 1.2 times a replica's mean density, or at least one atom per
+// sigma^3, plus 64 slots), the CTA size (1.1 times the largest mean tile,
+// 128..384 threads; the rare larger tile takes a second pass) and the list
+// arrays.
+int setup_tiles(md_handle *h, const md_replica *reps, int count) {
+  Sys &d = h->d;
+  const md_params &p = h->prm;
+  std::vector<Tile> tiles;
+  double need = 0.0, mean_win = 0.0, mean_tile = 0.0;
+  for (int k = 0; k < count; ++k) {
+    const Rep &R = h->reps[k];
+    const auto sx = tile_segments(R.nc, kTileExt[0]), sy = tile_segments(R.nc, kTileExt[1]),
+               sz = tile_segments(R.nc, kTileExt[2]);
+    int mx = 0, my = 0, mz = 0;
+    for (const auto &z : sz)
+      for (const auto &y : sy)
+        for (const auto &x : sx) {
+          Tile t{};
+          t.rep = k;
+          t.x0 = (unsigned short)x.first;
+          t.y0 = (unsigned short)y.first;
+          t.z0 = (unsigned short)z.first;
+          t.bx = (unsigned char)x.second;
+          t.by = (unsigned char)y.second;
+          t.bz = (unsigned char)z.second;
+          tiles.push_back(t);
+          mx = std::max(mx, x.second);
+          my = std::max(my, y.second);
+          mz = std::max(mz, z.second);
+        }
+    const double cell_vol = R.edge * R.edge * R.edge;
+    const double apc = reps[k].n / ((double)R.nc * R.nc * R.nc);
+    const double s3 = p.sigma * p.sigma * p.sigma;
+    const double win_cells = (double)(mx + 2) * (my + 2) * (mz + 2);
+    need = std::max(need, win_cells * std::max(1.2 * apc, cell_vol / s3) + 64.0);
+    mean_win = std::max(mean_win, win_cells * apc + 1.0);
+    mean_tile = std::max(mean_tile, (double)mx * my * mz * apc);
+  }
+  d.wcap = std::min(kWinMaxSlots, ((int)std::ceil(need) + 63) / 64 * 64);
+  if (1.1 * mean_win > d.wcap || d.maxnb > 65528) {
+    set_error("md_init: MD_PAIR_TILES: cells hold too many atoms for a shared-memory window "
+              "(mean window %.0f slots of %d); use MD_PAIR_VERLET",
+              mean_win, d.wcap);
+    return MD_EINVAL;
+  }
+  d.ntiles = (int)tiles.size();
+  h->tile_threads = std::max(128, std::min(kTileThreadsMax, ((int)std::ceil(1.1 * mean_tile) + 31) / 32 * 32));
+  OTF_CUDA(cudaMalloc(&h->d_tiles, tiles.size() * sizeof(Tile)));
+  OTF_CUDA(cudaMemcpy(h->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+  d.tiles = h->d_tiles;
+  OTF_CUDA(cudaMalloc(&d.tnb, (size_t)(d.maxnb / 8) * d.n * sizeof(uint4)));
+  OTF_CUDA(cudaMalloc(&d.tcl, (size_t)(kMaxCloseT / 8) * d.n * sizeof(uint4)));
+  OTF_CUDA(cudaMalloc(&d.trec, tiles.size() * sizeof(TileWin)));
+  OTF_CUDA(cudaMalloc(&d.tcell, tiles.size() * (size_t)(d.wcap + kWinPad)));
+  // until the first list build every record reads "no window" (natoms = -1)
+  OTF_CUDA(cudaMemset(d.trec, 0xff, tiles.size() * sizeof(TileWin)));
+  OTF_CUDA(cudaFuncSetAttribute(k_build_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tile_smem(d.wcap, false)));
+  OTF_CUDA(cudaFuncSetAttribute(k_pair_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tile_smem(d.wcap, true)));
+  return MD_OK;
+}
+
 int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int count, int mem) {
   h->prm = *p;
   h->build_kind = p->list_build == 0 ? kDefaultBuildKind : p->list_build - 1;
   h->fp64 = p->precision == MD_PREC_FP64;
   h->nrep = count;
   Sys &d = h->d;
-  const double rl = p->rc + (p->pair_mode == MD_PAIR_VERLET ? p->skin : 0.0);
+  const double rl = p->rc + (uses_lists(*p) ? p->skin : 0.0);
   // replica table: atoms, cells and reduction CTAs laid end to end
   h->reps.resize(count);
   int64_t n = 0, ncell = 0, blocks = 0;
@@ -2183,7 +2763,7 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   d.nrep = count;
   h->red_blocks = (int)blocks;
   d.dt = p->dt;
-  const double half_skin = 0.5 * (p->pair_mode == MD_PAIR_VERLET ? p->skin : 0.0);
+  const double half_skin = 0.5 * (uses_lists(*p) ? p->skin : 0.0);
   d.lim2 = half_skin * half_skin;
   d.always_rebuild = (p->pair_mode == MD_PAIR_CELLS || p->skin <= 0.0) ? 1 : 0;
   d.ntypes = p->ntypes;
@@ -2253,6 +2833,8 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   OTF_CUDA(cudaMalloc(&d.cellstart, (ncell + 1) * sizeof(int)));
   if (p->pair_mode == MD_PAIR_VERLET)
     OTF_CUDA(cudaMalloc(&d.nbr, (size_t)d.maxchunks * maxnb * 32 * sizeof(uint32_t)));
+  if (p->pair_mode == MD_PAIR_TILES)
+    if (int rc = setup_tiles(h, reps, count)) return rc;
   OTF_CUDA(cudaMalloc(&d.nnb, n * sizeof(int)));
   OTF_CUDA(cudaMalloc(&d.partials, (size_t)blocks * kNRed * sizeof(double)));
   OTF_CUDA(cudaMalloc(&d.counter, count * sizeof(unsigned)));
@@ -2647,6 +3229,11 @@ int md_get_config(md_handle *h, md_config *out) {
   out->build_warps = h->build_warps;
   out->build_kind = h->build_kind;
   out->vacf_input_bytes = (int64_t)h->d.vacf_slots * 3 * h->d.n * (h->fp64 ? sizeof(double) : sizeof(float));
+  const bool tiles = h->prm.pair_mode == MD_PAIR_TILES;
+  out->tiles = tiles ? h->d.ntiles : 0;
+  out->window_capacity = tiles ? h->d.wcap : 0;
+  out->tile_threads = tiles ? h->tile_threads : 0;
+  if (tiles) out->build_kind = 3;
   return MD_OK;
 }
 
