@@ -189,6 +189,12 @@ def vacf_timed_bytes(args, b, p, m, n):
     return vacf_bytes_blocked(done0, done1, b, p, m, 3 * n, 4, block)
 
 
+def pair_mode_for(pkg, precision):
+    """The pair path of a Lennard-Jones form: tile windows for the mixed form,
+    global Verlet lists for FP64."""
+    return pkg.MD_PAIR_TILES if precision == pkg.MD_PREC_MIXED else pkg.MD_PAIR_VERLET
+
+
 def melt(sysg, target_T, steps, every=10):
     for _ in range(steps // every):
         sysg.step(every)
@@ -352,7 +358,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32 forces/fluxes/products + f64 state/reductions/lag sums",
         "data": "synthetic (seeded fcc start melted at T*=2.0 then 0.722, Maxwell-Boltzmann velocities)",
-        "config": {"workload": workload_name(n), "n_atoms": n, "precision": "mixed", "pair": f"Verlet list, skin {args.skin}",
+        "config": {"workload": workload_name(n), "n_atoms": n, "precision": "mixed", "pair": ("tile windows (MD_PAIR_TILES)" if args.pair == "tiles" else "global Verlet lists") + f", skin {args.skin}",
                    "replicas": "one independent system per GPU" if world > 1 else "one system",
                    "l2": "inputs larger than L2 (state + neighbour lists + VACF ring about 5 GB)",
                    "timing": "CUDA events around every kernel class, recorded inside the replayed 8-step CUDA "
@@ -411,9 +417,9 @@ def melt_replicas(g, temps, steps_hot=600, steps_cold=600, every=10):
 
 def run_batched(pkg, synth, steps, torch):
     """Throughput of the 256-replica uneven ensemble in one handle (mixed
-    form, autotuned launch shapes, stress and heat-flux correlators)."""
+    form on the tile-window path, stress and heat-flux correlators)."""
     reps, temps = c4_ensemble(pkg, synth)
-    p = pkg.make_params(1, 1.0, rc=RC, dt=DT, skin=0.2, precision=pkg.MD_PREC_MIXED, autotune=True,
+    p = pkg.make_params(1, 1.0, rc=RC, dt=DT, skin=0.2, precision=pkg.MD_PREC_MIXED, pair_mode=pkg.MD_PAIR_TILES,
                         stress=(12, 16, 2, 1), heatflux=(12, 16, 2, 1), vacf=None)
     g = pkg.System(p, replicas=reps)
     melt_replicas(g, temps, 300, 300)
@@ -430,11 +436,11 @@ def run_batched(pkg, synth, steps, torch):
     cfg = g.config()
     g.close()
     return {"workload": "256 LJ replicas, sizes log-uniform in [500, 32000] atoms, rho* uniform in [0.7, 0.9], "
-                        "T* uniform in [0.7, 2.0], rc=2.5, dt=0.005, skin 0.2, mixed form, one handle, one graph "
+                        "T* uniform in [0.7, 2.0], rc=2.5, dt=0.005, skin 0.2, mixed form (tile windows), one handle, one graph "
                         "launch per 8 steps; stress and heat-flux correlators per replica",
             "atoms": cfg["atoms"], "replicas": cfg["replicas"], "steps": steps, "ms_per_step": ms / steps,
             "value": cfg["atoms"] * steps / (ms / 1e3), "unit": UNIT,
-            "autotuned": {"pair_threads": cfg["pair_threads"], "build_warps": cfg["build_warps"]}}
+            "tiles": cfg["tiles"], "tile_threads": cfg["tile_threads"], "window_capacity": cfg["window_capacity"]}
 
 
 IONIC = dict(cells=40, rho=0.031, T_K=1300.0, masses=(22.99, 35.45), A=1200.0, brho=0.32, C=10.0, rc=10.0,
@@ -612,8 +618,8 @@ def run_learned_tail_full(args):
     s = synth.lj_system(jc, rho=RHO, T=T_STAR, seed=3)
     n, L = s["n"], s["L"]
     V = L ** 3
-    p = pkg.make_params(n, L, rc=RC, dt=DT, skin=SKIN, precision=pkg.MD_PREC_MIXED, stress=(12, 16, 2, 1),
-                        heatflux=(12, 16, 2, 1), vacf=None)
+    p = pkg.make_params(n, L, rc=RC, dt=DT, skin=SKIN, precision=pkg.MD_PREC_MIXED, pair_mode=pkg.MD_PAIR_TILES,
+                        stress=(12, 16, 2, 1), heatflux=(12, 16, 2, 1), vacf=None)
     g = pkg.System(p, s["r"], s["v"])
     melt(g, 2.0, 600)
     melt(g, T_STAR, 600)
@@ -661,7 +667,8 @@ def tv_ensemble(pkg, synth, replicas, precision, seed0=500):
     for k in range(replicas):
         s = synth.lj_system(10, rho=RHO, T=T_STAR, seed=seed0 + k)
         reps.append(dict(r=s["r"], v=s["v"], box=s["L"]))
-    p = pkg.make_params(1, 1.0, rc=RC, dt=DT, skin=0.2, precision=precision, **TV_SPEC)
+    p = pkg.make_params(1, 1.0, rc=RC, dt=DT, skin=0.2, precision=precision, pair_mode=pair_mode_for(pkg, precision),
+                        **TV_SPEC)
     g = pkg.System(p, replicas=reps)
     melt_replicas(g, np.full(replicas, T_STAR), 2000, 3000)
     g.reset_correlators()
@@ -755,7 +762,8 @@ def run_time_to_viscosity(pkg, synth, torch, replicas=64, chunk=4000, max_steps=
     costs = {"mixed_gpu_batched_%d" % replicas: prod_s / (replicas * steps)}
     s = synth.lj_system(10, rho=RHO, T=T_STAR, seed=1)
     for name, prec in (("fp64_gpu_single", pkg.MD_PREC_FP64), ("mixed_gpu_single", pkg.MD_PREC_MIXED)):
-        ps = pkg.make_params(s["n"], s["L"], rc=RC, dt=DT, skin=0.3, precision=prec, **TV_SPEC)
+        ps = pkg.make_params(s["n"], s["L"], rc=RC, dt=DT, skin=0.3, precision=prec, pair_mode=pair_mode_for(pkg, prec),
+                             **TV_SPEC)
         gs = pkg.System(ps, s["r"], s["v"])
         gs.step(50)
         sync()

@@ -100,8 +100,9 @@ def generate(specs, short, long, *, precision=_lib.MD_PREC_MIXED, melt_steps=(60
             j += 1
         chunk = specs[i:j]
         reps = build_replicas(chunk)
-        p = _lib.make_params(1, 1.0, rc=RC, dt=DT, skin=0.2, precision=precision, stress=SPEC, heatflux=SPEC,
-                             vacf=None)
+        mode = _lib.MD_PAIR_TILES if precision == _lib.MD_PREC_MIXED else _lib.MD_PAIR_VERLET
+        p = _lib.make_params(1, 1.0, rc=RC, dt=DT, skin=0.2, precision=precision, pair_mode=mode, stress=SPEC,
+                             heatflux=SPEC, vacf=None)
         g = _lib.System(p, replicas=reps, stream=stream)
         melt(g, [s["T"] for s in chunk], *melt_steps)
         g.reset_correlators()
