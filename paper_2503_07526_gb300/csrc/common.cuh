@@ -160,6 +160,12 @@ struct dfacc {
     s = t.h;
     c += t.l;
   }
+  // adds another accumulator (s2, c2)
+  __device__ __forceinline__ void merge(float s2, float c2) {
+    const dfloat t = df_two_sum(s, s2);
+    s = t.h;
+    c += t.l + c2;
+  }
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 

@@ -53,7 +53,11 @@ constexpr int kMaxPairThreads = 256;
 constexpr int kCellWarps = 4;  // warps (cells) per CTA in the link-cell kernels
 constexpr int kNRed = 14;      // K, U, V*sigma[6], V*q[3], V*j[3]
 constexpr int kNBanks = 4;     // stress, heat flux, velocity, mass flux
-constexpr int kMaxRedBlocks = 152 * 4;
+constexpr int kMaxRedBlocks = 152 * 64;  // reduction CTAs per replica at most
+// atoms per reduction CTA in the mixed form (16 per thread): measured at
+// 2,048,000 atoms, 0.121 ms per step against 0.123 / 0.134 / 0.160 for 2,048 /
+// 1,024 / 512 (the per-CTA merge and the last CTA's pass grow with the count)
+constexpr int kRedAtomsMixed = 4096;
 constexpr double kRClose = 1.03;  // close-pair radius of the mixed form, in sigma
 
 // Step counters shared by all replicas.
@@ -1441,10 +1445,14 @@ __global__ void __launch_bounds__(kTileThreadsMax, 3) k_pair_tile(Sys d, LJ<floa
 // arithmetic from the double-float velocity, the double-float mass and the
 // FP32 per-particle energy and virial, and summed by a compensated FP32
 // accumulator (dfacc), so the partials carry ~48 bits like FP64 sums of
-// the same inputs.  The CTA and replica tree is FP64 (fixed order:
-// deterministic).  The mixed form runs at most 64 registers, so four CTAs
-// fit an SM and the ~500 CTAs of a 2,048,000-atom system run in one wave
-// (measured 6 % faster than three CTAs per SM).  The last CTA of a replica writes its observables; the
+// the same inputs; the CTA merges them in double-float too (butterflies
+// across each warp, then the warps in fixed order) and converts once per
+// CTA, since FP64 instructions run at a small fraction of the FP32 rate
+// (the FP64 merge took 15 % of the kernel).  The replica tree is FP64
+// (fixed order: deterministic).  The mixed form runs at most 64 registers,
+// so four CTAs fit an SM and the ~500 CTAs of a 2,048,000-atom system run
+// in one wave (measured 6 % faster than three CTAs per SM).  The last CTA
+// of a replica writes its observables; the
 // last replica to finish advances the step counter.  When a velocity sample
 // is due, velocities are also scattered to atom-id order.  The stress,
 // heat-flux and mass-flux correlator samples of the step are taken from the
@@ -1469,7 +1477,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(TF) == 4 ? 4 : 3)
   const int r = d.rep_of_block[blockIdx.x];
   const Rep &R = d.rep[r];
   const int lb = (int)(blockIdx.x - R.block0);
-  double part[kNRed];  // this thread's partial sums
   if constexpr (std::is_same<TF, float>::value) {
     dfacc acc[kNRed + 3];  // [kNRed, kNRed + 3): the virial diagonal (sigma's kinetic diagonal in [2, 5))
     const bool unit_mass = d.unit_mass != 0;
@@ -1547,13 +1554,37 @@ __global__ void __launch_bounds__(kThreads, sizeof(TF) == 4 ? 4 : 3)
         for (int a = 0; a < 3; ++a) acc[11 + a].add(mv[a]);
       }
     }
+    // the CTA's sums: double-float butterflies across each warp, then the
+    // warps' results merged in fixed order (FP64 only once per CTA)
+    __shared__ float2 redf[kThreads / 32][kNRed + 3];
+    __shared__ double totf[kNRed + 3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 1; q < kNRed; ++q) part[q] = acc[q].value();
-    // 2K from the kinetic diagonal, then the virial diagonal added to sigma
-    part[0] = part[2] + part[3] + part[4];
+    for (int q = 1; q < kNRed + 3; ++q) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) part[2 + a] += acc[kNRed + a].value();
-    part[0] *= 0.5;
+      for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, acc[q].s, o);
+        const float c2 = __shfl_xor_sync(0xffffffffu, acc[q].c, o);
+        acc[q].merge(s2, c2);
+      }
+      if (lane == 0) redf[warp][q] = make_float2(acc[q].s, acc[q].c);
+    }
+    __syncthreads();
+    if (threadIdx.x >= 1 && threadIdx.x < kNRed + 3) {
+      dfacc a;
+      a.s = redf[0][threadIdx.x].x;
+      a.c = redf[0][threadIdx.x].y;
+      for (int w = 1; w < kThreads / 32; ++w) a.merge(redf[w][threadIdx.x].x, redf[w][threadIdx.x].y);
+      totf[threadIdx.x] = a.value();
+    }
+    __syncthreads();
+    if (threadIdx.x < kNRed) {
+      // 2K from the kinetic diagonal, then the virial diagonal added to sigma
+      const int q = threadIdx.x;
+      const double v = q == 0 ? 0.5 * (totf[2] + totf[3] + totf[4])
+                              : (q >= 2 && q < 5 ? totf[q] + totf[kNRed + q - 2] : totf[q]);
+      d.partials[blockIdx.x * kNRed + q] = v;
+    }
   } else {  // FP64 form
     A acc[kNRed];
 #pragma unroll
@@ -1609,21 +1640,23 @@ __global__ void __launch_bounds__(kThreads, sizeof(TF) == 4 ? 4 : 3)
       acc[12] += sel * vy;
       acc[13] += sel * vz;
     }
+    double part[kNRed];  // this thread's partial sums
 #pragma unroll
     for (int q = 0; q < kNRed; ++q) part[q] = (double)acc[q];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kNRed; ++q) {
+      const double sm = warp_sum(part[q]);
+      if (lane == 0) red[warp][q] = sm;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNRed) {
+      double sm = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) sm += red[w][threadIdx.x];
+      d.partials[blockIdx.x * kNRed + threadIdx.x] = sm;
+    }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < kNRed; ++q) {
-    const double sm = warp_sum(part[q]);
-    if (lane == 0) red[warp][q] = sm;
-  }
-  __syncthreads();
-  if (threadIdx.x < kNRed) {
-    double sm = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) sm += red[w][threadIdx.x];
-    d.partials[blockIdx.x * kNRed + threadIdx.x] = sm;
-  }
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = (atomicAdd(d.counter + r, 1u) == (unsigned)R.nblk - 1);
@@ -2752,7 +2785,8 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
     R.atom1 = n + reps[k].n;
     R.cell0 = ncell;
     R.block0 = blocks;
-    R.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxRedBlocks, (reps[k].n + 4095) / 4096));
+    const int64_t per_cta = h->fp64 ? 4096 : kRedAtomsMixed;
+    R.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxRedBlocks, (reps[k].n + per_cta - 1) / per_cta));
     n += reps[k].n;
     ncell += (int64_t)R.nc * R.nc * R.nc;
     blocks += R.nblk;
