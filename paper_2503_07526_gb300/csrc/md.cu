@@ -1437,17 +1437,6 @@ __global__ void __launch_bounds__(kTileThreadsMax, 3) k_pair_tile(Sys d, LJ<floa
 
 // ---------------------------------------------------- reduce and sample
 
-// 4-byte asynchronous global-to-shared copy (cp.async, completion tracked
-// per thread by commit groups).
-__device__ __forceinline__ void cp_async4(uint32_t *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
 // Second half kick, then the per-step observables of every replica
 // (Sec. 2.3): K, U, V sigma_ab = sum m v_a v_b + sum W_i,ab,
 // V q = sum (E_i v_i + W_i v_i).  Each CTA works on one replica (rep_of_block)
@@ -1491,49 +1480,22 @@ __global__ void __launch_bounds__(kThreads, sizeof(TF) == 4 ? 4 : 3)
   if constexpr (std::is_same<TF, float>::value) {
     dfacc acc[kNRed + 3];  // [kNRed, kNRed + 3): the virial diagonal (sigma's kinetic diagonal in [2, 5))
     const bool unit_mass = d.unit_mass != 0;
-    // The inputs of a thread's next atom are copied into shared memory
-    // asynchronously (cp.async: nothing held in registers while in flight)
-    // while the current one is computed; each thread reads back only the
-    // words it copied, so no barrier is needed.  Words: type, epot, W[6],
-    // F[3], vh[3], vl[3], id.
-    __shared__ uint32_t stg[2][18][kThreads];
-    const int tid = threadIdx.x;
-    const int64_t stride = (int64_t)R.nblk * blockDim.x;
-    auto issue = [&](int sg, int64_t a) {
-      if (a < R.atom1) {
-        cp_async4(&stg[sg][0][tid], d.type + a);
-        cp_async4(&stg[sg][1][tid], Ep + a);
-#pragma unroll
-        for (int q = 0; q < 6; ++q) cp_async4(&stg[sg][2 + q][tid], Wp + q * n + a);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          if (KICK) cp_async4(&stg[sg][8 + c][tid], F + c * n + a);
-          cp_async4(&stg[sg][11 + c][tid], d.vh + c * n + a);
-          cp_async4(&stg[sg][14 + c][tid], d.vl + c * n + a);
-        }
-        if (vacf_due) cp_async4(&stg[sg][17][tid], d.id + a);
-      }
-      cp_async_commit();
-    };
-    int64_t i = R.atom0 + (int64_t)lb * blockDim.x + tid;
-    issue(0, i);
-    for (int k = 0; i < R.atom1; i += stride, ++k) {
-      issue((k + 1) & 1, i + stride);
-      cp_async_wait1();  // this atom's words have landed
-      const uint32_t(&g)[18][kThreads] = stg[k & 1];
-      const int t = min(max((int)g[0][tid], 0), 7);
-      const float ep = __uint_as_float(g[1][tid]);
+    for (int64_t i = R.atom0 + (int64_t)lb * blockDim.x + threadIdx.x; i < R.atom1;
+         i += (int64_t)R.nblk * blockDim.x) {
+      // every load of the atom first (the stores below could alias them)
+      const int t = type_of(d, i);
+      const float ep = Ep[i];
       float w[6];
 #pragma unroll
-      for (int q = 0; q < 6; ++q) w[q] = __uint_as_float(g[2 + q][tid]);
+      for (int q = 0; q < 6; ++q) w[q] = Wp[q * n + i];
       float f[3], vh[3], vl[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        f[a] = KICK ? __uint_as_float(g[8 + a][tid]) : 0.f;
-        vh[a] = __uint_as_float(g[11 + a][tid]);
-        vl[a] = __uint_as_float(g[14 + a][tid]);
+        f[a] = KICK ? F[a * n + i] : 0.f;
+        vh[a] = d.vh[a * n + i];
+        vl[a] = d.vl[a * n + i];
       }
-      const int id = vacf_due ? (int)g[17][tid] : 0;
+      const int id = vacf_due ? d.id[i] : 0;
       const dfloat h{d.hdtm_h[t], d.hdtm_l[t]};
       dfloat v[3];
 #pragma unroll
@@ -1592,7 +1554,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(TF) == 4 ? 4 : 3)
         for (int a = 0; a < 3; ++a) acc[11 + a].add(mv[a]);
       }
     }
-    cp_async_wait0();
     // the CTA's sums: double-float butterflies across each warp, then the
     // warps' results merged in fixed order (FP64 only once per CTA)
     __shared__ float2 redf[kThreads / 32][kNRed + 3];
