@@ -145,6 +145,11 @@ typedef struct {
   int32_t flux_species; /* atom type whose partial momentum density j is
                          observed and correlated with q (MD_CORR_MASSFLUX) */
   corr_spec massflux; /* MD_CORR_MASSFLUX settings (u = 0: off) */
+  int32_t window_slots; /* MD_PAIR_TILES: shared-memory window capacity per tile in
+                           atoms + 1 (0 = automatic: the largest window expected at
+                           1.2 times the mean density, or one atom per sigma^3, plus
+                           64); at most 4,096.  A window that needs more stops
+                           md_init or md_step with MD_ESTATE. */
 } md_params;
 
 typedef struct {

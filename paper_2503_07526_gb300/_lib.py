@@ -46,7 +46,8 @@ class md_params(C.Structure):
                 ("heatflux", corr_spec), ("vacf", corr_spec), ("list_build", C.c_int32),
                 ("potential", C.c_int32), ("charge", C.c_double * 8), ("buck_A", C.c_double), ("buck_rho", C.c_double),
                 ("buck_C", C.c_double), ("coulomb", C.c_double), ("ewald_alpha", C.c_double), ("mesh", C.c_int32),
-                ("order", C.c_int32), ("flux_species", C.c_int32), ("massflux", corr_spec)]
+                ("order", C.c_int32), ("flux_species", C.c_int32), ("massflux", corr_spec),
+                ("window_slots", C.c_int32)]
 
 
 class md_system(C.Structure):
@@ -228,7 +229,7 @@ def make_params(n, box, *, eps=1.0, sigma=1.0, rc=2.5, shift=True, masses=(1.0,)
                 precision=MD_PREC_FP64, pair_mode=MD_PAIR_VERLET, skin=0.3, max_neighbors=0, use_graph=True,
                 autotune=False, stress=(12, 16, 2, 1), heatflux=(12, 16, 2, 1), vacf=(8, 16, 2, 1), list_build=0,
                 potential=MD_POT_LJ, charges=(), buckingham=(0.0, 1.0, 0.0), coulomb=KE_EV_ANGSTROM, ewald_alpha=0.0,
-                mesh=0, order=8, flux_species=0, massflux=None):
+                mesh=0, order=8, flux_species=0, massflux=None, window_slots=0):
     p = md_params()
     p.n, p.box, p.eps, p.sigma, p.rc, p.shift = int(n), float(box), eps, sigma, rc, int(bool(shift))
     p.ntypes = len(masses)
@@ -243,6 +244,7 @@ def make_params(n, box, *, eps=1.0, sigma=1.0, rc=2.5, shift=True, masses=(1.0,)
     p.buck_A, p.buck_rho, p.buck_C = (float(x) for x in buckingham)
     p.coulomb, p.ewald_alpha, p.mesh, p.order = float(coulomb), float(ewald_alpha), int(mesh), int(order)
     p.flux_species = int(flux_species)
+    p.window_slots = int(window_slots)
     for name, spec in (("stress", stress), ("heatflux", heatflux), ("vacf", vacf), ("massflux", massflux)):
         cs = getattr(p, name)
         cs.b, cs.p, cs.m, cs.u = spec if spec is not None else (1, 2, 1, 0)

@@ -2487,6 +2487,10 @@ int validate_params(const md_params *p) {
     set_error("md_init: unknown pair_mode");
     return MD_EINVAL;
   }
+  if (p->window_slots < 0 || p->window_slots > kWinMaxSlots || (p->window_slots > 0 && p->window_slots % 16)) {
+    set_error("md_init: window_slots must be 0 (automatic) or a multiple of 16 up to 4096");
+    return MD_EINVAL;
+  }
   if (p->pair_mode == MD_PAIR_TILES && (p->precision != MD_PREC_MIXED || p->potential != MD_POT_LJ)) {
     set_error("md_init: MD_PAIR_TILES is for the mixed-precision Lennard-Jones form");
     return MD_EINVAL;
@@ -2738,7 +2742,8 @@ int setup_tiles(md_handle *h, const md_replica *reps, int count) {
     mean_tile = std::max(mean_tile, (double)mx * my * mz * apc);
   }
   d.wcap = std::min(kWinMaxSlots, ((int)std::ceil(need) + 63) / 64 * 64);
-  if (1.1 * mean_win > d.wcap || d.maxnb > 65528) {
+  if (p.window_slots > 0) d.wcap = p.window_slots;  // the caller's capacity (checked at every build)
+  if ((p.window_slots == 0 && 1.1 * mean_win > d.wcap) || d.maxnb > 65528) {
     set_error("md_init: MD_PAIR_TILES: cells hold too many atoms for a shared-memory window "
               "(mean window %.0f slots of %d); use MD_PAIR_VERLET",
               mean_win, d.wcap);

@@ -152,3 +152,26 @@ def test_tiles_only_for_mixed_lennard_jones(pkg):
     with pytest.raises(pkg.MdError) as ei:
         pkg.System(tiles(pkg, s, precision=pkg.MD_PREC_FP64), s["r"], s["v"])
     assert ei.value.code == -1
+
+
+def test_window_capacity_is_checked(pkg):
+    """A window that needs more slots than the capacity is an error (the
+    build marks the tile and writes nothing; MD_ESTATE), a capacity given
+    explicitly changes nothing else, and a capacity that is not a multiple of
+    16 up to 4,096 is refused."""
+    s = jittered(8, seed=5)
+    with pytest.raises(pkg.MdError) as ei:
+        pkg.System(tiles(pkg, s, window_slots=64), s["r"], s["v"])
+    assert ei.value.code == -4
+    a = pkg.System(tiles(pkg, s), s["r"], s["v"])
+    b = pkg.System(tiles(pkg, s, window_slots=4096), s["r"], s["v"])
+    assert b.config()["window_capacity"] == 4096 and a.config()["window_capacity"] < 4096
+    a.step(12)
+    b.step(12)
+    pa, pb = a.particles(), b.particles()
+    for key in ("r", "v", "F", "W", "epot"):
+        assert np.array_equal(pa[key], pb[key]), key
+    for bad in (17, 4112, -16):
+        with pytest.raises(pkg.MdError) as ei:
+            pkg.System(tiles(pkg, s, window_slots=bad), s["r"], s["v"])
+        assert ei.value.code == -1
