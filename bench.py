@@ -722,8 +722,8 @@ def run_time_to_viscosity(pkg, synth, torch, replicas=64, chunk=4000, max_steps=
     committed result of --tv-reference).  Every form carries the same
     correlators (stress and heat flux; no per-atom velocity correlator).
     Measured: the mixed batch of `replicas` replicas runs `chunk` steps at a
-    time until its standard error reaches 2 % (production seconds, readouts
-    included); the single-system forms (plain FP64 and mixed, one replica at
+    time until both conditions hold (production seconds, readouts included;
+    at most max_steps); the single-system forms (plain FP64 and mixed, one replica at
     a time) are projected: the replica-steps that run needed times their
     measured cost per replica-step.  With a trained learned tail, the batch
     is also read after `tail_steps` steps and the network's predictions are
@@ -752,7 +752,9 @@ def run_time_to_viscosity(pkg, synth, torch, replicas=64, chunk=4000, max_steps=
             continue
         mean, se = float(a["eta"].mean()), float(a["eta"].std(ddof=1) / math.sqrt(replicas))
         history.append([steps, mean, se])
-        if se <= 0.02 * abs(mean):
+        # both conditions of the criterion (the run goes on while the mean is
+        # still more than 2 % from the reference, even at 2 % standard error)
+        if se <= 0.02 * abs(mean) and (ref is None or abs(mean - ref["eta"]) <= 0.02 * abs(ref["eta"])):
             break
     g.close()
     reached_se = se <= 0.02 * abs(mean)
