@@ -1767,6 +1767,15 @@ __global__ void k_iota(int *id, int64_t n) {
 // Mixed form set-up: FP64 input positions and velocities (in the rB, vB
 // scratch, input order) become cell index + double-float offset from the
 // cell centre and double-float velocities.  FP64 arithmetic, once.
+// Sets ERR_NONFINITE when any of count values is NaN or infinite (md_init's
+// check of the caller's coordinates and velocities).
+__global__ void k_check_finite(const double *a, int64_t count, unsigned *err) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(a[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_NONFINITE);
+}
+
 __global__ void k_init_df(Sys d) {
   const int64_t n = d.n;
   float4 *rel = static_cast<float4 *>(d.rel);
@@ -2575,20 +2584,9 @@ int validate_replicas(const md_params *p, const md_replica *reps, int count, int
       return MD_EINVAL;
     }
     total += R.n;
-    if (mem == MD_MEM_HOST) {
-      for (int64_t i = 0; i < 3 * R.n; ++i)
-        if (!std::isfinite(R.r[i]) || !std::isfinite(R.v[i])) {
-          set_error("md_init: replica %d: non-finite position or velocity at %lld", k, (long long)i);
-          return MD_ESTATE;
-        }
-      if (R.type)
-        for (int64_t i = 0; i < R.n; ++i)
-          if (R.type[i] < 0 || R.type[i] >= p->ntypes) {
-            set_error("md_init: replica %d: atom %lld has type %d outside [0, %d)", k, (long long)i, R.type[i],
-                      p->ntypes);
-            return MD_EINVAL;
-          }
-    }
+    // the values themselves (finite coordinates and velocities, types in
+    // range) are checked on the device after the copy, for host and device
+    // arrays alike (k_check_finite, and the first sort for the types)
   }
   if (total >= (int64_t(1) << 26)) {  // 26 bits of atom index per neighbour-list entry
     set_error("md_init: %lld atoms in total; at most 2^26 - 1", (long long)total);
@@ -2934,15 +2932,17 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
     else
       OTF_CUDA(cudaMemsetAsync(d.type + R.atom0, 0, nk * sizeof(int), st));
   }
+  // rdst and vdst hold 3n values each (FP64 state or the mixed form's scratch)
+  k_check_finite<<<grid_for(3 * n, kThreads), kThreads, 0, st>>>(rdst, 3 * n, d.err);
+  k_check_finite<<<grid_for(3 * n, kThreads), kThreads, 0, st>>>(vdst, 3 * n, d.err);
   k_iota<<<grid_for(n, kThreads), kThreads, 0, st>>>(d.id, n);
   OTF_LAUNCH_CHECK();
   if (!h->fp64) {
     k_init_df<<<grid_for(n, kThreads), kThreads, 0, st>>>(d);
     OTF_LAUNCH_CHECK();
   }
-  // host-side copies of the inputs must be done before returning
-  OTF_CUDA(cudaStreamSynchronize(st));
-  // correlators: stress and heat flux have 3 series per replica, the
+  // correlators (their allocations overlap the input copies when the caller's
+  // host arrays are pinned): stress and heat flux have 3 series per replica, the
   // velocity correlator 3n series in 3 groups (single system)
   // and the mass-flux cross correlator 6 series per replica
   const corr_spec *specs[kNBanks] = {&p->stress, &p->heatflux, &p->vacf, &p->massflux};
@@ -2964,6 +2964,9 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
     c.host_base = &h->corr_base;
     c.u = specs[k]->u;
   }
+  // the copies from the caller's arrays are done and their values finite
+  // before anything works on them (check_device synchronises the stream)
+  if (int rc0 = check_device(h)) return rc0;
   // initial layout, forces and observables
   int rc = h->fp64 ? launch_rebuild<double>(h, st) : launch_rebuild<float>(h, st);
   if (rc) return rc;
