@@ -1767,6 +1767,24 @@ __global__ void k_iota(int *id, int64_t n) {
 // Mixed form set-up: FP64 input positions and velocities (in the rB, vB
 // scratch, input order) become cell index + double-float offset from the
 // cell centre and double-float velocities.  FP64 arithmetic, once.
+// Replica of every atom (which = 0), cell (1) or reduction CTA (2): the
+// last replica whose range starts at or before the index (binary search over
+// the descriptor table; the ranges are laid end to end in replica order).
+__global__ void k_rep_of(const Rep *rep, int nrep, int which, int *dst, int64_t total) {
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nrep - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      const int64_t start = which == 0 ? rep[mid].atom0 : (which == 1 ? rep[mid].cell0 : rep[mid].block0);
+      if (start <= x)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    dst[x] = lo;
+  }
+}
+
 // Sets ERR_NONFINITE when any of count values is NaN or infinite (md_init's
 // check of the caller's coordinates and velocities).
 __global__ void k_check_finite(const double *a, int64_t count, unsigned *err) {
@@ -2894,20 +2912,13 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   d.rep_of_block = h->d_rep_of_block;
   d.lam = h->d_lam;
   cudaStream_t st = h->stream;
-  {
-    // replica lookup tables (set-up only)
-    std::vector<int> roa(n), roc(ncell), rob(blocks);
-    for (int k = 0; k < count; ++k) {
-      const Rep &R = h->reps[k];
-      std::fill(roa.begin() + R.atom0, roa.begin() + R.atom1, k);
-      std::fill(roc.begin() + R.cell0, roc.begin() + R.cell0 + (int64_t)R.nc * R.nc * R.nc, k);
-      std::fill(rob.begin() + R.block0, rob.begin() + R.block0 + R.nblk, k);
-    }
-    OTF_CUDA(cudaMemcpy(h->d_rep, h->reps.data(), count * sizeof(Rep), cudaMemcpyHostToDevice));
-    OTF_CUDA(cudaMemcpy(h->d_rep_of_atom, roa.data(), n * sizeof(int), cudaMemcpyHostToDevice));
-    OTF_CUDA(cudaMemcpy(h->d_rep_of_cell, roc.data(), ncell * sizeof(int), cudaMemcpyHostToDevice));
-    OTF_CUDA(cudaMemcpy(h->d_rep_of_block, rob.data(), blocks * sizeof(int), cudaMemcpyHostToDevice));
-  }
+  // replica lookup tables (set-up only), filled on the device from the
+  // descriptor table
+  OTF_CUDA(cudaMemcpyAsync(h->d_rep, h->reps.data(), count * sizeof(Rep), cudaMemcpyHostToDevice, st));
+  k_rep_of<<<grid_for(n, kThreads), kThreads, 0, st>>>(h->d_rep, count, 0, h->d_rep_of_atom, n);
+  k_rep_of<<<grid_for(ncell, kThreads), kThreads, 0, st>>>(h->d_rep, count, 1, h->d_rep_of_cell, ncell);
+  k_rep_of<<<grid_for(blocks, kThreads), kThreads, 0, st>>>(h->d_rep, count, 2, h->d_rep_of_block, blocks);
+  OTF_LAUNCH_CHECK();
   OTF_CUDA(cudaMemsetAsync(d.counter, 0, count * sizeof(unsigned), st));
   OTF_CUDA(cudaMemsetAsync(d.obs, 0, count * sizeof(ObsDev), st));
   OTF_CUDA(cudaMemsetAsync(d.st, 0, sizeof(StepDev), st));
