@@ -2108,6 +2108,8 @@ struct md_handle_s {
   corr_handle banks[kNBanks];  // system-owned correlators (borrowed by md_corr)
   bool bank_on[kNBanks] = {false, false, false, false};
   double *d_out = nullptr;  // unsort staging [16][n]
+  char *arena = nullptr;    // one device allocation holding every per-atom, per-cell and per-tile array
+  std::vector<Tile> tiles_host;  // MD_PAIR_TILES: the tile table (uploaded once)
   ObsDev *h_obs = nullptr;  // pinned [nrep]
   StepDev *h_st = nullptr;  // pinned
   unsigned *h_err = nullptr;
@@ -2629,14 +2631,10 @@ void release(md_handle *h) {
   }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
-  Sys &d = h->d;
-  void *ptrs[] = {d.r, d.v, d.rlo, d.vh, d.vl, d.F, d.epot, d.W, d.rel, d.relb, d.vbuf, d.id, d.type,
-                  d.cpk, d.rB, d.vB, d.idB, d.typeB, d.cellB, d.slot, d.perm, d.cellcount, d.cellstart,
-                  d.nbr, d.nnb, d.tnb, d.tcl, d.trec, d.tcell, h->d_tiles, d.partials, d.counter, d.obs, d.st, d.rebuild, d.err,
-                  h->d_out, h->d_rep,
-                  h->d_rep_of_atom, h->d_rep_of_cell, h->d_rep_of_block, h->d_lam};
-  for (void *p : ptrs)
-    if (p) cudaFree(p);
+  // every device array of the handle lives in the arena, except the
+  // particles' readout staging
+  if (h->arena) cudaFree(h->arena);
+  if (h->d_out) cudaFree(h->d_out);
   h->spme.destroy();
   for (int k = 0; k < kNBanks; ++k)
     if (h->bank_on[k]) h->banks[k].c.destroy();
@@ -2767,21 +2765,39 @@ int setup_tiles(md_handle *h, const md_replica *reps, int count) {
   }
   d.ntiles = (int)tiles.size();
   h->tile_threads = std::max(128, std::min(kTileThreadsMax, ((int)std::ceil(1.1 * mean_tile) + 31) / 32 * 32));
-  OTF_CUDA(cudaMalloc(&h->d_tiles, tiles.size() * sizeof(Tile)));
-  OTF_CUDA(cudaMemcpy(h->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
-  d.tiles = h->d_tiles;
-  OTF_CUDA(cudaMalloc(&d.tnb, (size_t)(d.maxnb / 8) * d.n * sizeof(uint4)));
-  OTF_CUDA(cudaMalloc(&d.tcl, (size_t)(kMaxCloseT / 8) * d.n * sizeof(uint4)));
-  OTF_CUDA(cudaMalloc(&d.trec, tiles.size() * sizeof(TileWin)));
-  OTF_CUDA(cudaMalloc(&d.tcell, tiles.size() * (size_t)(d.wcap + kWinPad)));
-  // until the first list build every record reads "no window" (natoms = -1)
-  OTF_CUDA(cudaMemset(d.trec, 0xff, tiles.size() * sizeof(TileWin)));
+  h->tiles_host = std::move(tiles);
+  return MD_OK;
+}
+
+// MD_PAIR_TILES, once the arrays are carved: the tile table uploaded, every
+// record marked "no window" (natoms = -1) until the first list build, and
+// the kernels' shared-memory limits raised to the window size.
+int finish_tiles(md_handle *h, cudaStream_t st) {
+  Sys &d = h->d;
+  const size_t nt = h->tiles_host.size();
+  OTF_CUDA(cudaMemcpyAsync(h->d_tiles, h->tiles_host.data(), nt * sizeof(Tile), cudaMemcpyHostToDevice, st));
+  OTF_CUDA(cudaMemsetAsync(d.trec, 0xff, nt * sizeof(TileWin), st));
   OTF_CUDA(cudaFuncSetAttribute(k_build_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)tile_smem(d.wcap, false)));
   OTF_CUDA(cudaFuncSetAttribute(k_pair_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)tile_smem(d.wcap, true)));
   return MD_OK;
 }
+
+// Device arrays carved out of one allocation: a driver allocation costs tens
+// of microseconds whatever its size, and a handle has ~35 arrays.  The same
+// sequence of take() calls runs twice: without a base to add up the sizes,
+// then with the allocation to hand out the pointers (256-byte aligned).
+struct Arena {
+  char *base = nullptr;
+  size_t used = 0;
+  template <typename T>
+  void take(T *&p, size_t bytes) {
+    const size_t off = (used + 255) & ~size_t(255);
+    used = off + bytes;
+    p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+  }
+};
 
 int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int count, int mem) {
   h->prm = *p;
@@ -2860,48 +2876,66 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   OTF_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
   OTF_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   OTF_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
-  if (h->fp64) {
-    OTF_CUDA(cudaMalloc(&d.r, 3 * n * sizeof(double)));
-    OTF_CUDA(cudaMalloc(&d.v, 3 * n * sizeof(double)));
-  } else {
-    OTF_CUDA(cudaMalloc(&d.rlo, n * sizeof(float4)));
-    OTF_CUDA(cudaMalloc(&d.vh, 3 * n * sizeof(float)));
-    OTF_CUDA(cudaMalloc(&d.vl, 3 * n * sizeof(float)));
-  }
-  OTF_CUDA(cudaMalloc(&d.F, 3 * n * tf));
-  OTF_CUDA(cudaMalloc(&d.epot, n * tf));
-  OTF_CUDA(cudaMalloc(&d.W, 6 * n * tf));
-  OTF_CUDA(cudaMalloc(&d.rel, n * v4));
-  OTF_CUDA(cudaMalloc(&d.relb, n * v4));
-  if (d.vacf_slots > 0) OTF_CUDA(cudaMalloc(&d.vbuf, (size_t)d.vacf_slots * 3 * n * tf));
-  OTF_CUDA(cudaMalloc(&d.id, n * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&d.type, n * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&d.cpk, n * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&d.rB, 3 * n * sizeof(double)));
-  OTF_CUDA(cudaMalloc(&d.vB, 3 * n * sizeof(double)));
-  OTF_CUDA(cudaMalloc(&d.idB, n * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&d.typeB, n * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&d.cellB, n * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&d.slot, n * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&d.perm, n * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&d.cellcount, ncell * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&d.cellstart, (ncell + 1) * sizeof(int)));
-  if (p->pair_mode == MD_PAIR_VERLET)
-    OTF_CUDA(cudaMalloc(&d.nbr, (size_t)d.maxchunks * maxnb * 32 * sizeof(uint32_t)));
   if (p->pair_mode == MD_PAIR_TILES)
     if (int rc = setup_tiles(h, reps, count)) return rc;
-  OTF_CUDA(cudaMalloc(&d.nnb, n * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&d.partials, (size_t)blocks * kNRed * sizeof(double)));
-  OTF_CUDA(cudaMalloc(&d.counter, count * sizeof(unsigned)));
-  OTF_CUDA(cudaMalloc(&d.obs, count * sizeof(ObsDev)));
-  OTF_CUDA(cudaMalloc(&d.st, sizeof(StepDev)));
-  OTF_CUDA(cudaMalloc(&d.rebuild, (count + 1) * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&d.err, sizeof(unsigned)));
-  OTF_CUDA(cudaMalloc(&h->d_rep, count * sizeof(Rep)));
-  OTF_CUDA(cudaMalloc(&h->d_rep_of_atom, n * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&h->d_rep_of_cell, ncell * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&h->d_rep_of_block, blocks * sizeof(int)));
-  OTF_CUDA(cudaMalloc(&h->d_lam, count * sizeof(double)));
+  const size_t ntiles = h->tiles_host.size();
+  auto carve = [&](Arena &A) {
+    if (h->fp64) {
+      A.take(d.r, 3 * n * sizeof(double));
+      A.take(d.v, 3 * n * sizeof(double));
+    } else {
+      A.take(d.rlo, n * sizeof(float4));
+      A.take(d.vh, 3 * n * sizeof(float));
+      A.take(d.vl, 3 * n * sizeof(float));
+    }
+    A.take(d.F, 3 * n * tf);
+    A.take(d.epot, n * tf);
+    A.take(d.W, 6 * n * tf);
+    A.take(d.rel, n * v4);
+    A.take(d.relb, n * v4);
+    if (d.vacf_slots > 0) A.take(d.vbuf, (size_t)d.vacf_slots * 3 * n * tf);
+    A.take(d.id, n * sizeof(int));
+    A.take(d.type, n * sizeof(int));
+    A.take(d.cpk, n * sizeof(int));
+    A.take(d.rB, 3 * n * sizeof(double));
+    A.take(d.vB, 3 * n * sizeof(double));
+    A.take(d.idB, n * sizeof(int));
+    A.take(d.typeB, n * sizeof(int));
+    A.take(d.cellB, n * sizeof(int));
+    A.take(d.slot, n * sizeof(int));
+    A.take(d.perm, n * sizeof(int));
+    A.take(d.cellcount, ncell * sizeof(int));
+    A.take(d.cellstart, (ncell + 1) * sizeof(int));
+    if (p->pair_mode == MD_PAIR_VERLET) A.take(d.nbr, (size_t)d.maxchunks * maxnb * 32 * sizeof(uint32_t));
+    if (p->pair_mode == MD_PAIR_TILES) {
+      A.take(h->d_tiles, ntiles * sizeof(Tile));
+      A.take(d.tnb, (size_t)(d.maxnb / 8) * n * sizeof(uint4));
+      A.take(d.tcl, (size_t)(kMaxCloseT / 8) * n * sizeof(uint4));
+      A.take(d.trec, ntiles * sizeof(TileWin));
+      A.take(d.tcell, ntiles * (size_t)(d.wcap + kWinPad));
+    }
+    A.take(d.nnb, n * sizeof(int));
+    A.take(d.partials, (size_t)blocks * kNRed * sizeof(double));
+    A.take(d.counter, count * sizeof(unsigned));
+    A.take(d.obs, count * sizeof(ObsDev));
+    A.take(d.st, sizeof(StepDev));
+    A.take(d.rebuild, (count + 1) * sizeof(int));
+    A.take(d.err, sizeof(unsigned));
+    A.take(h->d_rep, count * sizeof(Rep));
+    A.take(h->d_rep_of_atom, n * sizeof(int));
+    A.take(h->d_rep_of_cell, ncell * sizeof(int));
+    A.take(h->d_rep_of_block, blocks * sizeof(int));
+    A.take(h->d_lam, count * sizeof(double));
+  };
+  {
+    Arena sizes;
+    carve(sizes);
+    OTF_CUDA(cudaMalloc(&h->arena, sizes.used));
+    Arena a;
+    a.base = h->arena;
+    carve(a);
+  }
+  d.tiles = h->d_tiles;
   OTF_CUDA(cudaMallocHost(&h->h_obs, count * sizeof(ObsDev)));
   OTF_CUDA(cudaMallocHost(&h->h_st, sizeof(StepDev)));
   OTF_CUDA(cudaMallocHost(&h->h_err, sizeof(unsigned)));
@@ -2912,6 +2946,8 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   d.rep_of_block = h->d_rep_of_block;
   d.lam = h->d_lam;
   cudaStream_t st = h->stream;
+  if (p->pair_mode == MD_PAIR_TILES)
+    if (int rc = finish_tiles(h, st)) return rc;
   // replica lookup tables (set-up only), filled on the device from the
   // descriptor table
   OTF_CUDA(cudaMemcpyAsync(h->d_rep, h->reps.data(), count * sizeof(Rep), cudaMemcpyHostToDevice, st));
