@@ -17,9 +17,14 @@
 // another cell shifts its offset by whole cell edges; crossing the periodic
 // boundary only changes the cell index.
 //
-// Neighbour lists are stored per chunk of up to 32 consecutive atoms of a
-// cell: a block of max_neighbors rows of 32 words, so the list build writes
-// rows that stay together in L2 and the pair kernel reads them coalesced.
+// Neighbour lists.  MD_PAIR_VERLET stores them per chunk of up to 32
+// consecutive atoms: a block of max_neighbors rows of 32 words (atom index
+// and image code), so the list build writes rows that stay together in L2
+// and the pair kernel reads them coalesced.  MD_PAIR_TILES (the mixed
+// Lennard-Jones form) cuts the cells into tiles; a tile's CTA stages the
+// tile and its one-cell shell in shared memory in the tile's own frame, and
+// the lists hold 16-bit byte offsets into that window (see the tile-window
+// section below).
 //
 // Replicas.  One handle can hold many independent systems ("replicas", of
 // uneven sizes, densities and temperatures).  Their atoms, cells and
