@@ -77,10 +77,12 @@ def test_tiles_agree_with_verlet_lists(pkg):
     assert np.abs(a["F"] - b["F"]).max() <= 4e-5 * max(np.abs(b["F"]).max(), frms)
 
 
-def test_full_size_tiles_forces_and_reduction(pkg, oracle_mod):
-    """The 2,048,000-atom liquid of the benchmark on the tile path."""
+@pytest.mark.parametrize("skin", [0.3, 0.4])
+def test_full_size_tiles_forces_and_reduction(pkg, oracle_mod, skin):
+    """The 2,048,000-atom liquid of the benchmark on the tile path (skin 0.4
+    is the benchmark's: 46^3 cells, a close segment out to 1.43 sigma)."""
     s, st = melted(pkg, 80, seed=1)
-    g = pkg.System(tiles(pkg, s), st["r"], st["v"])
+    g = pkg.System(tiles(pkg, s, skin=skin), st["r"], st["v"])
     g.step(2)
     got = g.particles()
     F, e, W = oracle_mod.lj_forces(got["r"], s["L"], method="cells")
