@@ -718,7 +718,7 @@ def tv_reference():
         return None
 
 
-def run_time_to_viscosity(pkg, synth, torch, replicas=64, chunk=4000, max_steps=48000, tail=None, tail_steps=2000):
+def run_time_to_viscosity(pkg, synth, torch, replicas=256, chunk=2000, max_steps=48000, tail=None, tail_steps=2000):
     """Time to a Green-Kubo viscosity at <= 2 % error, 4,000-atom LJ liquid
     (rho* = 0.8442, T* = 0.722; eta of each replica from its stress
     autocorrelation, mean of xy/xz/yz, integrated to t_cut = 2 tau).  The
@@ -740,7 +740,7 @@ def run_time_to_viscosity(pkg, synth, torch, replicas=64, chunk=4000, max_steps=
     Vs = np.full(replicas, V)
     sync = torch.cuda.synchronize
     learned, steps, prod_s, history = None, 0, 0.0, []
-    mean = se = 0.0
+    mean = se = T_mean = 0.0
     while steps < max_steps:
         k = tail_steps if (tail is not None and steps == 0) else chunk
         sync()
@@ -756,6 +756,7 @@ def run_time_to_viscosity(pkg, synth, torch, replicas=64, chunk=4000, max_steps=
             learned = (eta_l, used, prod_s, time.perf_counter() - ti)
             continue
         mean, se = float(a["eta"].mean()), float(a["eta"].std(ddof=1) / math.sqrt(replicas))
+        T_mean = float(a["T"].mean())
         history.append([steps, mean, se])
         # both conditions of the criterion (the run goes on while the mean is
         # still more than 2 % from the reference, even at 2 % standard error)
@@ -786,7 +787,8 @@ def run_time_to_viscosity(pkg, synth, torch, replicas=64, chunk=4000, max_steps=
                          "ensemble Green-Kubo viscosity has <= 2 % relative standard error and lies within 2 % of "
                          "the reference eta (long FP64 GPU ensemble); 4,000-atom LJ liquid, rho*=0.8442, T*=0.722, "
                          "eta to t_cut = 2 tau; stress and heat-flux correlators in every form",
-           "reference": ref, "eta": mean, "eta_se": se, "steps_per_replica": steps, "replicas": replicas,
+           "reference": ref, "eta": mean, "eta_se": se, "T_mean": T_mean, "steps_per_replica": steps,
+           "replicas": replicas,
            "history": history, "reached_2pct_se": bool(reached_se),
            "deviation_from_reference": dev, "within_2pct_of_reference": within,
            "replica_steps_needed": need,
