@@ -40,8 +40,8 @@ SPEC = dict(stress=(12, 16, 2, 1), heatflux=(12, 16, 2, 1), vacf=(8, 16, 2, 1))
 PAIR_FLOP_PER_ATOM = 0.5 * RHO * (4.0 / 3.0) * math.pi * RC ** 3 * 50.0  # unique pairs x 50 flop
 
 
-def workload_name(n):
-    return (f"LJ liquid {n:,} atoms (fcc {round((n / 4) ** (1 / 3))}^3 x 4 melted), rho*={RHO}, T*={T_STAR}, rc={RC} shifted, "
+def workload_name(n, start="melted"):
+    return (f"LJ liquid {n:,} atoms (fcc {round((n / 4) ** (1 / 3))}^3 x 4 {start}), rho*={RHO}, T*={T_STAR}, rc={RC} shifted, "
             f"dt={DT}, velocity Verlet NVE; on-the-fly correlators: stress xy/xz/yz and heat flux "
             f"(b=12,p=16,m=2,u=1), per-atom VACF over all atoms (b=8,p=16,m=2,u=1)")
 
@@ -882,7 +882,7 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded fcc, Maxwell-Boltzmann)",
            "impl": "reference",
-           "config": {"workload": workload_name(n) + " (fcc start, not melted)", "n_atoms": n, "precision": "fp64"},
+           "config": {"workload": workload_name(n, start="start, not melted"), "n_atoms": n, "precision": "fp64"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": f"{args.steps} timed steps of the full workload from the fcc start (not melted) "
                                       f"after {args.warmup} warm-up"},
