@@ -849,10 +849,18 @@ def cpu_baseline(st, s, budget_s=20.0):
         el = time.perf_counter() - t0
         if el > budget_s or steps >= 50:
             break
+    # the same oracle on one core (one whole step, continuing the same run)
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    md.step(1, cs=cs, cv=cv)
+    el1 = time.perf_counter() - t1
+    oracle.set_threads(cores)
     return {"value": n * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{steps} whole steps of the {n:,}-atom workload from the melted state the GPU runs "
                       f"(link-cell forces, integration, observables, stress/heat-flux and per-atom VACF "
-                      f"correlators) after 1 warm-up step, {el:.1f} s"}
+                      f"correlators) after 1 warm-up step, {el:.1f} s",
+            "single_core": {"value": n / el1, "unit": UNIT, "cores": 1,
+                            "sample": f"1 further whole step of the same run on one thread, {el1:.1f} s"}}
 
 
 def run_reference(args):

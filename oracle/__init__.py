@@ -78,12 +78,19 @@ def lib():
             L.orc_md_scale_velocities.argtypes = [C.c_void_p, C.c_double]
             L.orc_md_scale_velocities.restype = None
             L.orc_num_threads.restype = C.c_int
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_set_threads.restype = None
             _lib = L
     return _lib
 
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of the following oracle calls (for timing)."""
+    lib().orc_set_threads(int(n))
 
 
 def _f64(a, shape=None):

@@ -612,3 +612,13 @@ int orc_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Sets the number of OpenMP threads of the following calls (timing only:
+ * every per-atom result is computed by one thread whatever the count). */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
