@@ -501,7 +501,7 @@ int validate_corr_params(const corr_params &p) {
   return MD_OK;
 }
 
-int Correlator::create(const corr_params &p, cudaStream_t s) {
+int Correlator::create(const corr_params &p, cudaStream_t s, cudaStream_t zero_on) {
   int rc = validate_corr_params(p);
   if (rc) return rc;
   prm = p;
@@ -535,16 +535,17 @@ int Correlator::create(const corr_params &p, cudaStream_t s) {
   const size_t nvals = grouped ? (size_t)dev.ng * dev.nchunk * p.b * p.p : (size_t)p.nseries * p.b * p.p;
   OTF_CUDA(cudaMalloc(&dev.vals, nvals * sizeof(double)));
   OTF_CUDA(cudaMalloc(&d_fold, (size_t)dev.ng * p.b * p.p * sizeof(double)));
-  return reset();
+  return reset(zero_on);
 }
 
-int Correlator::reset() {
+int Correlator::reset(cudaStream_t on) {
+  cudaStream_t zs = on ? on : stream;
   const size_t esz = prec == MD_PREC_FP64 ? sizeof(double) : sizeof(float);
   const size_t ring = (size_t)prm.b * prm.p * prm.nseries * esz;
   const size_t nvals = grouped ? (size_t)dev.ng * dev.nchunk * prm.b * prm.p : (size_t)prm.nseries * prm.b * prm.p;
-  OTF_CUDA(cudaMemsetAsync(dev.ringx, 0, ring, stream));
-  if (dev.cross) OTF_CUDA(cudaMemsetAsync(dev.ringy, 0, ring, stream));
-  OTF_CUDA(cudaMemsetAsync(dev.vals, 0, nvals * sizeof(double), stream));
+  OTF_CUDA(cudaMemsetAsync(dev.ringx, 0, ring, zs));
+  if (dev.cross) OTF_CUDA(cudaMemsetAsync(dev.ringy, 0, ring, zs));
+  OTF_CUDA(cudaMemsetAsync(dev.vals, 0, nvals * sizeof(double), zs));
   pushes = 0;
   return MD_OK;
 }

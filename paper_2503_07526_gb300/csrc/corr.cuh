@@ -128,9 +128,11 @@ struct Correlator {
   double *d_in = nullptr;  // staging for host pushes, [2][ns]
   double *d_fold = nullptr;// [ng][b][p] folded lag sums
 
-  int create(const corr_params &p, cudaStream_t s);
+  // zero_on: the stream of the initial zeroing (null: s); a caller that
+  // passes another stream orders s after it before the first push
+  int create(const corr_params &p, cudaStream_t s, cudaStream_t zero_on = nullptr);
   void destroy();
-  int reset();
+  int reset(cudaStream_t on = nullptr);
   int64_t push_count() const {
     if (!host_steps) return pushes;
     return u > 0 ? (*host_steps - (host_base ? *host_base : 0)) / u : 0;

@@ -2085,6 +2085,7 @@ struct md_handle_s {
   cudaGraphExec_t graphR[kGraphSteps + 1] = {};
   cudaStream_t side = nullptr;       // the correlator pushes run here, beside the next step
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_ring = nullptr;  // md_init: the velocity correlator's ring zeroed (side stream)
   bool vacf_pending = false;         // correlator pushes on `side` the next reduction must wait for
   // timed graphs (md_set_timing with graphs), each with its own event
   // records inside: sets 0 and 1 are two instances of the kGraphSteps-step
@@ -2636,6 +2637,7 @@ void release(md_handle *h) {
   }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_ring) cudaEventDestroy(h->ev_ring);
   // every device array of the handle lives in the arena, except the
   // particles' readout staging
   if (h->arena) cudaFree(h->arena);
@@ -2880,6 +2882,7 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   OTF_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   OTF_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
   OTF_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  OTF_CUDA(cudaEventCreateWithFlags(&h->ev_ring, cudaEventDisableTiming));
   OTF_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   if (p->pair_mode == MD_PAIR_TILES)
     if (int rc = setup_tiles(h, reps, count)) return rc;
@@ -3005,8 +3008,11 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
                    k == 2 ? p->precision : MD_PREC_FP64, specs[k]->u * p->dt};
     Correlator &c = h->banks[k].c;
     h->bank_on[k] = true;
-    int rc = c.create(cp, st);
+    // the velocity correlator's ring (3.1 GB at 2,048,000 atoms) is zeroed
+    // on the side stream, beside the first sort, list build and forces
+    int rc = c.create(cp, st, k == 2 ? h->side : nullptr);
     if (rc) return rc;
+    if (k == 2) OTF_CUDA(cudaEventRecord(h->ev_ring, h->side));
     c.borrowed = true;
     c.host_steps = &h->steps_done;
     if (k == 2) {
@@ -3033,6 +3039,7 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   }
   rc = h->fp64 ? launch_pair<double>(h, st) : launch_pair<float>(h, st);
   if (rc) return rc;
+  if (h->bank_on[2]) OTF_CUDA(cudaStreamWaitEvent(st, h->ev_ring, 0));  // before any push or readout
   if ((rc = refresh_obs(h))) return rc;
   if ((rc = check_device(h))) return rc;
   if (p->autotune) {
