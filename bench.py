@@ -425,8 +425,8 @@ def run_batched(pkg, synth, steps, torch):
     form on the tile-window path, stress and heat-flux correlators)."""
     reps, temps = c4_ensemble(pkg, synth)
     p = pkg.make_params(1, 1.0, rc=RC, dt=DT, skin=0.2, precision=pkg.MD_PREC_MIXED, pair_mode=pkg.MD_PAIR_TILES,
-                        stress=(12, 16, 2, 1), heatflux=(12, 16, 2, 1), vacf=None)
-    g = pkg.System(p, replicas=reps)
+                        autotune=True, stress=(12, 16, 2, 1), heatflux=(12, 16, 2, 1), vacf=None)
+    g = pkg.System(p, replicas=reps)  # md_init picks the cell tiles and CTA size on the ensemble itself
     melt_replicas(g, temps, 300, 300)
     g.reset_correlators()
     g.step(5)
@@ -441,11 +441,13 @@ def run_batched(pkg, synth, steps, torch):
     cfg = g.config()
     g.close()
     return {"workload": "256 LJ replicas, sizes log-uniform in [500, 32000] atoms, rho* uniform in [0.7, 0.9], "
-                        "T* uniform in [0.7, 2.0], rc=2.5, dt=0.005, skin 0.2, mixed form (tile windows), one handle, one graph "
-                        "launch per 8 steps; stress and heat-flux correlators per replica",
+                        "T* uniform in [0.7, 2.0], rc=2.5, dt=0.005, skin 0.2, mixed form (tile windows; cell tiles and "
+                        "CTA size autotuned at md_init), one handle, one graph launch per 8 steps; stress and heat-flux "
+                        "correlators per replica",
             "atoms": cfg["atoms"], "replicas": cfg["replicas"], "steps": steps, "ms_per_step": ms / steps,
             "value": cfg["atoms"] * steps / (ms / 1e3), "unit": UNIT,
-            "tiles": cfg["tiles"], "tile_threads": cfg["tile_threads"], "window_capacity": cfg["window_capacity"]}
+            "tiles": cfg["tiles"], "tile_threads": cfg["tile_threads"], "window_capacity": cfg["window_capacity"],
+            "tile_extent": list(cfg["tile_extent"])}
 
 
 IONIC = dict(cells=40, rho=0.031, T_K=1300.0, masses=(22.99, 35.45), A=1200.0, brho=0.32, C=10.0, rc=10.0,

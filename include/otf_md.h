@@ -122,11 +122,17 @@ typedef struct {
                          correlator pushes on a second stream beside the next step; one graph
                          of 1..7 steps for the rest of a call), each captured the first time a
                          call needs it; 0: direct launches */
-  int32_t autotune;   /* 1: md_init times the pair kernel (64/128/256 threads
-                         per CTA) and the list build (j-parallel at 2/4/8,
-                         i-parallel and staged at 4/8 warps per CTA) on the
-                         system and
-                         keeps the fastest (md_get_config) */
+  int32_t autotune;   /* 1: md_init times launch shapes on the system itself and
+                         keeps the fastest (md_get_config).  MD_PAIR_VERLET:
+                         the pair kernel at 64/128/256 threads per CTA and the
+                         list build (j-parallel at 2/4/8, i-parallel and staged
+                         at 4/8 warps per CTA).  MD_PAIR_TILES: the cell tiles
+                         (at most 3x2x2, 2x2x2 or 3x3x2 cells, those whose
+                         windows fit) at 1.0/1.1/1.3 times the mean tile in
+                         threads per CTA, scored as one pair launch plus an
+                         eighth of a list build.  Tilings round coordinates in
+                         different frames, so results can differ from the
+                         untuned handle at FP32 rounding level. */
   corr_spec stress, heatflux, vacf; /* the three correlators of Sec. 2.3/2.7 */
   int32_t list_build; /* neighbour-list build when not autotuned: 0 = the
                          library's default, 1 = j-parallel, 2 = i-parallel,
@@ -183,6 +189,8 @@ typedef struct {
   int64_t tiles;            /* MD_PAIR_TILES: tiles (CTAs of the pair kernel); else 0 */
   int32_t window_capacity;  /* MD_PAIR_TILES: shared-memory window slots per tile */
   int32_t tile_threads;     /* MD_PAIR_TILES: threads per tile CTA */
+  int32_t tile_extent[3];   /* MD_PAIR_TILES: largest tile extent in cells along x, y, z
+                               (3 2 2 unless the autotuner picked another tiling) */
 } md_config;
 
 /* Observables of the last completed step (Sec. 2.3). */

@@ -62,7 +62,7 @@ class md_config(C.Structure):
     _fields_ = [("replicas", C.c_int32), ("pair_threads", C.c_int32), ("build_warps", C.c_int32),
                 ("max_neighbors", C.c_int32), ("atoms", C.c_int64), ("cells", C.c_int64),
                 ("build_kind", C.c_int32), ("vacf_input_bytes", C.c_int64), ("tiles", C.c_int64),
-                ("window_capacity", C.c_int32), ("tile_threads", C.c_int32)]
+                ("window_capacity", C.c_int32), ("tile_threads", C.c_int32), ("tile_extent", C.c_int32 * 3)]
 
 
 class gk_tail_rule(C.Structure):
@@ -398,7 +398,7 @@ class System:
                     build_kind=c.build_kind,
                     max_neighbors=c.max_neighbors, atoms=c.atoms, cells=c.cells,
                     vacf_input_bytes=c.vacf_input_bytes, tiles=c.tiles, window_capacity=c.window_capacity,
-                    tile_threads=c.tile_threads)
+                    tile_threads=c.tile_threads, tile_extent=tuple(c.tile_extent))
 
     def step(self, nsteps):
         _check(lib().md_step(self._h, int(nsteps)))

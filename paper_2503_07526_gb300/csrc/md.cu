@@ -2075,6 +2075,16 @@ __global__ void __launch_bounds__(WARPS * 32) k_build_ip(Sys d, LJ<TF> lj) {
 
 using namespace otf;
 
+// One tiling of the handle's replicas: tiles of at most ext[a] cells along
+// each axis, its window capacity and CTA size.
+struct TilePlan {
+  int ext[3] = {3, 2, 2};
+  std::vector<Tile> tiles;
+  int wcap = 0;
+  int threads = 0;
+  double mean_tile = 0.0;
+};
+
 struct md_handle_s {
   md_params prm{};
   Sys d{};
@@ -2115,7 +2125,10 @@ struct md_handle_s {
   bool bank_on[kNBanks] = {false, false, false, false};
   double *d_out = nullptr;  // unsort staging [16][n]
   char *arena = nullptr;    // one device allocation holding every per-atom, per-cell and per-tile array
-  std::vector<Tile> tiles_host;  // MD_PAIR_TILES: the tile table (uploaded once)
+  std::vector<Tile> tiles_host;  // MD_PAIR_TILES: the tile table in use
+  std::vector<TilePlan> tile_plans;  // MD_PAIR_TILES: the candidate tilings ([0]: the default)
+  int tile_plan = 0;                        // the one in use
+  size_t tile_rec_cap = 0, tile_cell_cap = 0;  // per-tile array capacity (records, window-cell bytes)
   ObsDev *h_obs = nullptr;  // pinned [nrep]
   StepDev *h_st = nullptr;  // pinned
   unsigned *h_err = nullptr;
@@ -2676,9 +2689,12 @@ float time_runs(md_handle *h, int reps, Fn fn) {
 // on the system itself (forces
 // and lists are recomputed from the unchanged state, so the trajectory is
 // not touched) and keeps the fastest of each.
+int autotune_tiles(md_handle *h);
+
 template <typename TF>
 int autotune(md_handle *h) {
-  if (h->prm.pair_mode != MD_PAIR_VERLET) return MD_OK;  // nothing to choose for the other modes
+  if (h->prm.pair_mode == MD_PAIR_TILES) return autotune_tiles(h);
+  if (h->prm.pair_mode != MD_PAIR_VERLET) return MD_OK;  // nothing to choose for the cell sweep
   float best = 1e30f;
   int best_t = h->pair_threads;
   for (int t : {64, 128, 256}) {
@@ -2728,15 +2744,30 @@ std::vector<std::pair<int, int>> tile_segments(int nc, int b) {
 // sigma^3, plus 64 slots), the CTA size (1.1 times the largest mean tile,
 // 128..384 threads; the rare larger tile takes a second pass) and the list
 // arrays.
-int setup_tiles(md_handle *h, const md_replica *reps, int count) {
-  Sys &d = h->d;
+// Threads per tile CTA: f times the largest mean tile, in warps, 128..384.
+int tile_threads_for(double mean_tile, double f) {
+  return std::max(128, std::min(kTileThreadsMax, ((int)std::ceil(f * mean_tile) + 31) / 32 * 32));
+}
+
+// Makes candidate tiling k, at `threads` per tile CTA, the handle's tiling
+// (host side; finish_tiles uploads it).
+void use_plan_host(md_handle *h, int k, int threads) {
+  const TilePlan &tp = h->tile_plans[k];
+  h->tile_plan = k;
+  h->tiles_host = tp.tiles;
+  h->d.ntiles = (int)tp.tiles.size();
+  h->d.wcap = tp.wcap;
+  h->tile_threads = threads;
+}
+
+int plan_tiles(const md_handle *h, const md_replica *reps, int count, const int ext[3], TilePlan &out) {
   const md_params &p = h->prm;
-  std::vector<Tile> tiles;
+  out = TilePlan{};
+  for (int a = 0; a < 3; ++a) out.ext[a] = ext[a];
   double need = 0.0, mean_win = 0.0, mean_tile = 0.0;
   for (int k = 0; k < count; ++k) {
     const Rep &R = h->reps[k];
-    const auto sx = tile_segments(R.nc, kTileExt[0]), sy = tile_segments(R.nc, kTileExt[1]),
-               sz = tile_segments(R.nc, kTileExt[2]);
+    const auto sx = tile_segments(R.nc, ext[0]), sy = tile_segments(R.nc, ext[1]), sz = tile_segments(R.nc, ext[2]);
     int mx = 0, my = 0, mz = 0;
     for (const auto &z : sz)
       for (const auto &y : sy)
@@ -2749,7 +2780,7 @@ int setup_tiles(md_handle *h, const md_replica *reps, int count) {
           t.bx = (unsigned char)x.second;
           t.by = (unsigned char)y.second;
           t.bz = (unsigned char)z.second;
-          tiles.push_back(t);
+          out.tiles.push_back(t);
           mx = std::max(mx, x.second);
           my = std::max(my, y.second);
           mz = std::max(mz, z.second);
@@ -2762,23 +2793,50 @@ int setup_tiles(md_handle *h, const md_replica *reps, int count) {
     mean_win = std::max(mean_win, win_cells * apc + 1.0);
     mean_tile = std::max(mean_tile, (double)mx * my * mz * apc);
   }
-  d.wcap = std::min(kWinMaxSlots, ((int)std::ceil(need) + 63) / 64 * 64);
-  if (p.window_slots > 0) d.wcap = p.window_slots;  // the caller's capacity (checked at every build)
-  if ((p.window_slots == 0 && 1.1 * mean_win > d.wcap) || d.maxnb > 65528) {
+  out.wcap = std::min(kWinMaxSlots, ((int)std::ceil(need) + 63) / 64 * 64);
+  if (p.window_slots > 0) out.wcap = p.window_slots;  // the caller's capacity (checked at every build)
+  if ((p.window_slots == 0 && 1.1 * mean_win > out.wcap) || h->d.maxnb > 65528) {
     set_error("md_init: MD_PAIR_TILES: cells hold too many atoms for a shared-memory window "
               "(mean window %.0f slots of %d); use MD_PAIR_VERLET",
-              mean_win, d.wcap);
+              mean_win, out.wcap);
     return MD_EINVAL;
   }
-  d.ntiles = (int)tiles.size();
-  h->tile_threads = std::max(128, std::min(kTileThreadsMax, ((int)std::ceil(1.1 * mean_tile) + 31) / 32 * 32));
-  h->tiles_host = std::move(tiles);
+  out.mean_tile = mean_tile;
+  out.threads = tile_threads_for(mean_tile, 1.1);
   return MD_OK;
 }
 
-// MD_PAIR_TILES, once the arrays are carved: the tile table uploaded, every
-// record marked "no window" (natoms = -1) until the first list build, and
-// the kernels' shared-memory limits raised to the window size.
+// MD_PAIR_TILES: the tile table of tiles of at most 3 x 2 x 2 cells, the
+// window capacity (the largest window expected at 1.2 times a replica's
+// mean density, or at least one atom per sigma^3, plus 64 slots) and the
+// CTA size (1.1 times the largest mean tile, 128..384 threads; the rare
+// larger tile takes a second pass).  With md_params.autotune the other
+// candidate tilings (2 x 2 x 2 and 3 x 3 x 2 cells) are planned too, and
+// the per-tile arrays are sized for the largest of them.
+int setup_tiles(md_handle *h, const md_replica *reps, int count) {
+  static const int kExts[3][3] = {{3, 2, 2}, {2, 2, 2}, {3, 3, 2}};
+  h->tile_plans.clear();
+  for (int c = 0; c < (h->prm.autotune ? 3 : 1); ++c) {
+    TilePlan tp;
+    const int rc = plan_tiles(h, reps, count, kExts[c], tp);
+    if (rc && c == 0) return rc;  // the default tiling must fit
+    if (!rc) h->tile_plans.push_back(std::move(tp));
+  }
+  clear_error();
+  h->tile_rec_cap = 0;
+  h->tile_cell_cap = 0;
+  for (const TilePlan &tp : h->tile_plans) {
+    h->tile_rec_cap = std::max(h->tile_rec_cap, tp.tiles.size());
+    h->tile_cell_cap = std::max(h->tile_cell_cap, tp.tiles.size() * (size_t)(tp.wcap + kWinPad));
+  }
+  use_plan_host(h, 0, h->tile_plans[0].threads);
+  return MD_OK;
+}
+
+// MD_PAIR_TILES, once the arrays are carved (and again for every tiling the
+// autotuner tries): the tile table uploaded, every record marked "no window"
+// (natoms = -1) until the next list build, and the kernels' shared-memory
+// limits set to the window size.
 int finish_tiles(md_handle *h, cudaStream_t st) {
   Sys &d = h->d;
   const size_t nt = h->tiles_host.size();
@@ -2788,6 +2846,57 @@ int finish_tiles(md_handle *h, cudaStream_t st) {
                                 (int)tile_smem(d.wcap, false)));
   OTF_CUDA(cudaFuncSetAttribute(k_pair_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)tile_smem(d.wcap, true)));
+  return MD_OK;
+}
+
+// MD_PAIR_TILES autotuner (md_params.autotune): every candidate tiling
+// whose windows fit (tiles of at most 3 x 2 x 2, 2 x 2 x 2 and 3 x 3 x 2
+// cells) at 1.0, 1.1 and 1.3 times its largest mean tile in threads per
+// CTA, timed on the system itself as one pair-kernel launch plus an eighth
+// of a list build (a rebuild's share of a step at a skin of 0.3-0.4 sigma).
+// A tiling whose build finds a window over capacity is dropped.  The
+// fastest is kept, and the lists, window records and forces are rebuilt
+// with it; the trajectory is not touched.
+int autotune_tiles(md_handle *h) {
+  const LJ<float> lj = lj_of<float>(h->prm);
+  const size_t nflags = (size_t)(h->nrep + 1) * sizeof(int);
+  auto build = [&] {
+    cudaMemsetAsync(h->d.rebuild, 1, nflags, h->stream);
+    k_build_tile<<<h->d.ntiles, h->tile_threads, tile_smem(h->d.wcap, false), h->stream>>>(h->d, lj);
+  };
+  float best = 1e30f;
+  int best_k = 0, best_t = h->tile_threads;
+  for (int k = 0; k < (int)h->tile_plans.size(); ++k) {
+    int tried[3], ntried = 0;
+    for (double f : {1.0, 1.1, 1.3}) {
+      const int t = tile_threads_for(h->tile_plans[k].mean_tile, f);
+      bool seen = false;
+      for (int q = 0; q < ntried; ++q) seen = seen || tried[q] == t;
+      if (seen) continue;
+      tried[ntried++] = t;
+      use_plan_host(h, k, t);
+      if (int rc = finish_tiles(h, h->stream)) return rc;
+      const float mb = time_runs(h, 2, build);
+      OTF_LAUNCH_CHECK();
+      OTF_CUDA(cudaMemcpyAsync(h->h_err, h->d.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+      OTF_CUDA(cudaStreamSynchronize(h->stream));
+      if (*h->h_err) {  // a window over capacity: not a candidate
+        OTF_CUDA(cudaMemsetAsync(h->d.err, 0, sizeof(unsigned), h->stream));
+        continue;
+      }
+      const float mp = time_runs(h, 5, [&] { launch_pair<float>(h, h->stream); });
+      OTF_LAUNCH_CHECK();
+      const float cost = mp + 0.125f * mb;
+      if (cost < best) best = cost, best_k = k, best_t = t;
+    }
+  }
+  use_plan_host(h, best_k, best_t);
+  if (int rc = finish_tiles(h, h->stream)) return rc;
+  build();
+  OTF_LAUNCH_CHECK();
+  if (int rc = launch_pair<float>(h, h->stream)) return rc;
+  OTF_CUDA(cudaMemsetAsync(h->d.rebuild, 0, nflags, h->stream));
+  OTF_CUDA(cudaStreamSynchronize(h->stream));
   return MD_OK;
 }
 
@@ -2886,7 +2995,6 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
   OTF_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   if (p->pair_mode == MD_PAIR_TILES)
     if (int rc = setup_tiles(h, reps, count)) return rc;
-  const size_t ntiles = h->tiles_host.size();
   auto carve = [&](Arena &A) {
     if (h->fp64) {
       A.take(d.r, 3 * n * sizeof(double));
@@ -2916,11 +3024,11 @@ int init_impl(md_handle *h, const md_params *p, const md_replica *reps, int coun
     A.take(d.cellstart, (ncell + 1) * sizeof(int));
     if (p->pair_mode == MD_PAIR_VERLET) A.take(d.nbr, (size_t)d.maxchunks * maxnb * 32 * sizeof(uint32_t));
     if (p->pair_mode == MD_PAIR_TILES) {
-      A.take(h->d_tiles, ntiles * sizeof(Tile));
+      A.take(h->d_tiles, h->tile_rec_cap * sizeof(Tile));
       A.take(d.tnb, (size_t)(d.maxnb / 8) * n * sizeof(uint4));
       A.take(d.tcl, (size_t)(kMaxCloseT / 8) * n * sizeof(uint4));
-      A.take(d.trec, ntiles * sizeof(TileWin));
-      A.take(d.tcell, ntiles * (size_t)(d.wcap + kWinPad));
+      A.take(d.trec, h->tile_rec_cap * sizeof(TileWin));
+      A.take(d.tcell, h->tile_cell_cap);
     }
     A.take(d.nnb, n * sizeof(int));
     A.take(d.partials, (size_t)blocks * kNRed * sizeof(double));
@@ -3334,6 +3442,7 @@ int md_get_config(md_handle *h, md_config *out) {
   out->tiles = tiles ? h->d.ntiles : 0;
   out->window_capacity = tiles ? h->d.wcap : 0;
   out->tile_threads = tiles ? h->tile_threads : 0;
+  for (int a = 0; a < 3; ++a) out->tile_extent[a] = tiles ? h->tile_plans[h->tile_plan].ext[a] : 0;
   if (tiles) out->build_kind = 3;
   return MD_OK;
 }

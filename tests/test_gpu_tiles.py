@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from paper_2503_07526_gb300 import synth
-from test_gpu_md import check_mixed_forces, jittered, melted, params, rel
+from test_gpu_md import F_AT_RC, check_mixed_forces, jittered, melted, params, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -32,10 +32,17 @@ def tiles(pkg, s, **kw):
 
 
 def check_particles(got, oracle_mod, L):
+    """Forces as check_mixed_forces; per-particle energy and virial within
+    2e-5 of their largest magnitude.  The shifted energy is continuous at the
+    cutoff, the virial is not: a pair within 1e-5 rc of rc may fall on either
+    side in FP32 and in FP64, which moves each virial component of both atoms
+    by up to rc |f(rc)| / 2, allowed per such pair as for the forces."""
     F, e, W = oracle_mod.lj_forces(got["r"], L, method="cells")
     check_mixed_forces(got["F"], F, got["r"], L, oracle_mod)
     assert np.abs(got["epot"] - e).max() <= 2e-5 * np.abs(e).max()
-    assert np.abs(got["W"] - W).max() <= 2e-5 * np.abs(W).max()
+    near = oracle_mod.near_cutoff_pairs(got["r"], L, 2.5, 1e-5 * 2.5)
+    allow = 1.001 * 0.5 * 2.5 * abs(F_AT_RC) * near
+    assert (np.abs(got["W"] - W) - allow[None, :]).max() <= 2e-5 * np.abs(W).max()
 
 
 @pytest.mark.parametrize("cells", [6, 7, 9, 12])
@@ -177,3 +184,41 @@ def test_window_capacity_is_checked(pkg):
         with pytest.raises(pkg.MdError) as ei:
             pkg.System(tiles(pkg, s, window_slots=bad), s["r"], s["v"])
         assert ei.value.code == -1
+
+
+def test_tiles_autotune(pkg, oracle_mod):
+    """md_params.autotune on the tile path picks a candidate tiling (tiles of
+    at most 3x2x2, 2x2x2 or 3x3x2 cells) and a CTA size in whole warps; the
+    forces with it stay within the mixed bound of the oracle at init and
+    after ten steps over list rebuilds."""
+    s = jittered(12, seed=31)
+    g = pkg.System(tiles(pkg, s, autotune=True, skin=0.1), s["r"], s["v"])
+    cfg = g.config()
+    assert cfg["tile_extent"] in ((3, 2, 2), (2, 2, 2), (3, 3, 2))
+    assert 128 <= cfg["tile_threads"] <= 384 and cfg["tile_threads"] % 32 == 0
+    check_particles(g.particles(), oracle_mod, s["L"])
+    g.step(10)
+    check_particles(g.particles(), oracle_mod, s["L"])
+    assert g.observables()["rebuilds"] >= 2
+    assert pkg.System(tiles(pkg, s), s["r"], s["v"]).config()["tile_extent"] == (3, 2, 2)
+
+
+def test_tiles_autotune_batch(pkg, oracle_mod):
+    """The autotuner on an uneven batch (replicas of 5 to 8 cells per side):
+    every replica within the mixed bound of the oracle after 20 steps."""
+    reps = []
+    for k, (cells, rho, T) in enumerate(((5, 0.70, 1.5), (6, 0.85, 0.9), (7, 0.80, 1.2), (8, 0.90, 1.0))):
+        t = synth.lj_system(cells, rho=rho, T=T, seed=60 + k)
+        t["r"] = t["r"] + 0.15 * (synth.uniform01(70 + k, t["r"].size).reshape(t["r"].shape) - 0.5)
+        reps.append(dict(r=t["r"], v=t["v"], box=t["L"], n=t["n"]))
+    p = pkg.make_params(1, 1.0, precision=pkg.MD_PREC_MIXED, pair_mode=pkg.MD_PAIR_TILES, skin=0.2, autotune=True,
+                        stress=(6, 16, 2, 1), heatflux=(6, 16, 2, 1), vacf=None)
+    b = pkg.System(p, replicas=reps)
+    assert b.config()["tile_extent"] in ((3, 2, 2), (2, 2, 2), (3, 3, 2))
+    b.step(20)
+    got = b.particles()
+    a0 = 0
+    for rp in reps:
+        sl = slice(a0, a0 + rp["n"])
+        a0 += rp["n"]
+        check_particles({key: got[key][..., sl] for key in ("r", "F", "epot", "W")}, oracle_mod, rp["box"])
