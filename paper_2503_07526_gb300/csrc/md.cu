@@ -59,10 +59,13 @@ constexpr int kCellWarps = 4;  // warps (cells) per CTA in the link-cell kernels
 constexpr int kNRed = 14;      // K, U, V*sigma[6], V*q[3], V*j[3]
 constexpr int kNBanks = 4;     // stress, heat flux, velocity, mass flux
 constexpr int kMaxRedBlocks = 152 * 64;  // reduction CTAs per replica at most
-// atoms per reduction CTA in the mixed form (16 per thread): measured at
-// 2,048,000 atoms, 0.121 ms per step against 0.123 / 0.134 / 0.160 for 2,048 /
-// 1,024 / 512 (the per-CTA merge and the last CTA's pass grow with the count)
-constexpr int kRedAtomsMixed = 4096;
+// atoms per reduction CTA in the mixed form (14 per thread): at 2,048,000
+// atoms its 572 CTAs fill 94 % of the 608 that fit the GPU at once (four per
+// SM) where 4,096 atoms per CTA left 500 (82 %, the SMs holding four CTAs
+// setting the time): 0.1146 against 0.1190 ms per step, and 3,840 atoms
+// 0.1169; smaller CTAs lose more to the per-CTA merge and the last CTA's pass
+// (0.123 / 0.134 / 0.160 ms for 2,048 / 1,024 / 512 atoms)
+constexpr int kRedAtomsMixed = 3584;
 constexpr double kRClose = 1.03;  // close-pair radius of the mixed form, in sigma
 
 // Step counters shared by all replicas.
