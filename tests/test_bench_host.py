@@ -39,10 +39,14 @@ def test_timed_bytes_count_whole_blocks(bench):
 
     # pushes 1..5 wait after the warm-up call; the timed call's passes apply
     # pushes 1..1008 (126 whole blocks) and leave 1009 and 1010 waiting
-    got = bench.vacf_timed_bytes(A, 8, 16, 2, 100)
+    got = bench.vacf_timed_bytes(A, 8, 16, 2, 100, pre=0)
     assert got == bench.vacf_bytes_blocked(0, 1008, 8, 16, 2, 300, 4, 8)
 
     class B:
         warmup, steps = 5, 20
 
-    assert bench.vacf_timed_bytes(B, 8, 16, 2, 100) == bench.vacf_bytes_blocked(0, 24, 8, 16, 2, 300, 4, 8)
+    assert bench.vacf_timed_bytes(B, 8, 16, 2, 100, pre=0) == bench.vacf_bytes_blocked(0, 24, 8, 16, 2, 300, 4, 8)
+    # after the bench's untimed fill of 256 steps the timed call of 20 steps
+    # (warm-up 5) applies pushes 257 .. 280: blocks 33 to 35 in steady state
+    assert bench.vacf_timed_bytes(B, 8, 16, 2, 100, pre=256) == bench.vacf_bytes_blocked(256, 280, 8, 16, 2, 300,
+                                                                                           4, 8)
